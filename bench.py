@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Benchmark of the plain dynamic-circuit path: amplitude-gate updates/s.
+
+Workload (one step = one trajectory of the whole program): the layered
+dynamic circuit on n=30 qubits in complex64 -- 20 layers of a random rotation
+on every qubit then CX on a random perfect matching, a measure + reset of two
+random qubits every 4 layers and a 3-bit feed-forward cond (X / Z), generator
+seed 5, Philox seed 0, shot = step index.  The 8 GiB state is larger than L2,
+so no flush is needed between steps.
+
+value     updates/s = (gates + measures + resets) * 2^n per step / device time,
+          inputs resident (the lowered program is on the device), CUDA events
+          on the launching stream, K steps after W warm-up steps.
+e2e       the same metric through sv_run with host buffers: every step lowers
+          the op list and copies the plan to the device, runs, and reads the
+          classical register back.
+roofline  the state-sweep pass kernel (k_pass): algorithmic bytes (state read
+          + written once per storing pass) / its event-timed duration,
+          against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference
+          the FP64 oracle on the machine's host cores over a bounded prefix of the
+          same n=30 program (gates only), in the same metric.
+
+Multi-GPU: the path shards by independent trajectories; each rank runs its own
+replica (no collective on the data path), time is the max over ranks and
+value the sum of all ranks' updates over that time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-gate updates/s"
+UNIT = "updates/s"
+GEN_SEED = {(28, "c128"): 2, (28, "c64"): 3, (30, "c128"): 4, (30, "c64"): 5}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n, dtype):
+    return (f"plain layered dynamic circuit, n={n}, {'complex64' if dtype == 'c64' else 'complex128'}: "
+            f"20 layers (rotation on every qubit + CX perfect matching), measure+reset 2 qubits every 4 layers, "
+            f"3-bit cond X/Z; 1 trajectory per step")
+
+
+def circuit(n, dtype):
+    from paper_2604_11599_gb300 import workloads
+
+    return workloads.layered(GEN_SEED.get((n, dtype), 5), n, layers=20)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(n, dtype, seconds, gates_cap=None):
+    """The oracle over the longest gate-only prefix of the program that fits in
+    `seconds`; returns (updates/s, sample description, threads)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    c = circuit(n, dtype)
+    ops = c.ops
+    gate_only = 0
+    while gate_only < len(ops) and ops[gate_only]["kind"] == 1:
+        gate_only += 1
+    psi = np.empty(1 << n, dtype=np.complex128)
+    # calibrate on 4 gates, then size the prefix to the time budget
+    t0 = time.perf_counter()
+    oracle.run(ops[:4], n, out=psi)
+    t_small = time.perf_counter() - t0
+    per_gate = max(t_small / 4, 1e-6)
+    k = int(max(4, min(gate_only, seconds / per_gate)))
+    if gates_cap:
+        k = min(k, gates_cap)
+    t0 = time.perf_counter()
+    tr = oracle.run(ops[:k], n, out=psi)
+    dt = time.perf_counter() - t0
+    assert tr.status == 0
+    ups = k * float(1 << n) / dt
+    return ups, f"first {k} gates (gate-only prefix) of the n={n} program, FP64, one trajectory", \
+        oracle.get_threads(), dt
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on the host cores, same metric and config."""
+    if rank != 0:
+        return
+    per_step = max(1.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    desc = threads = None
+    for i in range(args.warmup + args.steps):
+        ups, desc, threads, dt = oracle_sample(args.n, args.dtype, per_step)
+        if i >= args.warmup:
+            vals.append((ups, dt))
+    ups = statistics.median(v for v, _ in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.median(d for _, d in vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(args.n, args.dtype), "n": args.n},
+        "cpu_baseline": {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import sv
+
+    n, dtype = args.n, args.dtype
+    c = circuit(n, dtype)
+    st = sv.State(n, dtype)
+    prog = st.prepare(c.ops)
+    stats = prog.stats
+    upd = float(stats["gates"] + stats["draws"]) * float(1 << n)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        st.launch(prog, seed=0, shot=1000 + i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    st.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        st.launch(prog, seed=0, shot=i)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof = st.profile_read()
+    st.profile(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = upd * world / (ms / 1000.0)
+
+    # end to end through the public API with host buffers, plan lowered + copied each step
+    e2e = None
+    if not args.no_e2e:
+        st.set_cache(False)
+        st.run(c.ops, seed=0, shot=0)  # warm
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            st.run(c.ops, seed=0, shot=i)  # waits for the classical register
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        st.set_cache(True)
+        e2e = {"value": upd * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(stats["plan_bytes"]), "d2h_bytes_per_step": 8,
+               "ms_per_step": dt * 1000.0}
+
+    peaks, kind = measured_peaks()
+    achieved = prof["bytes"] / (prof["ms"] / 1000.0) / 1e9 if prof["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_pass",
+                "peak_kind": f"of {kind}", "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
+                "avg_launch_ms": prof["ms"] / max(1, prof["launches"])}
+    if dtype == "c128":
+        roofline["note"] = "complex128 sweeps are FP64-ALU-bound on GB300"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ups, desc, threads, dt = oracle_sample(n, dtype, args.cpu_seconds)
+        cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(n, dtype), "n": n, "state": dtype,
+                       "gates_per_step": stats["gates"], "draws_per_step": stats["draws"],
+                       "passes_per_step": stats["passes"], "tile_bits": stats["tile_bits"],
+                       "low_bits": stats["low_bits"], "l2": "inputs larger than L2 (state 2^n amplitudes)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (2 + stats["passes"]), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    st.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

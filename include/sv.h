@@ -1,0 +1,241 @@
+/*
+ * sv.h -- C-ABI of libsv, a GB300 (sm_103a) state-vector simulator for dynamic
+ * circuits: mid-circuit measurement, reset, if/else on classical predicates
+ * and bounded loops, with feed-forward decided on the GPU.
+ *
+ * The operations follow the paper's statement of the problem (arXiv
+ * 2604.11599): OpenQASM 3.0 programs with "classical control structures
+ * (conditionals and bounded loops)" and mid-circuit measurement (Abstract);
+ * `if` statements executed as "true classical feedforward rather than
+ * pre-calculated branching" (Sec. III-C); `input` parameters resolved at run
+ * time so that a kernel is compiled once and run many times (Sec. III-D);
+ * energies <H> for VQE (Sec. IV-A.2, IV-D); repeated shots (Sec. IV-C).
+ *
+ * Conventions (the paper is silent on them):
+ *   - qubit q is bit q of the amplitude index (little-endian); classical bit
+ *     j is bit j of a 64-bit register (creg); unwritten bits read 0;
+ *   - amplitudes are interleaved (re, im): SV_C64 = 2 x float, SV_C128 =
+ *     2 x double, 2^n of them, contiguous;
+ *   - a measurement of qubit q draws u = Philox4x64-10(key = (seed,
+ *     stream_id), counter = (shot, m, 0, 0)) word 0, u = (w >> 11) * 2^-53,
+ *     where m counts the measure/reset ops executed so far in the
+ *     trajectory; outcome = 1 iff u >= p0/(p0+p1); the state is projected
+ *     and scaled by 1/sqrt(p_outcome);
+ *   - a terminal sample of shot s uses counter (s, 2^32, 0, 0) and returns
+ *     the smallest index i with CDF_i > u * CDF_last.
+ *
+ * Errors: every call returns an sv_status and never throws; sv_last_error()
+ * gives a thread-local message for the last failing call on the calling
+ * thread.  After a failed call the handle stays valid but the state's
+ * contents are undefined.
+ *
+ * Streams: every call that touches the GPU is enqueued on the stream bound
+ * with sv_bind_stream (default: the legacy default stream) and returns
+ * without waiting, unless it has a host output (creg_out, sample output,
+ * expectation values, amplitudes), in which case it waits for that output.
+ */
+#ifndef LIBSV_SV_H_
+#define LIBSV_SV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+typedef enum {
+  SV_OK = 0,
+  SV_ERR_ARG = -1,          /* invalid argument or malformed op list          */
+  SV_ERR_OOM = -2,          /* device or host allocation failed               */
+  SV_ERR_CUDA = -3,         /* a CUDA call failed                             */
+  SV_ERR_TIMEOUT = -4,      /* a bounded device wait ran out                  */
+  SV_ERR_UNSUPPORTED = -5,  /* valid but not supported (e.g. unroll too large)*/
+  SV_ERR_NUMERIC = -6       /* a measurement saw a zero-norm state            */
+} sv_status;
+
+/* op kinds of the flat IR */
+enum { SV_GATE = 1, SV_DENSE = 2, SV_MEASURE = 3, SV_RESET = 4, SV_COND = 5, SV_LOOP = 6 };
+
+/* standard gates (OpenQASM 3 stdgates meanings; Sec. III-B maps them one-to-one) */
+enum {
+  SV_I = 0, SV_H, SV_X, SV_Y, SV_Z, SV_S, SV_SDG, SV_T, SV_TDG, SV_SX, SV_RX, SV_RY, SV_RZ,
+  SV_P, SV_U, SV_CX, SV_CY, SV_CZ, SV_SWAP, SV_CP, SV_CRX, SV_CRY, SV_CRZ, SV_CH, SV_CU,
+  SV_GATE_COUNT
+};
+
+/*
+ * One record of the flat, pre-order IR (120 bytes).
+ *   GATE    gate on q[0..] (controlled gates: q[0] control, q[1] target).
+ *           Angle i = pidx[i] >= 0 ? angle[i] * params[pidx[i]] : angle[i]
+ *           (U / CU use angles theta, phi, lambda).
+ *   DENSE   nq-qubit unitary on q[0..nq-1] (nq <= 4), row-major 2^nq x 2^nq
+ *           complex128 matrix at element dense_off of the dense pool
+ *           (sv_set_dense_pool); local bit r of its index is qubit q[r].
+ *   MEASURE measure q[0] into classical bit cbit (< 64).
+ *   RESET   measure q[0] (no classical write; it consumes a draw), then X if 1.
+ *   COND    run the next then_len records iff (creg & mask) == value, else the
+ *           else_len records after them (predicate read when the COND is reached).
+ *   LOOP    run the next body_len records loop_k times.
+ * Lengths count flat records, nested headers and bodies included.
+ */
+typedef struct sv_op {
+  uint16_t kind;
+  uint16_t gate;
+  uint32_t cbit;
+  int32_t q[8];
+  int32_t pidx[3];
+  uint32_t nq;
+  double angle[3];
+  uint64_t mask, value;
+  uint32_t then_len, else_len;
+  uint32_t loop_k, body_len;
+  uint64_t dense_off;
+} sv_op;
+
+/* Pauli string: X on q iff bit q of x_mask, Z iff bit q of z_mask, Y iff both. */
+typedef struct sv_pauli {
+  uint64_t x_mask, z_mask;
+  double coeff;
+} sv_pauli;
+
+/* one executed measure/reset of the last run (debug and parity record) */
+typedef struct sv_draw {
+  int32_t qubit, is_reset, outcome, pad;
+  double p0, p1, u; /* p0, p1 as the device saw them (unnormalised) */
+} sv_draw;
+
+typedef struct sv_state sv_state;     /* opaque, library-owned */
+typedef struct sv_program sv_program; /* opaque lowered program (plan) */
+
+typedef struct sv_program_stats {
+  uint64_t records;       /* IR records                                   */
+  uint64_t unrolled_ops;  /* gate + measure + reset ops after unrolling   */
+  uint64_t gates;         /* gates after unrolling (counted in updates/s) */
+  uint64_t draws;         /* measure + reset ops after unrolling          */
+  uint64_t passes;        /* state sweeps per run (without init)          */
+  uint64_t stages;        /* register stages over all passes              */
+  uint64_t flags;         /* device predicate slots                       */
+  int32_t tile_bits, low_bits;
+  uint64_t plan_bytes;    /* bytes of plan data copied to the device      */
+} sv_program_stats;
+
+/*
+ * Create a state of n qubits (1 <= n <= 34) in |0...0>.
+ *   dev_buf  NULL: the library allocates 2^n amplitudes on the current device.
+ *            Otherwise caller-owned device memory of `bytes` >= 2^max(n,4) *
+ *            amplitude size, which must outlive the handle (e.g. a torch tensor).
+ * On success *out receives the handle.  SV_ERR_ARG for bad n/dtype/size,
+ * SV_ERR_OOM if allocation fails.
+ */
+sv_status sv_create(int n, sv_dtype dtype, void* dev_buf, size_t bytes, sv_state** out);
+
+/* Release the handle and everything the library allocated for it (not dev_buf). */
+sv_status sv_destroy(sv_state* h);
+
+/* Enqueue all later work of h on this cudaStream_t (NULL: legacy default stream). */
+sv_status sv_bind_stream(sv_state* h, void* cuda_stream);
+
+/* Copy a host complex128 pool (interleaved re, im; n_complex entries) used by DENSE ops. */
+sv_status sv_set_dense_pool(sv_state* h, const double* pool, size_t n_complex);
+
+/*
+ * Lower an op list for this state's n and dtype.  The caller's ops are read
+ * during the call only.  SV_ERR_ARG for a malformed list (qubit >= n,
+ * duplicate qubits, cbit >= 64, lengths out of range, nesting > 64),
+ * SV_ERR_UNSUPPORTED if the unrolled program exceeds 2^22 ops or 2^20 predicates.
+ */
+sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out);
+
+/*
+ * Host-only lowering (no device touched): validates an op list for n qubits
+ * and reports the plan statistics the given tuning would produce (tile_bits,
+ * low_bits, max_pass_gates as in sv_set_tuning; 0 = default).
+ */
+sv_status sv_plan_info(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                       size_t n_complex, int tile_bits, int low_bits, int max_pass_gates, sv_program_stats* out);
+sv_status sv_program_free(sv_program* p);
+sv_status sv_program_info(const sv_program* p, sv_program_stats* out);
+
+/*
+ * Run one trajectory of a prepared program from |0...0> on the bound stream,
+ * with parameters already on the device (dev_params: n_params doubles, may be
+ * NULL if the program has no parameter references).  Asynchronous.
+ */
+sv_status sv_launch(sv_state* h, sv_program* p, const double* dev_params, size_t n_params,
+                    uint64_t seed, uint64_t stream_id, uint64_t shot);
+
+/*
+ * Prepare (cached by content) + copy params to the device + launch, then if
+ * creg_out is non-NULL wait and write the classical register there.
+ */
+sv_status sv_run(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
+                 uint64_t seed, uint64_t stream_id, uint64_t shot, uint64_t* creg_out);
+
+/* Classical register and draw record of the last run (waits for it). */
+sv_status sv_get_creg(sv_state* h, uint64_t* creg);
+sv_status sv_get_trace(sv_state* h, sv_draw* out, size_t max, size_t* n_out);
+
+/*
+ * `shots` shots of a program.  With MEASURE/RESET in the program, shot s runs
+ * its own trajectory (counter shot = s) and creg_out[s] receives its
+ * register; otherwise the program runs once.  bits_out (nullable) receives
+ * one terminal sample per shot (counter (s, 2^32)).  Waits for the outputs.
+ */
+sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
+                    uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
+                    uint64_t* bits_out);
+
+/* Terminal samples of the current state: out[s] for counter (shot0 + s, 2^32). */
+sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                          uint64_t* out);
+
+/*
+ * <psi| sum_t coeff_t P_t |psi> of the current state (FP64 accumulation).
+ * total (nullable) receives the sum, per_term (nullable, n_terms) each <P_t>.
+ */
+sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* total, double* per_term);
+
+/* Copy amplitudes [first, first+count) to / from host memory (amplitude-size elements). */
+sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count);
+sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count);
+
+/* Device pointer and byte size of the state (for zero-copy views). */
+sv_status sv_state_buffer(sv_state* h, void** dev_ptr, size_t* bytes);
+
+/* Planner tuning: tile bits (10..14), contiguous low bits (2..tile), max gates per pass; 0 = default. */
+sv_status sv_set_tuning(sv_state* h, int tile_bits, int low_bits, int max_pass_gates);
+
+/*
+ * Kernel timing of the state-sweep passes.  While enabled, every pass launch
+ * is bracketed by CUDA events on the bound stream.  sv_profile_read waits,
+ * then reports the summed event time (ms), the number of pass launches and
+ * their algorithmic bytes (state read + written once per storing pass, read
+ * once per read-only pass), and resets the counters.
+ */
+sv_status sv_profile(sv_state* h, int enable);
+sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, double* bytes);
+
+/*
+ * Program cache of sv_run / sv_sample (on by default): a repeated op list
+ * reuses its lowered plan.  With the cache off every call lowers the list
+ * and copies the plan to the device again.
+ */
+sv_status sv_set_cache(sv_state* h, int enable);
+
+/* Wait for all work of h. */
+sv_status sv_sync(sv_state* h);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* sv_last_error(void);
+
+/* Library version string. */
+const char* sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBSV_SV_H_ */

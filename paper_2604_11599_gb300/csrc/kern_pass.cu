@@ -1,0 +1,770 @@
+// kern_pass.cu -- gate matrices, state init and the fused tile-pass kernel.
+//
+// One pass sweeps the state once.  Each CTA walks its share of the 2^(n-m)
+// tiles; a tile is the 2^m amplitudes that share the values of the n-m qubits
+// outside the pass's tile set.  The tile is read with 16-byte coalesced loads
+// (runs of 2^L contiguous amplitudes), with any pending measurement
+// projector applied on the way in (the collapse and 1/sqrt(p)
+// renormalisation of the previous measurement group is fused into this load,
+// Fig. 2's "measurement collapses the state"), kept in XOR-swizzled shared
+// memory, and processed in stages: each thread pulls 16 amplitudes (four
+// register qubits) into registers, applies the stage's gates there and writes
+// them back.  If a measurement group follows, the |amp|^2 table of its
+// qubits is accumulated (FP32 within a warp for complex64, FP64 across
+// warps and CTAs) and the last CTA to finish draws the outcomes
+// (Philox4x64-10 keyed on seed, stream, shot and draw index), updates the
+// classical register and evaluates the feed-forward predicates that follow
+// (Sec. III-C) -- all on the device.
+#include <cstdio>
+
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace svk {
+using namespace svp;
+
+// ============================================================ gates on 16 registers
+// a[j] holds the amplitude whose register bits are j; template parameters
+// are register-bit positions, so every index below is a compile-time constant.
+
+template <int P, typename V>
+__device__ __forceinline__ void g_u(V* a, const V* m) {
+  const V m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = cmac2(m0, x, m1, y);
+    a[k] = cmac2(m2, x, m3, y);
+  }
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_r(V* a, const V* m) {
+  const auto r00 = m[0].x, r01 = m[1].x, r10 = m[2].x, r11 = m[3].x;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = mkc(fma(r00, x.x, r01 * y.x), fma(r00, x.y, r01 * y.y));
+    a[k] = mkc(fma(r10, x.x, r11 * y.x), fma(r10, x.y, r11 * y.y));
+  }
+}
+
+// RX: [c, -i s; -i s, c]
+template <int P, typename V>
+__device__ __forceinline__ void g_rx(V* a, const V* m) {
+  const auto c = m[0].x, s = m[1].x;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = mkc(fma(c, x.x, s * y.y), fma(c, x.y, -s * y.x));
+    a[k] = mkc(fma(s, x.y, c * y.x), fma(-s, x.x, c * y.y));
+  }
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_d(V* a, const V* m) {
+  const V d0 = m[0], d1 = m[1];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = cmul((j & (1 << P)) ? d1 : d0, a[j]);
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_x(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cu(V* a, const V* m) {
+  const V m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << C)) || (j & (1 << T))) continue;
+    const int k = j | (1 << T);
+    const V x = a[j], y = a[k];
+    a[j] = cmac2(m0, x, m1, y);
+    a[k] = cmac2(m2, x, m3, y);
+  }
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cx(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << C)) || (j & (1 << T))) continue;
+    const int k = j | (1 << T);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+template <int A, int B, typename V>
+__device__ __forceinline__ void g_cz(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if ((j & (1 << A)) && (j & (1 << B))) a[j] = mkc(-a[j].x, -a[j].y);
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cd(V* a, const V* m) {
+  const V d0 = m[0], d1 = m[1];
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j & (1 << C)) a[j] = cmul((j & (1 << T)) ? d1 : d0, a[j]);
+}
+
+template <int A, int B, typename V>
+__device__ __forceinline__ void g_swap(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << A)) || (j & (1 << B))) continue;
+    const int k = (j ^ (1 << A)) | (1 << B);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+// dense 4x4; matrix index bit 0 <-> register bit P0, bit 1 <-> P1
+template <int P0, int P1, typename V>
+__device__ __forceinline__ void g_u4(V* a, const V* m) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if ((j & (1 << P0)) || (j & (1 << P1))) continue;
+    const int i0 = j, i1 = j | (1 << P0), i2 = j | (1 << P1), i3 = j | (1 << P0) | (1 << P1);
+    const V v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
+    a[i0] = cadd(cmac2(m[0], v0, m[1], v1), cmac2(m[2], v2, m[3], v3));
+    a[i1] = cadd(cmac2(m[4], v0, m[5], v1), cmac2(m[6], v2, m[7], v3));
+    a[i2] = cadd(cmac2(m[8], v0, m[9], v1), cmac2(m[10], v2, m[11], v3));
+    a[i3] = cadd(cmac2(m[12], v0, m[13], v1), cmac2(m[14], v2, m[15], v3));
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void g_d16(V* a, const V* m) {
+  V w[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    V acc = mkc(decltype(a[0].x)(0), decltype(a[0].x)(0));
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) acc = cadd(acc, cmac2(m[r * 16 + c], a[c], m[r * 16 + c + 1], a[c + 1]));
+    w[r] = acc;
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) a[r] = w[r];
+}
+
+#define SVK_1Q(FN)                  \
+  switch (g.p0) {                   \
+    case 0: FN<0>(a, mt); break;    \
+    case 1: FN<1>(a, mt); break;    \
+    case 2: FN<2>(a, mt); break;    \
+    default: FN<3>(a, mt); break;   \
+  }
+
+#define SVK_2Q(FN)                     \
+  switch (g.p0 * 4 + g.p1) {           \
+    case 1: FN<0, 1>(a, mt); break;    \
+    case 2: FN<0, 2>(a, mt); break;    \
+    case 3: FN<0, 3>(a, mt); break;    \
+    case 4: FN<1, 0>(a, mt); break;    \
+    case 6: FN<1, 2>(a, mt); break;    \
+    case 7: FN<1, 3>(a, mt); break;    \
+    case 8: FN<2, 0>(a, mt); break;    \
+    case 9: FN<2, 1>(a, mt); break;    \
+    case 11: FN<2, 3>(a, mt); break;   \
+    case 12: FN<3, 0>(a, mt); break;   \
+    case 13: FN<3, 1>(a, mt); break;   \
+    default: FN<3, 2>(a, mt); break;   \
+  }
+
+template <typename V>
+__device__ __forceinline__ void apply_gate(V* a, const DGate& g, const V* mt) {
+  switch (g.op) {
+    case OP_U: SVK_1Q(g_u) break;
+    case OP_R: SVK_1Q(g_r) break;
+    case OP_RX: SVK_1Q(g_rx) break;
+    case OP_D: SVK_1Q(g_d) break;
+    case OP_X: SVK_1Q(g_x) break;
+    case OP_CU: SVK_2Q(g_cu) break;
+    case OP_CX: SVK_2Q(g_cx) break;
+    case OP_CZ: SVK_2Q(g_cz) break;
+    case OP_CD: SVK_2Q(g_cd) break;
+    case OP_SWAP: SVK_2Q(g_swap) break;
+    case OP_U4: SVK_2Q(g_u4) break;
+    case OP_D16: g_d16(a, mt); break;
+    default: break;
+  }
+}
+
+// ============================================================ gate matrices (FP64)
+// OpenQASM 3 standard-gate definitions; m = [m00 m01; m10 m11] of the target.
+__device__ void std_gate_2x2(int gate, const double* t, double2* m) {
+  const double h = 0.70710678118654752440;
+  double c, s, sp, cp, sl, cl;
+  for (int k = 0; k < 4; ++k) m[k] = make_double2(0, 0);
+  switch (gate) {
+    case SV_H: case SV_CH: m[0] = m[1] = m[2] = make_double2(h, 0); m[3] = make_double2(-h, 0); break;
+    case SV_X: case SV_CX: m[1] = m[2] = make_double2(1, 0); break;
+    case SV_Y: case SV_CY: m[1] = make_double2(0, -1); m[2] = make_double2(0, 1); break;
+    case SV_Z: case SV_CZ: m[0] = make_double2(1, 0); m[3] = make_double2(-1, 0); break;
+    case SV_S: m[0] = make_double2(1, 0); m[3] = make_double2(0, 1); break;
+    case SV_SDG: m[0] = make_double2(1, 0); m[3] = make_double2(0, -1); break;
+    case SV_T: m[0] = make_double2(1, 0); m[3] = make_double2(h, h); break;
+    case SV_TDG: m[0] = make_double2(1, 0); m[3] = make_double2(h, -h); break;
+    case SV_SX:
+      m[0] = m[3] = make_double2(0.5, 0.5);
+      m[1] = m[2] = make_double2(0.5, -0.5);
+      break;
+    case SV_RX: case SV_CRX:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = m[3] = make_double2(c, 0);
+      m[1] = m[2] = make_double2(0, -s);
+      break;
+    case SV_RY: case SV_CRY:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = m[3] = make_double2(c, 0);
+      m[1] = make_double2(-s, 0);
+      m[2] = make_double2(s, 0);
+      break;
+    case SV_RZ: case SV_CRZ:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = make_double2(c, -s);
+      m[3] = make_double2(c, s);
+      break;
+    case SV_P: case SV_CP:
+      sincos(t[0], &s, &c);
+      m[0] = make_double2(1, 0);
+      m[3] = make_double2(c, s);
+      break;
+    case SV_U: case SV_CU:
+      sincos(0.5 * t[0], &s, &c);
+      sincos(t[1], &sp, &cp);
+      sincos(t[2], &sl, &cl);
+      m[0] = make_double2(c, 0);
+      m[1] = make_double2(-cl * s, -sl * s);
+      m[2] = make_double2(cp * s, sp * s);
+      m[3] = make_double2((cp * cl - sp * sl) * c, (sp * cl + cp * sl) * c);
+      break;
+    default: m[0] = m[3] = make_double2(1, 0); break;
+  }
+}
+
+template <typename T>
+__global__ void k_prep(PrepArgs P) {
+  using V = typename CxT<T>::V;
+  V* mats = reinterpret_cast<V*>(P.mats);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < P.njobs) {
+    const DJob j = P.jobs[i];
+    if (j.kind == J_CONST) {
+      for (uint32_t k = 0; k < j.len; ++k)
+        mats[j.out + k] = mkc(T(P.consts[2 * (j.src + k)]), T(P.consts[2 * (j.src + k) + 1]));
+    } else {
+      double t[3];
+      for (int k = 0; k < 3; ++k) {
+        if (j.pidx[k] >= 0) {
+          if (uint64_t(j.pidx[k]) < P.n_params) t[k] = j.angle[k] * P.params[j.pidx[k]];
+          else { t[k] = 0; P.ctrl->status = SV_ERR_ARG; }
+        } else {
+          t[k] = j.angle[k];
+        }
+      }
+      double2 m[4];
+      std_gate_2x2(j.gate, t, m);
+      switch (j.op) {
+        case OP_U: case OP_CU:
+          for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(m[k].y));
+          break;
+        case OP_R:
+          for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(0));
+          break;
+        case OP_RX:  // m00 = c, m01 = -i s
+          mats[j.out] = mkc(T(m[0].x), T(0));
+          mats[j.out + 1] = mkc(T(-m[1].y), T(0));
+          break;
+        case OP_D: case OP_CD:
+          mats[j.out] = mkc(T(m[0].x), T(m[0].y));
+          mats[j.out + 1] = mkc(T(m[3].x), T(m[3].y));
+          break;
+        default: break;
+      }
+    }
+  }
+  if (i == 0) {
+    Ctrl* C = P.ctrl;
+    C->creg = 0;
+    C->seed = P.seed;
+    C->stream = P.stream;
+    C->shot = P.shot;
+    C->m = 0;
+    C->pm = C->pv = C->px = 0;
+    C->ps = 1.0;
+    C->ticket = 0;
+    C->n_trace = 0;
+    if (C->status == 0) C->status = 0;
+    for (int k = 0; k < P.ninit; ++k) {  // COND evaluations before the first measurement
+      const DScalar s = P.init[k];
+      const bool par = s.flag < 0 || P.flags[s.flag];
+      const bool pred = (0ull & s.mask) == s.value;
+      P.flags[s.f_then] = par && pred;
+      if (s.f_else >= 0) P.flags[s.f_else] = par && !pred;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_init_state(void* state, uint64_t n_amp) {
+  using V = typename CxT<T>::V;
+  V* s = reinterpret_cast<V*>(state);
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_amp; i += stride)
+    s[i] = (i == 0) ? mkc(T(1), T(0)) : mkc(T(0), T(0));
+}
+
+// ============================================================ the pass kernel
+
+__device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
+  uint64_t out = 0;
+  for (uint64_t bb = 1; mask; bb <<= 1) {
+    const uint64_t low = mask & (~mask + 1);
+    if (v & bb) out |= low;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+__device__ __forceinline__ uint64_t pext64(uint64_t v, uint64_t mask) {
+  uint64_t out = 0, bb = 1;
+  for (; mask; bb <<= 1) {
+    const uint64_t low = mask & (~mask + 1);
+    if (v & low) out |= bb;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+// 16 per-lane values -> lane holds the warp sum of slot(lane); 16 shuffles.
+template <typename A>
+__device__ __forceinline__ A warp_transpose_reduce16(A (&v)[16], int lane) {
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int o = 16 >> st, h = 8 >> st;
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const A send = up ? v[i] : v[i + h];
+      const A keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int transpose_slot(int lane) {
+  return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PASS_THREADS) k_pass(PassArgs A, int pi) {
+  using V = typename CxT<T>::V;
+  using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tile = reinterpret_cast<V*>(smem_raw);
+  __shared__ DPass sp;
+  __shared__ DGate sg[MAX_PASS_GATES];
+  __shared__ uint8_t sact[MAX_PASS_GATES];
+  __shared__ __align__(16) V smat[MAX_PASS_MAT];
+  __shared__ uint64_t schunk[512];
+  __shared__ double ctab[16];
+  __shared__ double wsum[PASS_THREADS / 32][16];
+  __shared__ double tile16[16];
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bd = blockDim.x;
+  if (tid == 0) sp = A.passes[pi];
+  if (tid < 16) ctab[tid] = 0.0;
+  __syncthreads();
+  const int m = sp.m, L = sp.L, n = A.n;
+
+  int act_any = 0;
+  for (int g = tid; g < int(sp.ng); g += bd) {
+    const DGate d = A.gates[sp.g0 + g];
+    sg[g] = d;
+    const uint8_t on = d.flag < 0 ? 1 : (A.flags[d.flag] ? 1 : 0);
+    sact[g] = on;
+    act_any |= on;
+  }
+  const bool any_gate = __syncthreads_or(act_any) != 0;
+  int need = 0;
+  if (sp.gk) {
+    if (sp.group_always) need = 1;
+    else
+      for (int c = tid; c < int(sp.nc); c += bd) {
+        const DScalar s = A.scalars[sp.c0 + c];
+        if (s.kind != S_COND && (s.flag < 0 || A.flags[s.flag])) need = 1;
+      }
+  }
+  const bool needed = __syncthreads_or(need) != 0;
+
+  const Ctrl* C = A.ctrl;
+  const uint64_t pm = C->pm, pv = C->pv, px = C->px;
+  const double ps = C->ps;
+  const bool ident = (pm == 0 && px == 0 && ps == 1.0);
+  const bool do_store = any_gate || (sp.flush && !ident);
+  const bool do_work = do_store || needed;
+  const bool need_ticket = sp.nc > 0 || (do_store && !ident);
+
+  if (do_work) {
+    if (any_gate)
+      for (int i = tid; i < int(sp.nmat); i += bd) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
+    const int hb = m - L;
+    for (int c = tid; c < (1 << hb); c += bd) {
+      uint64_t o = 0;
+      for (int k = 0; k < hb; ++k)
+        if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
+      schunk[c] = o;
+    }
+    __syncthreads();
+
+    uint64_t tmask = 0;
+    for (int j = 0; j < m; ++j) tmask |= 1ull << sp.tq[j];
+    const uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t omask = full & ~tmask;
+    const uint64_t ntiles = 1ull << (n - m);
+    const uint64_t xo = px & omask;  // part of the pending X that moves whole tiles
+    const bool pair = xo != 0;
+    const uint64_t xt = pair ? pext64(xo, omask) : 0;
+    const int hbit = pair ? __ffsll((long long)xt) - 1 : 0;
+    const uint64_t nunits = pair ? (ntiles >> 1) : ntiles;
+    const T sc = T(ps);
+    const int ngrp = 1 << (m - REG_BITS);
+    const uint32_t kmask = (1u << sp.kin) - 1;
+
+    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+      uint64_t tl[2];
+      int cnt = 1;
+      if (!pair) {
+        tl[0] = u;
+      } else {
+        const uint64_t lo = u & ((1ull << hbit) - 1);
+        const uint64_t t0 = ((u >> hbit) << (hbit + 1)) | lo;
+        const uint64_t t1 = t0 ^ xt;
+        const uint64_t b0 = pdep64(t0, omask);
+        const bool t0_reads = (((b0 ^ px) & pm & omask) == (pv & omask));
+        tl[0] = t0_reads ? t0 : t1;  // the tile that reads its partner goes first
+        tl[1] = t0_reads ? t1 : t0;
+        cnt = 2;
+      }
+      for (int k = 0; k < cnt; ++k) {
+        const uint64_t base = pdep64(tl[k], omask);
+        const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
+
+        // ---- load (with the pending projector)
+        if constexpr (sizeof(T) == 4) {
+          const int nvec = 1 << (m - 1), vl = L - 1;
+          const float4* gs = reinterpret_cast<const float4*>(A.state);
+          for (int v = tid; v < nvec; v += bd) {
+            const uint32_t ch = uint32_t(v) >> vl, w = uint32_t(v) & ((1u << vl) - 1);
+            const uint32_t loc = (ch << L) | (w << 1);
+            const uint64_t gi = base | schunk[ch] | (uint64_t(w) << 1);
+            float2 x0, x1;
+            if (zero_tile) {
+              x0 = x1 = make_float2(0.f, 0.f);
+            } else if (ident) {
+              const float4 q = __ldcg(gs + (gi >> 1));
+              x0 = make_float2(q.x, q.y);
+              x1 = make_float2(q.z, q.w);
+            } else {
+              const uint64_t s0 = gi ^ px;
+              const bool ok0 = (s0 & pm) == pv, ok1 = ((s0 ^ 1ull) & pm) == pv;
+              float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (ok0 || ok1) q = __ldcg(gs + (s0 >> 1));
+              const float2 e0 = make_float2(q.x, q.y), e1 = make_float2(q.z, q.w);
+              x0 = (s0 & 1) ? e1 : e0;
+              x1 = (s0 & 1) ? e0 : e1;
+              x0 = ok0 ? make_float2(x0.x * sc, x0.y * sc) : make_float2(0.f, 0.f);
+              x1 = ok1 ? make_float2(x1.x * sc, x1.y * sc) : make_float2(0.f, 0.f);
+            }
+            const uint32_t p = swz<T>(loc);
+            float4* dst = reinterpret_cast<float4*>(tile + (p & ~1u));
+            *dst = (p & 1) ? make_float4(x1.x, x1.y, x0.x, x0.y) : make_float4(x0.x, x0.y, x1.x, x1.y);
+          }
+        } else {
+          const int nvec = 1 << m;
+          const double2* gs = reinterpret_cast<const double2*>(A.state);
+          for (int v = tid; v < nvec; v += bd) {
+            const uint32_t ch = uint32_t(v) >> L, w = uint32_t(v) & ((1u << L) - 1);
+            const uint32_t loc = (ch << L) | w;
+            const uint64_t gi = base | schunk[ch] | uint64_t(w);
+            double2 x;
+            if (zero_tile) {
+              x = make_double2(0, 0);
+            } else if (ident) {
+              x = __ldcg(gs + gi);
+            } else {
+              const uint64_t s0 = gi ^ px;
+              if ((s0 & pm) == pv) {
+                x = __ldcg(gs + s0);
+                x.x *= sc;
+                x.y *= sc;
+              } else {
+                x = make_double2(0, 0);
+              }
+            }
+            tile[swz<T>(loc)] = x;
+          }
+        }
+        __syncthreads();
+
+        // ---- gate stages
+        if (any_gate) {
+          for (uint32_t si = 0; si < sp.ns; ++si) {
+            const DStage st = A.stages[sp.s0 + si];
+            uint32_t roff[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) roff[j] = swz<T>(deposit_bits(uint32_t(j), st.reg, REG_BITS));
+            for (int grp = tid; grp < ngrp; grp += bd) {
+              const uint32_t b = swz<T>(deposit_bits(uint32_t(grp), st.thr, m - REG_BITS));
+              V a[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) a[j] = tile[b ^ roff[j]];
+              for (int g = st.g0; g < st.g0 + st.ng; ++g)
+                if (sact[g]) apply_gate(a, sg[g], smat + sg[g].mat);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) tile[b ^ roff[j]] = a[j];
+            }
+            __syncthreads();
+          }
+        }
+
+        // ---- measurement-group table
+        if (needed) {
+          Acc acc[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
+          uint32_t roff[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) roff[j] = swz<T>(deposit_bits(uint32_t(j), sp.red_reg, REG_BITS));
+          for (int grp = tid; grp < ngrp; grp += bd) {
+            const uint32_t b = swz<T>(deposit_bits(uint32_t(grp), sp.red_thr, m - REG_BITS));
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const V x = tile[b ^ roff[j]];
+              acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
+            }
+          }
+          const Acc r = warp_transpose_reduce16(acc, lane);
+          if ((lane & 1) == 0) wsum[warp][transpose_slot(lane)] = double(r);
+          __syncthreads();
+          if (tid < 16) {
+            double s = 0;
+            for (int w = 0; w < bd / 32; ++w) s += wsum[w][tid];
+            tile16[tid] = s;
+          }
+          __syncthreads();
+          if (tid < (1 << sp.kin)) {
+            uint32_t ob = 0;
+            for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
+            double s = 0;
+            for (int j = 0; j < 16; ++j)
+              if ((uint32_t(j) & kmask) == uint32_t(tid)) s += tile16[j];
+            ctab[tid | (ob << sp.kin)] += s;
+          }
+        }
+
+        // ---- store
+        if (do_store) {
+          if constexpr (sizeof(T) == 4) {
+            const int nvec = 1 << (m - 1), vl = L - 1;
+            float4* gs = reinterpret_cast<float4*>(A.state);
+            for (int v = tid; v < nvec; v += bd) {
+              const uint32_t ch = uint32_t(v) >> vl, w = uint32_t(v) & ((1u << vl) - 1);
+              const uint32_t loc = (ch << L) | (w << 1);
+              const uint64_t gi = base | schunk[ch] | (uint64_t(w) << 1);
+              const uint32_t p = swz<T>(loc);
+              const float4 q = *reinterpret_cast<const float4*>(tile + (p & ~1u));
+              __stcg(gs + (gi >> 1), (p & 1) ? make_float4(q.z, q.w, q.x, q.y) : q);
+            }
+          } else {
+            const int nvec = 1 << m;
+            double2* gs = reinterpret_cast<double2*>(A.state);
+            for (int v = tid; v < nvec; v += bd) {
+              const uint32_t ch = uint32_t(v) >> L, w = uint32_t(v) & ((1u << L) - 1);
+              const uint32_t loc = (ch << L) | w;
+              const uint64_t gi = base | schunk[ch] | uint64_t(w);
+              __stcg(gs + gi, tile[swz<T>(loc)]);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
+  if (!need_ticket) return;
+  if (needed && tid < 16) A.partials[blockIdx.x * 16 + tid] = ctab[tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&A.ctrl->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (needed && tid < 16) {
+    double s = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(A.partials + b * 16 + tid);
+    ctab[tid] = s;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+
+  // ---- scalar phase: draws, classical register, predicates (one thread)
+  Ctrl* W = A.ctrl;
+  uint64_t creg = W->creg, mc = W->m;
+  uint64_t npm = do_store ? 0 : pm, npv = do_store ? 0 : pv, npx = do_store ? 0 : px;
+  double nps = do_store ? 1.0 : ps;
+  double tab[16];
+  for (int e = 0; e < 16; ++e) tab[e] = ctab[e];
+  const int tsize = 1 << sp.gk;
+  bool drew = false;
+  for (uint32_t c = 0; c < sp.nc; ++c) {
+    const DScalar s = A.scalars[sp.c0 + c];
+    if (s.kind == S_COND) {
+      const bool par = s.flag < 0 || A.flags[s.flag];
+      const bool pred = (creg & s.mask) == s.value;
+      A.flags[s.f_then] = (par && pred) ? 1 : 0;
+      if (s.f_else >= 0) A.flags[s.f_else] = (par && !pred) ? 1 : 0;
+      continue;
+    }
+    if (!(s.flag < 0 || A.flags[s.flag])) continue;
+    double p0 = 0, p1 = 0;
+    for (int e = 0; e < tsize; ++e) {
+      if ((e >> s.tbit) & 1) p1 += tab[e];
+      else p0 += tab[e];
+    }
+    const double u = draw_uniform(W->seed, W->stream, W->shot, mc);
+    int o = 0;
+    if (!(p0 + p1 > 0)) W->status = SV_ERR_NUMERIC;
+    else o = (u >= p0 / (p0 + p1)) ? 1 : 0;
+    if (W->n_trace < MAX_TRACE) {
+      DTrace& tr = A.trace[W->n_trace];
+      tr.qubit = int(s.qubit);
+      tr.is_reset = s.kind == S_RESET;
+      tr.outcome = o;
+      tr.pad = 0;
+      tr.p0 = p0;
+      tr.p1 = p1;
+      tr.u = u;
+      W->n_trace = W->n_trace + 1;
+    }
+    ++mc;
+    const int bt = 1 << s.tbit;
+    for (int e = 0; e < tsize; ++e)
+      if (((e >> s.tbit) & 1) != o) tab[e] = 0;
+    if (s.kind == S_RESET && o)
+      for (int e = 0; e < tsize; ++e)
+        if (e & bt) {
+          tab[e ^ bt] = tab[e];
+          tab[e] = 0;
+        }
+    if (s.kind == S_MEASURE) creg = (creg & ~(1ull << s.cbit)) | (uint64_t(o) << s.cbit);
+    const uint64_t qb = 1ull << s.qubit;
+    const uint64_t xq = (npx >> s.qubit) & 1ull;
+    npm |= qb;
+    npv = (npv & ~qb) | ((uint64_t(o) ^ xq) << s.qubit);
+    if (s.kind == S_RESET && o) npx ^= qb;
+    drew = true;
+  }
+  if (drew) {
+    double mass = 0;
+    for (int e = 0; e < tsize; ++e) mass += tab[e];
+    if (mass > 0) nps *= 1.0 / sqrt(mass);
+    else W->status = SV_ERR_NUMERIC;
+  }
+  W->creg = creg;
+  W->m = mc;
+  W->pm = npm;
+  W->pv = npv;
+  W->px = npx;
+  W->ps = nps;
+  W->ticket = 0;
+  __threadfence();
+}
+
+// ============================================================ host launchers
+
+template <typename T>
+static cudaError_t launch_pass_t(const PassArgs& a, int pi, int grid, int m, cudaStream_t s) {
+  using V = typename CxT<T>::V;
+  const size_t smem = (size_t(1) << m) * sizeof(V);
+  k_pass<T><<<grid, PASS_THREADS, smem, s>>>(a, pi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s) {
+  return dtype == SV_C64 ? launch_pass_t<float>(a, pi, grid, m, s) : launch_pass_t<double>(a, pi, grid, m, s);
+}
+
+cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s) {
+  const int blocks = p.njobs > 0 ? (p.njobs + 255) / 256 : 1;
+  if (dtype == SV_C64) k_prep<float><<<blocks, 256, 0, s>>>(p);
+  else k_prep<double><<<blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s) {
+  const uint64_t want = (n_amp + 255) / 256;
+  const int blocks = int(want < uint64_t(sms) * 8 ? want : uint64_t(sms) * 8);
+  if (dtype == SV_C64) k_init_state<float><<<blocks, 256, 0, s>>>(state, n_amp);
+  else k_init_state<double><<<blocks, 256, 0, s>>>(state, n_amp);
+  return cudaGetLastError();
+}
+
+cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm) {
+  static int cache[2][MAX_TILE_BITS + 1] = {};
+  static bool attr_set[2] = {false, false};
+  const int d = dtype == SV_C64 ? 0 : 1;
+  int& c = cache[d][m];
+  if (c) {
+    *blocks_per_sm = c;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (dtype == SV_C64) {
+    if (!attr_set[d])
+      e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int((size_t(1) << MAX_TILE_BITS) * sizeof(float2)));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass<float>, PASS_THREADS,
+                                                        (size_t(1) << m) * sizeof(float2));
+  } else {
+    if (!attr_set[d])
+      e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int((size_t(1) << MAX_TILE_BITS) * sizeof(double2)));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass<double>, PASS_THREADS,
+                                                        (size_t(1) << m) * sizeof(double2));
+  }
+  if (e == cudaSuccess) attr_set[d] = true;
+  if (c < 1) c = 1;
+  *blocks_per_sm = c;
+  return e;
+}
+
+}  // namespace svk

@@ -1,0 +1,71 @@
+// kernels.h -- host-side launchers of the libsv kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sv.h"
+#include "sv_plan.h"
+
+namespace svk {
+
+struct PassArgs {
+  void* state;
+  const svp::DPass* passes;
+  const svp::DGate* gates;
+  const svp::DStage* stages;
+  const svp::DScalar* scalars;
+  const void* mats;
+  uint8_t* flags;
+  svp::Ctrl* ctrl;
+  svp::DTrace* trace;
+  double* partials;  // [grid][16]
+  int n;             // simulated qubits
+};
+
+struct PrepArgs {
+  const svp::DJob* jobs;
+  int njobs;
+  const double* params;
+  uint64_t n_params;
+  const double* consts;
+  void* mats;
+  svp::Ctrl* ctrl;
+  const svp::DScalar* init;
+  int ninit;
+  uint8_t* flags;
+  uint64_t seed, stream, shot;
+};
+
+cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s);
+cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s);
+cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s);
+cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm);
+
+// terminal sampling: block sums -> scan -> per-shot search
+struct SampleArgs {
+  const void* state;
+  int n;                 // simulated qubits
+  int n_logical;
+  double* block_sums;    // [nblocks]
+  double* block_prefix;  // [nblocks] exclusive prefix; [nblocks] total at the end
+  uint64_t shots, seed, stream, shot0;
+  uint64_t* out;         // [shots]
+};
+cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t s);
+uint64_t sample_blocks(int n);
+
+// Pauli expectation values of one group of terms sharing an X mask
+struct ExpvalArgs {
+  const void* state;
+  int n;
+  uint64_t x_mask;
+  const uint64_t* z_masks;  // [nterms]
+  const int* phase;         // [nterms] i^phase factor (|x & z| mod 4)
+  int nterms;               // <= 32
+  double* partials;         // [grid][32]
+  double* out;              // [nterms] (written by the last CTA)
+  unsigned* ticket;
+};
+cudaError_t launch_expval_group(int dtype, const ExpvalArgs& a, int grid, cudaStream_t s);
+
+}  // namespace svk

@@ -1,0 +1,607 @@
+// planner.cpp -- lowering of the flat IR (include/sv.h) into device passes.
+//
+// 1. Unroll: COND/LOOP records are interpreted into a straight item list in
+//    which every gate/measure/reset carries the predicate flag of its
+//    enclosing branch and every COND becomes a flag-evaluation item.  The
+//    flags are evaluated on the device from the classical register when the
+//    COND is reached, so branches are decided by feed-forward on the GPU and
+//    never duplicated into outcome-specific copies (Sec. III-C); loops
+//    (Abstract: "bounded loops") are repeated.
+// 2. Segment: a measurement group is a run of measure/reset items with no
+//    gate between them on at most four distinct qubits.  The gates before a
+//    group are swept in passes; the last pass also accumulates the group's
+//    joint |amp|^2 table, and the group's draws, plus every COND evaluation
+//    up to the next group (the register cannot change in between), run as
+//    the scalar phase after that pass.
+// 3. Fuse: gates are packed greedily (in dependency order) into passes whose
+//    tile holds m qubits (the L lowest plus gathered higher ones), and each
+//    pass into stages of four register qubits.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace svp {
+namespace {
+
+enum ItemKind { I_GATE = 0, I_MEAS, I_RESET, I_COND };
+
+struct Item {
+  ItemKind kind = I_GATE;
+  int flag = -1;  // predicate flag of the enclosing branch; COND: parent flag
+  // gates
+  uint8_t op = OP_NONE;
+  int nq = 0;
+  int q[4] = {-1, -1, -1, -1};
+  int gate = -1;  // IR gate, or -1 for a dense record
+  int32_t pidx[3] = {-1, -1, -1};
+  double angle[3] = {0, 0, 0};
+  const double* dense = nullptr;  // row-major 2^k x 2^k complex (re, im)
+  // measure / reset
+  int qubit = -1;
+  uint32_t cbit = 0;
+  // cond
+  int f_then = -1, f_else = -1;
+  uint64_t mask = 0, value = 0;
+
+  uint64_t qmask() const {
+    uint64_t m = 0;
+    for (int i = 0; i < nq; ++i) m |= 1ull << q[i];
+    return m;
+  }
+};
+
+int gate_qubits(int g) { return (g >= SV_CX && g <= SV_CU) ? 2 : 1; }
+
+uint8_t gate_opcode(int g) {
+  switch (g) {
+    case SV_I: return OP_NONE;
+    case SV_H: case SV_RY: return OP_R;
+    case SV_X: return OP_X;
+    case SV_Y: case SV_SX: case SV_U: return OP_U;
+    case SV_RX: return OP_RX;
+    case SV_Z: case SV_S: case SV_SDG: case SV_T: case SV_TDG: case SV_P: case SV_RZ: return OP_D;
+    case SV_CX: return OP_CX;
+    case SV_CZ: return OP_CZ;
+    case SV_SWAP: return OP_SWAP;
+    case SV_CY: case SV_CH: case SV_CRX: case SV_CRY: case SV_CU: return OP_CU;
+    case SV_CP: case SV_CRZ: return OP_CD;
+    default: return OP_COUNT;
+  }
+}
+
+struct Unroller {
+  const sv_op* ops = nullptr;
+  size_t n_ops = 0;
+  int n = 0;
+  const double* pool = nullptr;
+  size_t pool_len = 0;
+  std::vector<Item> items;
+  uint32_t n_flags = 0;
+  uint64_t max_param = 0;
+  sv_status st = SV_OK;
+  std::string err;
+  static constexpr size_t kMaxItems = size_t(1) << 22;
+  static constexpr uint32_t kMaxFlags = 1u << 20;
+
+  bool fail(sv_status s, const std::string& m) {
+    if (st == SV_OK) {
+      st = s;
+      err = m;
+    }
+    return false;
+  }
+  bool qok(int32_t q) const { return q >= 0 && q < n; }
+
+  bool walk(size_t begin, size_t end, int flag, int depth) {
+    if (depth > 64) return fail(SV_ERR_ARG, "COND/LOOP nesting deeper than 64");
+    size_t i = begin;
+    while (i < end) {
+      const sv_op& o = ops[i];
+      switch (o.kind) {
+        case SV_GATE: {
+          if (o.gate >= SV_GATE_COUNT) return fail(SV_ERR_ARG, "unknown gate at record " + std::to_string(i));
+          Item it;
+          it.kind = I_GATE;
+          it.flag = flag;
+          it.gate = o.gate;
+          it.op = gate_opcode(o.gate);
+          it.nq = gate_qubits(o.gate);
+          for (int k = 0; k < it.nq; ++k) {
+            if (!qok(o.q[k])) return fail(SV_ERR_ARG, "qubit out of range at record " + std::to_string(i));
+            it.q[k] = o.q[k];
+          }
+          if (it.nq == 2 && it.q[0] == it.q[1]) return fail(SV_ERR_ARG, "repeated qubit at record " + std::to_string(i));
+          for (int k = 0; k < 3; ++k) {
+            it.pidx[k] = o.pidx[k];
+            it.angle[k] = o.angle[k];
+            if (o.pidx[k] >= 0) max_param = std::max<uint64_t>(max_param, uint64_t(o.pidx[k]) + 1);
+          }
+          if (it.op != OP_NONE) items.push_back(it);
+          ++i;
+          break;
+        }
+        case SV_DENSE: {
+          int k = int(o.nq);
+          if (k < 1 || k > 8) return fail(SV_ERR_ARG, "dense record needs 1..8 qubits");
+          if (k > 4) return fail(SV_ERR_UNSUPPORTED, "dense unitaries on more than 4 qubits");
+          Item it;
+          it.kind = I_GATE;
+          it.flag = flag;
+          it.nq = k;
+          uint64_t seen = 0;
+          for (int r = 0; r < k; ++r) {
+            if (!qok(o.q[r]) || ((seen >> o.q[r]) & 1)) return fail(SV_ERR_ARG, "bad dense qubits at record " + std::to_string(i));
+            seen |= 1ull << o.q[r];
+            it.q[r] = o.q[r];
+          }
+          uint64_t need = (1ull << k) * (1ull << k);
+          if (!pool || o.dense_off + need > pool_len) return fail(SV_ERR_ARG, "dense matrix outside the dense pool");
+          it.dense = pool + 2 * o.dense_off;
+          it.op = k == 1 ? OP_U : (k == 2 ? OP_U4 : OP_D16);
+          items.push_back(it);
+          ++i;
+          break;
+        }
+        case SV_MEASURE:
+        case SV_RESET: {
+          if (!qok(o.q[0])) return fail(SV_ERR_ARG, "measured qubit out of range at record " + std::to_string(i));
+          if (o.kind == SV_MEASURE && o.cbit >= 64) return fail(SV_ERR_ARG, "classical bit >= 64");
+          Item it;
+          it.kind = o.kind == SV_MEASURE ? I_MEAS : I_RESET;
+          it.flag = flag;
+          it.qubit = o.q[0];
+          it.cbit = o.cbit;
+          items.push_back(it);
+          ++i;
+          break;
+        }
+        case SV_COND: {
+          size_t t0 = i + 1, t1 = t0 + o.then_len, e1 = t1 + o.else_len;
+          if (e1 > end || t1 < t0 || e1 < t1) return fail(SV_ERR_ARG, "COND lengths exceed the enclosing block");
+          if (n_flags + 2 > kMaxFlags) return fail(SV_ERR_UNSUPPORTED, "too many predicates after unrolling");
+          Item it;
+          it.kind = I_COND;
+          it.flag = flag;
+          it.f_then = int(n_flags++);
+          it.f_else = o.else_len ? int(n_flags++) : -1;
+          it.mask = o.mask;
+          it.value = o.value;
+          items.push_back(it);
+          int ft = it.f_then, fe = it.f_else;
+          if (!walk(t0, t1, ft, depth + 1)) return false;
+          if (!walk(t1, e1, fe, depth + 1)) return false;
+          i = e1;
+          break;
+        }
+        case SV_LOOP: {
+          size_t b0 = i + 1, b1 = b0 + o.body_len;
+          if (b1 > end || b1 < b0) return fail(SV_ERR_ARG, "LOOP body exceeds the enclosing block");
+          for (uint32_t r = 0; r < o.loop_k; ++r)
+            if (!walk(b0, b1, flag, depth + 1)) return false;
+          i = b1;
+          break;
+        }
+        default:
+          return fail(SV_ERR_ARG, "unknown record kind at record " + std::to_string(i));
+      }
+      if (items.size() > kMaxItems) return fail(SV_ERR_UNSUPPORTED, "unrolled program exceeds 2^22 ops");
+    }
+    return true;
+  }
+};
+
+struct Segment {
+  std::vector<int> gates;    // item indices
+  std::vector<int> phase;    // scalar items after the last pass (program order)
+  uint64_t group_q = 0;      // qubits of the group's measure/reset items
+  bool has_group = false;
+};
+
+int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+// Orders the tile-local bits that receive thread-group index bits so that the
+// first lanes of a warp hit distinct shared-memory banks under the XOR
+// swizzle (bank bit of local bit p is p mod B).
+void order_thread_bits(const std::vector<int>& free_bits, int B, uint8_t* out) {
+  std::vector<int> rest(free_bits);
+  std::sort(rest.begin(), rest.end());
+  std::vector<int> order;
+  for (int r = 0; r < B; ++r) {
+    for (size_t k = 0; k < rest.size(); ++k) {
+      if (rest[k] % B == r) {
+        order.push_back(rest[k]);
+        rest.erase(rest.begin() + long(k));
+        break;
+      }
+    }
+  }
+  for (int b : rest) order.push_back(b);
+  for (size_t k = 0; k < order.size() && k < MAX_TILE_BITS; ++k) out[k] = uint8_t(order[k]);
+}
+
+struct Builder {
+  Plan& P;
+  const std::vector<Item>& items;
+  int B;  // swizzle bank bits (4: complex64, 3: complex128)
+  int max_pass_gates;
+
+  Builder(Plan& p, const std::vector<Item>& it, int b, int mpg) : P(p), items(it), B(b), max_pass_gates(mpg) {}
+
+  // complex constant pool helpers
+  uint32_t add_consts(const std::vector<double>& v) {
+    uint32_t off = uint32_t(P.consts.size() / 2);
+    P.consts.insert(P.consts.end(), v.begin(), v.end());
+    return off;
+  }
+
+  void emit_job_gate(const Item& it, uint32_t out) {
+    DJob j{};
+    j.kind = J_GATE;
+    j.op = it.op;
+    j.gate = uint8_t(it.gate);
+    for (int k = 0; k < 3; ++k) {
+      j.pidx[k] = it.pidx[k];
+      j.angle[k] = it.angle[k];
+    }
+    j.out = out;
+    P.jobs.push_back(j);
+  }
+
+  void emit_job_const(uint8_t op, const std::vector<double>& v, uint32_t out) {
+    DJob j{};
+    j.kind = J_CONST;
+    j.op = op;
+    j.src = add_consts(v);
+    j.len = uint32_t(v.size() / 2);
+    j.out = out;
+    P.jobs.push_back(j);
+  }
+
+  // matrix entries of an item once its stage register bits are known
+  int mat_len(const Item& it) const { return op_mat_len(it.op); }
+
+  // Emit one pass: `chosen` gate items, tile bits `tq` (m entries), optional phase.
+  void emit_pass(const std::vector<int>& chosen, const std::vector<int>& tq, const Segment* seg, bool flush) {
+    const int m = int(tq.size());
+    DPass ps{};
+    ps.m = uint8_t(m);
+    ps.L = uint8_t(P.L);
+    for (int j = 0; j < m; ++j) ps.tq[j] = uint8_t(tq[j]);
+    int loc[64];
+    for (int q = 0; q < 64; ++q) loc[q] = -1;
+    for (int j = 0; j < m; ++j) loc[tq[j]] = j;
+
+    ps.g0 = uint32_t(P.gates.size());
+    ps.s0 = uint32_t(P.stages.size());
+    ps.mat0 = P.n_mat;
+    uint32_t mat = 0;
+
+    // stages: greedy, four register bits, dependency order preserved
+    std::vector<int> rem(chosen);
+    while (!rem.empty()) {
+      uint32_t S = 0, blocked = 0;
+      std::vector<int> sg, left;
+      for (int idx : rem) {
+        const Item& it = items[idx];
+        uint32_t lm = 0;
+        for (int k = 0; k < it.nq; ++k) lm |= 1u << loc[it.q[k]];
+        if ((lm & blocked) || popc(S | lm) > REG_BITS) {
+          blocked |= lm;
+          left.push_back(idx);
+          continue;
+        }
+        S |= lm;
+        sg.push_back(idx);
+      }
+      rem.swap(left);
+      DStage st{};
+      st.g0 = uint16_t(P.gates.size() - ps.g0);
+      st.ng = uint16_t(sg.size());
+      // register bits: the stage's qubits, padded with the highest other local bits
+      std::vector<int> reg;
+      for (int j = 0; j < m; ++j)
+        if ((S >> j) & 1) reg.push_back(j);
+      for (int j = m - 1; j >= 0 && int(reg.size()) < REG_BITS; --j)
+        if (!((S >> j) & 1)) reg.push_back(j);
+      int rpos[MAX_TILE_BITS];
+      for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
+      for (int r = 0; r < REG_BITS; ++r) {
+        st.reg[r] = uint8_t(reg[r]);
+        rpos[reg[r]] = r;
+      }
+      std::vector<int> freeb;
+      for (int j = 0; j < m; ++j)
+        if (rpos[j] < 0) freeb.push_back(j);
+      order_thread_bits(freeb, B, st.thr);
+      for (int idx : sg) {
+        const Item& it = items[idx];
+        DGate g{};
+        g.op = it.op;
+        g.flag = it.flag;
+        g.p0 = uint8_t(rpos[loc[it.q[0]]]);
+        g.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;
+        g.mat = mat;
+        const uint32_t out = P.n_mat + mat;
+        if (it.gate >= 0) {
+          emit_job_gate(it, out);
+        } else if (it.op == OP_U || it.op == OP_U4) {
+          const int K = it.op == OP_U ? 2 : 4;
+          std::vector<double> v(it.dense, it.dense + 2 * K * K);
+          emit_job_const(it.op, v, out);
+        } else {  // OP_D16: expand onto the four register bits
+          const int k = it.nq;
+          int ri[4];
+          uint32_t gm = 0;
+          for (int r = 0; r < k; ++r) {
+            ri[r] = rpos[loc[it.q[r]]];
+            gm |= 1u << ri[r];
+          }
+          const int K = 1 << k;
+          std::vector<double> v(2 * 256, 0.0);
+          for (int a = 0; a < 16; ++a)
+            for (int b = 0; b < 16; ++b) {
+              if ((a & ~gm) != (b & ~gm)) continue;
+              int la = 0, lb = 0;
+              for (int r = 0; r < k; ++r) {
+                la |= ((a >> ri[r]) & 1) << r;
+                lb |= ((b >> ri[r]) & 1) << r;
+              }
+              v[2 * (a * 16 + b)] = it.dense[2 * (la * K + lb)];
+              v[2 * (a * 16 + b) + 1] = it.dense[2 * (la * K + lb) + 1];
+            }
+          emit_job_const(OP_D16, v, out);
+        }
+        mat += uint32_t(mat_len(it));
+        P.gates.push_back(g);
+      }
+      P.stages.push_back(st);
+    }
+    ps.ng = uint32_t(P.gates.size() - ps.g0);
+    ps.ns = uint32_t(P.stages.size() - ps.s0);
+    ps.nmat = mat;
+    P.n_mat += mat;
+    P.max_pass_mat = std::max(P.max_pass_mat, mat);
+    P.max_stages = std::max(P.max_stages, ps.ns);
+    P.max_gates = std::max(P.max_gates, ps.ng);
+
+    // group table and scalar phase
+    ps.c0 = uint32_t(P.scalars.size());
+    if (seg && seg->has_group) {
+      // table bits: group qubits inside the tile first (they become the
+      // reduction stage's register bits), then the ones outside
+      std::vector<int> in_q, out_q;
+      for (int q = 0; q < 64; ++q) {
+        if (!((seg->group_q >> q) & 1)) continue;
+        if (loc[q] >= 0) in_q.push_back(q);
+        else out_q.push_back(q);
+      }
+      ps.kin = uint8_t(in_q.size());
+      ps.gk = uint8_t(in_q.size() + out_q.size());
+      int tbit[64];
+      for (int q = 0; q < 64; ++q) tbit[q] = -1;
+      uint32_t used = 0;
+      std::vector<int> reg;
+      for (size_t k = 0; k < in_q.size(); ++k) {
+        tbit[in_q[k]] = int(k);
+        reg.push_back(loc[in_q[k]]);
+        used |= 1u << loc[in_q[k]];
+      }
+      for (size_t k = 0; k < out_q.size(); ++k) {
+        tbit[out_q[k]] = int(in_q.size() + k);
+        ps.outer_gq[k] = uint8_t(out_q[k]);
+      }
+      for (int j = m - 1; j >= 0 && int(reg.size()) < REG_BITS; --j)
+        if (!((used >> j) & 1)) {
+          reg.push_back(j);
+          used |= 1u << j;
+        }
+      for (int r = 0; r < REG_BITS; ++r) ps.red_reg[r] = uint8_t(reg[r]);
+      std::vector<int> freeb;
+      for (int j = 0; j < m; ++j)
+        if (!((used >> j) & 1)) freeb.push_back(j);
+      order_thread_bits(freeb, B, ps.red_thr);
+
+      // which flags are decided inside this phase
+      std::vector<int> decided_here;
+      bool always = false;
+      for (int idx : seg->phase) {
+        const Item& it = items[idx];
+        DScalar s{};
+        if (it.kind == I_COND) {
+          s.kind = S_COND;
+          s.flag = it.flag;
+          s.f_then = it.f_then;
+          s.f_else = it.f_else;
+          s.mask = it.mask;
+          s.value = it.value;
+          decided_here.push_back(it.f_then);
+          if (it.f_else >= 0) decided_here.push_back(it.f_else);
+        } else {
+          s.kind = it.kind == I_MEAS ? S_MEASURE : S_RESET;
+          s.flag = it.flag;
+          s.f_then = s.f_else = -1;
+          s.qubit = uint32_t(it.qubit);
+          s.cbit = it.cbit;
+          s.tbit = uint8_t(tbit[it.qubit]);
+          if (it.flag < 0 || std::find(decided_here.begin(), decided_here.end(), it.flag) != decided_here.end())
+            always = true;
+        }
+        P.scalars.push_back(s);
+      }
+      ps.group_always = always ? 1 : 0;
+    }
+    ps.nc = uint32_t(P.scalars.size() - ps.c0);
+    P.max_scalars = std::max(P.max_scalars, ps.nc);
+    ps.flush = flush ? 1 : 0;
+    P.passes.push_back(ps);
+  }
+
+  // Greedy fusion of a segment's gates into passes.
+  void emit_segment(const Segment& seg) {
+    const int n = P.n_int, m = P.m, L = P.L;
+    const uint64_t low = (L >= 64) ? ~0ull : ((1ull << L) - 1);
+    std::vector<int> rem(seg.gates);
+    if (rem.empty()) {
+      // a measurement group with no gate before it: an empty (read-only) pass
+      std::vector<int> tq;
+      uint64_t T = low;
+      for (int q = 0; q < n && popc(T) < m; ++q) {
+        if ((seg.group_q >> q) & 1) T |= 1ull << q;
+      }
+      for (int q = 0; q < n && popc(T) < m; ++q) T |= 1ull << q;
+      for (int q = 0; q < n; ++q)
+        if ((T >> q) & 1) tq.push_back(q);
+      emit_pass({}, tq, &seg, false);
+      return;
+    }
+    while (!rem.empty()) {
+      uint64_t T = low, blocked = 0;
+      std::vector<int> chosen, left;
+      uint32_t mat = 0;
+      const size_t cap = max_pass_gates > 0 ? size_t(max_pass_gates) : size_t(MAX_PASS_GATES);
+      for (int idx : rem) {
+        const Item& it = items[idx];
+        const uint64_t qm = it.qmask();
+        const uint32_t ml = uint32_t(op_mat_len(it.op));
+        if ((qm & blocked) || popc(T | qm) > m || chosen.size() >= cap || mat + ml > MAX_PASS_MAT) {
+          blocked |= qm;
+          left.push_back(idx);
+          continue;
+        }
+        T |= qm;
+        mat += ml;
+        chosen.push_back(idx);
+      }
+      rem.swap(left);
+      const bool last = rem.empty();
+      if (last && seg.has_group) {
+        // bring measured qubits into the tile when there is room
+        for (int q = 0; q < n && popc(T) < m; ++q)
+          if ((seg.group_q >> q) & 1) T |= 1ull << q;
+      }
+      for (int q = 0; q < n && popc(T) < m; ++q) T |= 1ull << q;
+      std::vector<int> tq;
+      for (int q = 0; q < n; ++q)
+        if ((T >> q) & 1) tq.push_back(q);
+      emit_pass(chosen, tq, last ? &seg : nullptr, false);
+    }
+  }
+};
+
+}  // namespace
+
+sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool, size_t dense_len,
+                     const Tuning& tune, Plan& P, std::string& err) {
+  P = Plan{};
+  if (n < 1 || n > 34) {
+    err = "n must be in 1..34";
+    return SV_ERR_ARG;
+  }
+  if (n_ops && !ops) {
+    err = "ops is NULL";
+    return SV_ERR_ARG;
+  }
+  P.n = n;
+  P.n_int = std::max(n, 4);
+  P.dtype = dtype;
+  int tb = tune.tile_bits > 0 ? tune.tile_bits : 12;
+  tb = std::min(std::max(tb, 10), MAX_TILE_BITS);
+  P.m = std::min(P.n_int, tb);
+  int lb = tune.low_bits > 0 ? tune.low_bits : (dtype == SV_C64 ? 5 : 4);
+  P.L = std::min(std::max(lb, 2), P.m);
+  P.L = std::max(P.L, P.m - 9);  // at most 2^9 gathered chunks per tile
+
+  Unroller U;
+  U.ops = ops;
+  U.n_ops = n_ops;
+  U.n = n;
+  U.pool = dense_pool;
+  U.pool_len = dense_pool ? dense_len : 0;
+  if (!U.walk(0, n_ops, -1, 0)) {
+    err = U.err;
+    return U.st;
+  }
+  P.n_flags = U.n_flags;
+  P.n_params_needed = U.max_param;
+
+  // segmentation
+  std::vector<Segment> segs(1);
+  bool seen_group = false;
+  uint64_t n_gates = 0, n_draws = 0;
+  for (size_t i = 0; i < U.items.size(); ++i) {
+    const Item& it = U.items[i];
+    Segment* cur = &segs.back();
+    switch (it.kind) {
+      case I_GATE:
+        ++n_gates;
+        if (cur->has_group) {
+          segs.emplace_back();
+          cur = &segs.back();
+        }
+        cur->gates.push_back(int(i));
+        break;
+      case I_MEAS:
+      case I_RESET: {
+        ++n_draws;
+        seen_group = true;
+        const uint64_t qb = 1ull << it.qubit;
+        if (cur->has_group && popc(cur->group_q | qb) > MAX_GROUP_Q) {
+          segs.emplace_back();
+          cur = &segs.back();
+        }
+        cur->has_group = true;
+        cur->group_q |= qb;
+        cur->phase.push_back(int(i));
+        break;
+      }
+      case I_COND: {
+        if (!seen_group) {
+          DScalar s{};
+          s.kind = S_COND;
+          s.flag = it.flag;
+          s.f_then = it.f_then;
+          s.f_else = it.f_else;
+          s.mask = it.mask;
+          s.value = it.value;
+          P.init_items.push_back(s);
+        } else if (cur->has_group) {
+          cur->phase.push_back(int(i));
+        } else {
+          segs[segs.size() - 2].phase.push_back(int(i));
+        }
+        break;
+      }
+    }
+  }
+
+  Builder b(P, U.items, dtype == SV_C64 ? 4 : 3, tune.max_pass_gates);
+  for (const Segment& s : segs) {
+    if (s.gates.empty() && !s.has_group) continue;
+    b.emit_segment(s);
+  }
+  // a projector left pending by a final measurement group is applied by a flush pass
+  if (!P.passes.empty() && P.passes.back().nc > 0) {
+    P.needs_flush = true;
+    std::vector<int> tq;
+    for (int q = 0; q < P.m; ++q) tq.push_back(q);
+    b.emit_pass({}, tq, nullptr, true);
+  }
+
+  P.stats.records = n_ops;
+  P.stats.unrolled_ops = n_gates + n_draws;
+  P.stats.gates = n_gates;
+  P.stats.draws = n_draws;
+  P.stats.passes = P.passes.size();
+  P.stats.stages = P.stages.size();
+  P.stats.flags = P.n_flags;
+  P.stats.tile_bits = P.m;
+  P.stats.low_bits = P.L;
+  P.stats.plan_bytes = P.passes.size() * sizeof(DPass) + P.gates.size() * sizeof(DGate) +
+                       P.stages.size() * sizeof(DStage) + (P.scalars.size() + P.init_items.size()) * sizeof(DScalar) +
+                       P.jobs.size() * sizeof(DJob) + P.consts.size() * sizeof(double);
+  return SV_OK;
+}
+
+}  // namespace svp

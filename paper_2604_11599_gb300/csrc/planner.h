@@ -1,0 +1,46 @@
+// planner.h -- lowering of the flat IR into passes, stages and scalar items.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "sv_plan.h"
+
+namespace svp {
+
+struct Tuning {
+  int tile_bits = 12;      // m: qubits held by one shared-memory tile
+  int low_bits = -1;       // L: contiguous low qubits of every tile (-1: per dtype)
+  int max_pass_gates = 0;  // 0: up to MAX_PASS_GATES
+};
+
+struct Plan {
+  int n = 0;        // logical qubits
+  int n_int = 0;    // simulated qubits (>= 4; extra qubits stay |0>)
+  int dtype = 0;
+  int m = 0, L = 0;
+  std::vector<DPass> passes;
+  std::vector<DGate> gates;
+  std::vector<DStage> stages;
+  std::vector<DScalar> scalars;      // phase items, referenced by passes
+  std::vector<DScalar> init_items;   // COND evaluations before the first measurement
+  std::vector<DJob> jobs;
+  std::vector<double> consts;        // complex constant pool (re, im pairs)
+  uint32_t n_mat = 0;                // complex entries in the matrix pool
+  uint32_t n_flags = 0;
+  uint32_t max_pass_mat = 0;
+  uint32_t max_stages = 0;
+  uint32_t max_gates = 0;
+  uint32_t max_scalars = 0;
+  bool needs_flush = false;
+  sv_program_stats stats{};
+  uint64_t n_params_needed = 0;      // 1 + the largest parameter index referenced
+};
+
+// Builds a plan; returns SV_OK or an error with a message in `err`.
+sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                     size_t dense_len, const Tuning& tune, Plan& out, std::string& err);
+
+}  // namespace svp

@@ -1,0 +1,627 @@
+// sv_api.cu -- the C-ABI of libsv (include/sv.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "kernels.h"
+#include "planner.h"
+
+using svp::Ctrl;
+using svp::DTrace;
+
+namespace {
+
+thread_local std::string g_err;
+
+sv_status fail(sv_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+sv_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SV_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t reserve(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) n = std::max<size_t>(count, 1);
+    return e;
+  }
+  template <typename U>
+  cudaError_t upload(const std::vector<U>& v, cudaStream_t s) {
+    const size_t bytes = v.size() * sizeof(U);
+    cudaError_t e = reserve((bytes + sizeof(T) - 1) / sizeof(T));
+    if (e != cudaSuccess || bytes == 0) return e;
+    return cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, s);
+  }
+};
+
+uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < len; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+struct sv_program {
+  sv_state* owner = nullptr;
+  svp::Plan plan;
+  DevBuf<svp::DPass> passes;
+  DevBuf<svp::DGate> gates;
+  DevBuf<svp::DStage> stages;
+  DevBuf<svp::DScalar> scalars;
+  DevBuf<svp::DScalar> init;
+  DevBuf<svp::DJob> jobs;
+  DevBuf<double> consts;
+  DevBuf<unsigned char> mats;
+  DevBuf<uint8_t> flags;
+  bool cached = false;  // owned by the state's cache
+};
+
+struct sv_state {
+  int n = 0, n_int = 0;
+  sv_dtype dtype = SV_C64;
+  size_t amp_bytes = 8;
+  void* state = nullptr;
+  bool owns_state = false;
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  Ctrl* ctrl = nullptr;
+  DTrace* trace = nullptr;
+  DevBuf<double> partials;
+  DevBuf<double> params;
+  DevBuf<double> sample_buf;
+  DevBuf<uint64_t> sample_out;
+  DevBuf<double> exp_partials;
+  DevBuf<uint64_t> exp_z;
+  DevBuf<int> exp_k;
+  DevBuf<double> exp_out;
+  unsigned* exp_ticket = nullptr;
+  std::vector<double> dense;  // host copy for planning
+  uint64_t dense_hash = 0;
+  svp::Tuning tune;
+  std::unordered_map<uint64_t, std::unique_ptr<sv_program>> cache;
+  const sv_program* last = nullptr;
+  // pass timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  double prof_bytes = 0;
+  bool use_cache = true;
+};
+
+namespace {
+
+sv_status upload_program(sv_state* h, sv_program* p) {
+  const svp::Plan& P = p->plan;
+  cudaStream_t s = h->stream;
+  SV_CUDA(p->passes.upload(P.passes, s));
+  SV_CUDA(p->gates.upload(P.gates, s));
+  SV_CUDA(p->stages.upload(P.stages, s));
+  SV_CUDA(p->scalars.upload(P.scalars, s));
+  SV_CUDA(p->init.upload(P.init_items, s));
+  SV_CUDA(p->jobs.upload(P.jobs, s));
+  SV_CUDA(p->consts.upload(P.consts, s));
+  SV_CUDA(p->mats.reserve(size_t(std::max<uint32_t>(P.n_mat, 1)) * h->amp_bytes));
+  SV_CUDA(p->flags.reserve(std::max<uint32_t>(P.n_flags, 1)));
+  SV_CUDA(cudaMemsetAsync(p->flags.p, 0, std::max<uint32_t>(P.n_flags, 1), s));
+  // the host copies above read pageable vectors; finish them before the plan can change
+  SV_CUDA(cudaStreamSynchronize(s));
+  return SV_OK;
+}
+
+int pass_grid(sv_state* h, int m) {
+  int per_sm = 1;
+  svk::pass_occupancy(h->dtype, m, &per_sm);
+  const uint64_t tiles = 1ull << (h->n_int - m);
+  const uint64_t want = uint64_t(h->sms) * uint64_t(per_sm);
+  return int(std::min<uint64_t>(tiles, want));
+}
+
+sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, size_t n_params, uint64_t seed,
+                         uint64_t stream_id, uint64_t shot) {
+  const svp::Plan& P = p->plan;
+  if (n_params < P.n_params_needed)
+    return fail(SV_ERR_ARG, "program references " + std::to_string(P.n_params_needed) + " parameters, got " +
+                                std::to_string(n_params));
+  if (P.n_params_needed && !dev_params) return fail(SV_ERR_ARG, "params is NULL");
+  cudaStream_t s = h->stream;
+  SV_CUDA(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), s));
+  svk::PrepArgs pa{};
+  pa.jobs = p->jobs.p;
+  pa.njobs = int(P.jobs.size());
+  pa.params = dev_params;
+  pa.n_params = n_params;
+  pa.consts = p->consts.p;
+  pa.mats = p->mats.p;
+  pa.ctrl = h->ctrl;
+  pa.init = p->init.p;
+  pa.ninit = int(P.init_items.size());
+  pa.flags = p->flags.p;
+  pa.seed = seed;
+  pa.stream = stream_id;
+  pa.shot = shot;
+  SV_CUDA(svk::launch_prep(h->dtype, pa, s));
+  SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
+  if (!P.passes.empty()) {
+    const int grid = pass_grid(h, P.m);
+    SV_CUDA(h->partials.reserve(size_t(grid) * 16));
+    svk::PassArgs a{};
+    a.state = h->state;
+    a.passes = p->passes.p;
+    a.gates = p->gates.p;
+    a.stages = p->stages.p;
+    a.scalars = p->scalars.p;
+    a.mats = p->mats.p;
+    a.flags = p->flags.p;
+    a.ctrl = h->ctrl;
+    a.trace = h->trace;
+    a.partials = h->partials.p;
+    a.n = h->n_int;
+    const double sbytes = double(1ull << h->n_int) * double(h->amp_bytes);
+    for (size_t i = 0; i < P.passes.size(); ++i) {
+      if (h->profiling) {
+        while (h->events.size() < h->ev_used + 2) {
+          cudaEvent_t e;
+          SV_CUDA(cudaEventCreate(&e));
+          h->events.push_back(e);
+        }
+        SV_CUDA(cudaEventRecord(h->events[h->ev_used], s));
+      }
+      SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s));
+      if (h->profiling) {
+        SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));
+        h->ev_used += 2;
+        const svp::DPass& d = P.passes[i];
+        h->prof_bytes += (d.ng > 0 || d.flush) ? 2 * sbytes : sbytes;
+      }
+    }
+  }
+  h->last = p;
+  return SV_OK;
+}
+
+sv_status check_status(sv_state* h) {
+  int32_t st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, &h->ctrl->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (st == SV_ERR_NUMERIC) return fail(SV_ERR_NUMERIC, "a measurement saw a zero-norm state");
+  if (st != 0) return fail(sv_status(st), "device reported an error");
+  return SV_OK;
+}
+
+sv_status get_program(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out) {
+  uint64_t key = fnv1a(ops, n_ops * sizeof(sv_op));
+  key = fnv1a(&h->dense_hash, sizeof(h->dense_hash), key);
+  key = fnv1a(&h->tune, sizeof(h->tune), key);
+  auto it = h->cache.find(key);
+  if (it != h->cache.end() && !h->use_cache) {
+    cudaStreamSynchronize(h->stream);
+    h->cache.erase(it);
+    it = h->cache.end();
+  }
+  if (it != h->cache.end()) {
+    *out = it->second.get();
+    return SV_OK;
+  }
+  std::unique_ptr<sv_program> p(new sv_program());
+  p->owner = h;
+  std::string err;
+  sv_status st = svp::build_plan(h->n, h->dtype, ops, n_ops, h->dense.empty() ? nullptr : h->dense.data(),
+                                 h->dense.size() / 2, h->tune, p->plan, err);
+  if (st != SV_OK) return fail(st, err);
+  st = upload_program(h, p.get());
+  if (st != SV_OK) return st;
+  p->cached = true;
+  if (h->cache.size() > 256) h->cache.clear();
+  *out = p.get();
+  h->cache[key] = std::move(p);
+  return SV_OK;
+}
+
+bool has_draws(const sv_op* ops, size_t n_ops) {
+  for (size_t i = 0; i < n_ops; ++i)
+    if (ops[i].kind == SV_MEASURE || ops[i].kind == SV_RESET) return true;
+  return false;
+}
+
+sv_status sample_current(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                         uint64_t* dev_out) {
+  const uint64_t nb = svk::sample_blocks(h->n_int);
+  SV_CUDA(h->sample_buf.reserve(2 * nb + 1));
+  svk::SampleArgs a{};
+  a.state = h->state;
+  a.n = h->n_int;
+  a.n_logical = h->n;
+  a.block_sums = h->sample_buf.p;
+  a.block_prefix = h->sample_buf.p + nb;
+  a.shots = shots;
+  a.seed = seed;
+  a.stream = stream_id;
+  a.shot0 = shot0;
+  a.out = dev_out;
+  SV_CUDA(svk::launch_sample(h->dtype, a, h->sms, h->stream));
+  return SV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sv_last_error(void) { return g_err.c_str(); }
+
+const char* sv_version(void) { return "libsv 0.1 (sm_103a)"; }
+
+sv_status sv_create(int n, sv_dtype dtype, void* dev_buf, size_t bytes, sv_state** out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 34) return fail(SV_ERR_ARG, "n must be in 1..34");
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  std::unique_ptr<sv_state> h(new sv_state());
+  h->n = n;
+  h->n_int = std::max(n, 4);
+  h->dtype = dtype;
+  h->amp_bytes = dtype == SV_C64 ? 8 : 16;
+  const size_t need = (size_t(1) << h->n_int) * h->amp_bytes;
+  SV_CUDA(cudaGetDevice(&h->device));
+  SV_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+  if (dev_buf) {
+    if (bytes < need) return fail(SV_ERR_ARG, "dev_buf smaller than 2^max(n,4) amplitudes");
+    if (reinterpret_cast<uintptr_t>(dev_buf) % 16) return fail(SV_ERR_ARG, "dev_buf must be 16-byte aligned");
+    h->state = dev_buf;
+  } else {
+    cudaError_t e = cudaMalloc(&h->state, need);
+    if (e != cudaSuccess) return fail(SV_ERR_OOM, std::string("state allocation: ") + cudaGetErrorString(e));
+    h->owns_state = true;
+  }
+  if (cudaMalloc(&h->ctrl, sizeof(Ctrl)) != cudaSuccess ||
+      cudaMalloc(&h->trace, sizeof(DTrace) * svp::MAX_TRACE) != cudaSuccess ||
+      cudaMalloc(&h->exp_ticket, sizeof(unsigned)) != cudaSuccess) {
+    if (h->owns_state) cudaFree(h->state);
+    return fail(SV_ERR_OOM, "control block allocation");
+  }
+  SV_CUDA(cudaMemset(h->ctrl, 0, sizeof(Ctrl)));
+  SV_CUDA(cudaMemset(h->exp_ticket, 0, sizeof(unsigned)));
+  SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, nullptr));
+  SV_CUDA(cudaDeviceSynchronize());
+  *out = h.release();
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_state* h) {
+  if (!h) return SV_OK;
+  cudaStreamSynchronize(h->stream);
+  h->cache.clear();
+  if (h->owns_state && h->state) cudaFree(h->state);
+  if (h->ctrl) cudaFree(h->ctrl);
+  if (h->trace) cudaFree(h->trace);
+  if (h->exp_ticket) cudaFree(h->exp_ticket);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  delete h;
+  return SV_OK;
+}
+
+sv_status sv_bind_stream(sv_state* h, void* cuda_stream) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return SV_OK;
+}
+
+sv_status sv_set_dense_pool(sv_state* h, const double* pool, size_t n_complex) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (n_complex && !pool) return fail(SV_ERR_ARG, "pool is NULL");
+  h->dense.assign(pool, pool + 2 * n_complex);
+  h->dense_hash = fnv1a(h->dense.data(), h->dense.size() * sizeof(double), 7);
+  return SV_OK;
+}
+
+sv_status sv_set_tuning(sv_state* h, int tile_bits, int low_bits, int max_pass_gates) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (tile_bits && (tile_bits < 10 || tile_bits > svp::MAX_TILE_BITS)) return fail(SV_ERR_ARG, "tile_bits in 10..14");
+  if (low_bits && (low_bits < 2 || low_bits > 14)) return fail(SV_ERR_ARG, "low_bits in 2..14");
+  if (tile_bits && low_bits && tile_bits - low_bits > 9) return fail(SV_ERR_ARG, "tile_bits - low_bits <= 9");
+  if (!tile_bits && low_bits && 12 - low_bits > 9) return fail(SV_ERR_ARG, "tile_bits - low_bits <= 9");
+  if (max_pass_gates < 0 || max_pass_gates > svp::MAX_PASS_GATES) return fail(SV_ERR_ARG, "max_pass_gates in 0..128");
+  h->tune.tile_bits = tile_bits;
+  h->tune.low_bits = low_bits ? low_bits : -1;
+  h->tune.max_pass_gates = max_pass_gates;
+  return SV_OK;
+}
+
+sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out) {
+  if (!h || !out) return fail(SV_ERR_ARG, "null argument");
+  sv_program* cached = nullptr;
+  sv_status st = get_program(h, ops, n_ops, &cached);
+  if (st != SV_OK) return st;
+  // hand out a private copy so that sv_program_free never touches the cache
+  std::unique_ptr<sv_program> p(new sv_program());
+  p->owner = h;
+  p->plan = cached->plan;
+  st = upload_program(h, p.get());
+  if (st != SV_OK) return st;
+  *out = p.release();
+  return SV_OK;
+}
+
+sv_status sv_plan_info(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                       size_t n_complex, int tile_bits, int low_bits, int max_pass_gates, sv_program_stats* out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  svp::Tuning t;
+  t.tile_bits = tile_bits;
+  t.low_bits = low_bits ? low_bits : -1;
+  t.max_pass_gates = max_pass_gates;
+  svp::Plan P;
+  std::string err;
+  sv_status st = svp::build_plan(n, dtype, ops, n_ops, dense_pool, n_complex, t, P, err);
+  if (st != SV_OK) return fail(st, err);
+  *out = P.stats;
+  return SV_OK;
+}
+
+sv_status sv_program_free(sv_program* p) {
+  if (!p) return SV_OK;
+  if (p->cached) return fail(SV_ERR_ARG, "program belongs to a cache");
+  if (p->owner) cudaStreamSynchronize(p->owner->stream);
+  delete p;
+  return SV_OK;
+}
+
+sv_status sv_program_info(const sv_program* p, sv_program_stats* out) {
+  if (!p || !out) return fail(SV_ERR_ARG, "null argument");
+  *out = p->plan.stats;
+  return SV_OK;
+}
+
+sv_status sv_launch(sv_state* h, sv_program* p, const double* dev_params, size_t n_params, uint64_t seed,
+                    uint64_t stream_id, uint64_t shot) {
+  if (!h || !p) return fail(SV_ERR_ARG, "null argument");
+  if (p->owner != h) return fail(SV_ERR_ARG, "program prepared for another state");
+  return launch_program(h, p, dev_params, n_params, seed, stream_id, shot);
+}
+
+sv_status sv_run(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params, uint64_t seed,
+                 uint64_t stream_id, uint64_t shot, uint64_t* creg_out) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (n_ops && !ops) return fail(SV_ERR_ARG, "ops is NULL");
+  if (n_params && !params) return fail(SV_ERR_ARG, "params is NULL");
+  sv_program* p = nullptr;
+  sv_status st = get_program(h, ops, n_ops, &p);
+  if (st != SV_OK) return st;
+  if (n_params) {
+    SV_CUDA(h->params.reserve(n_params));
+    SV_CUDA(cudaMemcpyAsync(h->params.p, params, n_params * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  st = launch_program(h, p, n_params ? h->params.p : nullptr, n_params, seed, stream_id, shot);
+  if (st != SV_OK) return st;
+  if (creg_out) {
+    SV_CUDA(cudaMemcpyAsync(creg_out, &h->ctrl->creg, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+    return check_status(h);
+  }
+  return SV_OK;
+}
+
+sv_status sv_get_creg(sv_state* h, uint64_t* creg) {
+  if (!h || !creg) return fail(SV_ERR_ARG, "null argument");
+  SV_CUDA(cudaMemcpyAsync(creg, &h->ctrl->creg, sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+  return check_status(h);
+}
+
+sv_status sv_get_trace(sv_state* h, sv_draw* out, size_t max, size_t* n_out) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  Ctrl c;
+  SV_CUDA(cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  const size_t k = std::min<size_t>(std::min<size_t>(c.n_trace, svp::MAX_TRACE), max);
+  if (n_out) *n_out = c.m;
+  if (k && out) {
+    static_assert(sizeof(sv_draw) == sizeof(DTrace), "trace layout");
+    SV_CUDA(cudaMemcpyAsync(out, h->trace, k * sizeof(DTrace), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return SV_OK;
+}
+
+sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                          uint64_t* out) {
+  if (!h || (shots && !out)) return fail(SV_ERR_ARG, "null argument");
+  if (!shots) return SV_OK;
+  SV_CUDA(h->sample_out.reserve(shots));
+  sv_status st = sample_current(h, shots, seed, stream_id, shot0, h->sample_out.p);
+  if (st != SV_OK) return st;
+  SV_CUDA(cudaMemcpyAsync(out, h->sample_out.p, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  return SV_OK;
+}
+
+sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
+                    uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out, uint64_t* bits_out) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (!shots) return SV_OK;
+  sv_program* p = nullptr;
+  sv_status st = get_program(h, ops, n_ops, &p);
+  if (st != SV_OK) return st;
+  if (n_params) {
+    SV_CUDA(h->params.reserve(n_params));
+    SV_CUDA(cudaMemcpyAsync(h->params.p, params, n_params * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  const double* dp = n_params ? h->params.p : nullptr;
+  if (!has_draws(ops, n_ops)) {
+    st = launch_program(h, p, dp, n_params, seed, stream_id, 0);
+    if (st != SV_OK) return st;
+    if (creg_out) std::fill(creg_out, creg_out + shots, 0ull);
+    if (bits_out) return sv_sample_state(h, shots, seed, stream_id, 0, bits_out);
+    return check_status(h);
+  }
+  // one trajectory per shot; records gathered on the device
+  SV_CUDA(h->sample_out.reserve(2 * shots));
+  uint64_t* d_creg = h->sample_out.p;
+  uint64_t* d_bits = h->sample_out.p + shots;
+  for (uint64_t s = 0; s < shots; ++s) {
+    st = launch_program(h, p, dp, n_params, seed, stream_id, s);
+    if (st != SV_OK) return st;
+    SV_CUDA(cudaMemcpyAsync(d_creg + s, &h->ctrl->creg, sizeof(uint64_t), cudaMemcpyDeviceToDevice, h->stream));
+    if (bits_out) {
+      st = sample_current(h, 1, seed, stream_id, s, d_bits + s);
+      if (st != SV_OK) return st;
+    }
+  }
+  if (creg_out)
+    SV_CUDA(cudaMemcpyAsync(creg_out, d_creg, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+  if (bits_out)
+    SV_CUDA(cudaMemcpyAsync(bits_out, d_bits, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+  return check_status(h);
+}
+
+sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* total, double* per_term) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (n_terms && !terms) return fail(SV_ERR_ARG, "terms is NULL");
+  const uint64_t lim = h->n >= 64 ? ~0ull : ((1ull << h->n) - 1);
+  for (size_t t = 0; t < n_terms; ++t)
+    if ((terms[t].x_mask | terms[t].z_mask) & ~lim) return fail(SV_ERR_ARG, "Pauli term acts on a qubit >= n");
+  // group by X mask, in first-appearance order
+  std::vector<uint64_t> keys;
+  std::map<uint64_t, std::vector<size_t>> groups;
+  for (size_t t = 0; t < n_terms; ++t) {
+    auto it = groups.find(terms[t].x_mask);
+    if (it == groups.end()) keys.push_back(terms[t].x_mask);
+    groups[terms[t].x_mask].push_back(t);
+  }
+  std::vector<uint64_t> zs;
+  std::vector<int> ks;
+  std::vector<std::pair<size_t, size_t>> launches;  // (x key index, first term slot)
+  std::vector<size_t> order;
+  for (uint64_t x : keys)
+    for (size_t t : groups[x]) order.push_back(t);
+  for (size_t t : order) {
+    zs.push_back(terms[t].z_mask);
+    ks.push_back(__builtin_popcountll(terms[t].x_mask & terms[t].z_mask) & 3);
+  }
+  const size_t nt = order.size();
+  SV_CUDA(h->exp_z.upload(zs, h->stream));
+  SV_CUDA(h->exp_k.upload(ks, h->stream));
+  SV_CUDA(h->exp_out.reserve(std::max<size_t>(nt, 1)));
+  const int grid = std::max(1, std::min(h->sms * 4, int((1ull << h->n_int) / 256)));
+  SV_CUDA(h->exp_partials.reserve(size_t(grid) * 32));
+  size_t slot = 0;
+  for (uint64_t x : keys) {
+    const size_t cnt = groups[x].size();
+    for (size_t c = 0; c < cnt; c += 32) {
+      svk::ExpvalArgs a{};
+      a.state = h->state;
+      a.n = h->n_int;
+      a.x_mask = x;
+      a.z_masks = h->exp_z.p + slot + c;
+      a.phase = h->exp_k.p + slot + c;
+      a.nterms = int(std::min<size_t>(32, cnt - c));
+      a.partials = h->exp_partials.p;
+      a.out = h->exp_out.p + slot + c;
+      a.ticket = h->exp_ticket;
+      SV_CUDA(svk::launch_expval_group(h->dtype, a, grid, h->stream));
+    }
+    slot += cnt;
+  }
+  std::vector<double> vals(nt);
+  if (nt) SV_CUDA(cudaMemcpyAsync(vals.data(), h->exp_out.p, nt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  double tot = 0;
+  std::vector<double> per(n_terms, 0.0);
+  for (size_t k = 0; k < nt; ++k) per[order[k]] = vals[k];
+  for (size_t t = 0; t < n_terms; ++t) tot += terms[t].coeff * per[t];
+  if (total) *total = tot;
+  if (per_term) std::copy(per.begin(), per.end(), per_term);
+  return SV_OK;
+}
+
+sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count) {
+  if (!h || (count && !host_dst)) return fail(SV_ERR_ARG, "null argument");
+  if (first + count > (size_t(1) << h->n) || first + count < first) return fail(SV_ERR_ARG, "range outside the state");
+  SV_CUDA(cudaMemcpyAsync(host_dst, static_cast<char*>(h->state) + first * h->amp_bytes, count * h->amp_bytes,
+                          cudaMemcpyDeviceToHost, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  return SV_OK;
+}
+
+sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count) {
+  if (!h || (count && !host_src)) return fail(SV_ERR_ARG, "null argument");
+  if (first + count > (size_t(1) << h->n) || first + count < first) return fail(SV_ERR_ARG, "range outside the state");
+  SV_CUDA(cudaMemcpyAsync(static_cast<char*>(h->state) + first * h->amp_bytes, host_src, count * h->amp_bytes,
+                          cudaMemcpyHostToDevice, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  return SV_OK;
+}
+
+sv_status sv_state_buffer(sv_state* h, void** dev_ptr, size_t* bytes) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (dev_ptr) *dev_ptr = h->state;
+  if (bytes) *bytes = (size_t(1) << h->n_int) * h->amp_bytes;
+  return SV_OK;
+}
+
+sv_status sv_set_cache(sv_state* h, int enable) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->use_cache = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_profile(sv_state* h, int enable) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->profiling = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, double* bytes) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  double ms = 0;
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float t = 0;
+    SV_CUDA(cudaEventElapsedTime(&t, h->events[i], h->events[i + 1]));
+    ms += t;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = h->ev_used / 2;
+  if (bytes) *bytes = h->prof_bytes;
+  h->ev_used = 0;
+  h->prof_bytes = 0;
+  return SV_OK;
+}
+
+sv_status sv_sync(sv_state* h) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  return SV_OK;
+}
+
+}  // extern "C"

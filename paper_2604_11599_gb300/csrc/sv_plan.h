@@ -1,0 +1,141 @@
+// sv_plan.h -- plan records shared by the host planner and the CUDA kernels.
+//
+// A program (the flat IR of include/sv.h) is lowered once into:
+//   * matrix jobs   -- one per gate, evaluated on the device from the run-time
+//                      parameters (OpenQASM `input` values, Sec. III-D), so a
+//                      plan is compiled once and run with many parameter sets;
+//   * passes        -- sweeps over the whole state.  A pass holds a tile of 2^m
+//                      amplitudes (m tile qubits: the L lowest qubits plus m-L
+//                      gathered higher ones) in shared memory, applies every gate
+//                      of the pass in register-resident stages of four qubits,
+//                      and optionally accumulates the |amp|^2 table of up to four
+//                      measured qubits for the measurement group that follows;
+//   * scalar items  -- measure / reset / cond-evaluation records run by one
+//                      thread after a pass (the device-side feed-forward of
+//                      Sec. III-C: predicates are read from the classical record
+//                      on the GPU, never on the host).
+#pragma once
+#include <stdint.h>
+
+namespace svp {
+
+enum OpCode : uint8_t {
+  OP_NONE = 0,
+  OP_U,     // general 2x2 complex on p0: 4 complex
+  OP_R,     // real 2x2 on p0: [r00 r01; r10 r11] stored as 4 complex (re only)
+  OP_RX,    // [c, -is; -is, c]: stored as (c, s)
+  OP_D,     // diag(d0, d1) on p0: 2 complex
+  OP_X,     // swap halves of p0
+  OP_CU,    // control p0, target p1, 2x2 complex: 4 complex
+  OP_CX,    // control p0, target p1
+  OP_CZ,    // phase -1 where p0 and p1 are both 1
+  OP_CD,    // control p0, target p1: diag(d0, d1) where control is 1: 2 complex
+  OP_SWAP,  // swap p0 <-> p1
+  OP_U4,    // dense 4x4 on (p0 = local bit 0, p1 = local bit 1): 16 complex
+  OP_D16,   // dense 16x16 on the four register bits: 256 complex
+  OP_COUNT
+};
+
+// number of complex matrix entries each op reads
+static inline int op_mat_len(int op) {
+  switch (op) {
+    case OP_U: case OP_R: case OP_CU: return 4;
+    case OP_RX: case OP_D: case OP_CD: return 2;
+    case OP_U4: return 16;
+    case OP_D16: return 256;
+    default: return 0;
+  }
+}
+
+enum ScalarKind : uint8_t { S_MEASURE = 1, S_RESET = 2, S_COND = 3 };
+
+enum JobKind : uint8_t { J_GATE = 1, J_CONST = 2 };
+
+constexpr int REG_BITS = 4;
+constexpr int REG_N = 16;
+constexpr int PASS_THREADS = 256;
+constexpr int MAX_TILE_BITS = 14;
+constexpr int MAX_GROUP_Q = 4;
+constexpr int MAX_PASS_GATES = 128;
+constexpr int MAX_PASS_STAGES = 48;
+constexpr int MAX_PASS_MAT = 1024;  // complex entries staged in shared memory per pass
+constexpr int MAX_TRACE = 4096;     // draw records kept per trajectory
+
+// gate as the kernel sees it: positions are register-bit indices (0..3) of its stage
+struct DGate {
+  uint8_t op, p0, p1, pad;
+  int32_t flag;   // -1: unconditional; else index into the flag array
+  uint32_t mat;   // offset (complex entries) from the pass's matrix base
+  uint32_t pad2;
+};
+
+struct DStage {
+  uint16_t g0, ng;                   // gate range (pass-relative)
+  uint8_t reg[REG_BITS];             // tile-local bit of register bit r
+  uint8_t thr[MAX_TILE_BITS];        // tile-local bits receiving the group index bits (m-4 used)
+  uint8_t pad[6];
+};
+
+struct DScalar {
+  uint8_t kind;     // ScalarKind
+  uint8_t tbit;     // MEASURE/RESET: bit of the qubit in the pass's group table
+  uint16_t pad;
+  int32_t flag;     // MEASURE/RESET: own flag; COND: parent flag (-1: none)
+  int32_t f_then;   // COND: flag receiving the then-predicate
+  int32_t f_else;   // COND: flag receiving the else-predicate (-1: none)
+  uint32_t qubit;   // MEASURE/RESET: qubit (physical bit)
+  uint32_t cbit;    // MEASURE: classical bit
+  uint32_t pad2;
+  uint64_t mask, value;  // COND predicate
+};
+
+struct DPass {
+  uint32_t g0, ng;        // gates
+  uint32_t s0, ns;        // stages
+  uint32_t c0, nc;        // scalar items run after the pass
+  uint32_t mat0, nmat;    // matrix range (complex entries) in the matrix pool
+  uint8_t m, L;           // tile bits, contiguous low bits
+  uint8_t gk;             // group table bits (0: no table)
+  uint8_t kin;            // how many of the group bits are tile bits (table bits 0..kin-1)
+  uint8_t group_always;   // 1: the table is needed whatever the flags say
+  uint8_t flush;          // 1: final pass that only applies a pending projector
+  uint8_t pad[2];
+  uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
+  uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
+  uint8_t red_reg[REG_BITS];      // reduction stage: register bit r <- tile-local bit
+  uint8_t red_thr[MAX_TILE_BITS]; // reduction stage: group-index bits
+  uint32_t pad2[2];
+};
+
+struct DJob {
+  uint8_t kind;     // JobKind
+  uint8_t op;       // OpCode the matrix is laid out for
+  uint8_t gate;     // IR gate enum (J_GATE)
+  uint8_t pad;
+  int32_t pidx[3];
+  double angle[3];
+  uint32_t out;     // offset (complex entries) into the matrix pool
+  uint32_t src;     // J_CONST: offset into the constant pool (complex entries)
+  uint32_t len;     // J_CONST: entries to copy
+  uint32_t pad2;
+};
+
+// per-trajectory control block on the device
+struct Ctrl {
+  uint64_t creg;
+  uint64_t seed, stream, shot;
+  uint64_t m;                 // draws executed
+  uint64_t pm, pv, px;        // pending projector: a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv
+  double ps;
+  uint32_t ticket;            // last-CTA-done counter of the running pass
+  int32_t status;             // 0 ok, else an sv_status
+  uint32_t n_trace;
+  uint32_t pad;
+};
+
+struct DTrace {
+  int32_t qubit, is_reset, outcome, pad;
+  double p0, p1, u;
+};
+
+}  // namespace svp

@@ -1,0 +1,307 @@
+"""Python binding of libsv (argument marshalling only).
+
+Every function maps onto one C-ABI entry point of ``include/sv.h`` with the
+same name; all simulation work runs in the CUDA library.  PyTorch, when it is
+importable, supplies the device memory of the state (a tensor the handle
+views, zero-copy) and the CUDA stream the library enqueues on.
+
+Importing this module loads ``libsv.so``; it raises if the library was not
+built (``python -m paper_2604_11599_gb300.build``) -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from .ir import OP_DTYPE, PAULI_DTYPE
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsv.so")
+
+SV_C64, SV_C128 = 0, 1
+STATUS = {0: "SV_OK", -1: "SV_ERR_ARG", -2: "SV_ERR_OOM", -3: "SV_ERR_CUDA", -4: "SV_ERR_TIMEOUT",
+          -5: "SV_ERR_UNSUPPORTED", -6: "SV_ERR_NUMERIC"}
+
+DRAW_DTYPE = np.dtype([("qubit", "<i4"), ("is_reset", "<i4"), ("outcome", "<i4"), ("pad", "<i4"),
+                       ("p0", "<f8"), ("p1", "<f8"), ("u", "<f8")])
+
+
+class SVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProgramStats(C.Structure):
+    _fields_ = [("records", C.c_uint64), ("unrolled_ops", C.c_uint64), ("gates", C.c_uint64),
+                ("draws", C.c_uint64), ("passes", C.c_uint64), ("stages", C.c_uint64),
+                ("flags", C.c_uint64), ("tile_bits", C.c_int32), ("low_bits", C.c_int32),
+                ("plan_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsv (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsv.so is not built ({LIB_PATH}); run python -m paper_2604_11599_gb300.build")
+    L = C.CDLL(LIB_PATH)
+    vp, sz, u64, i32, st = C.c_void_p, C.c_size_t, C.c_uint64, C.c_int, C.c_int
+    sig = {
+        "sv_create": ([i32, i32, vp, sz, C.POINTER(vp)], st),
+        "sv_destroy": ([vp], st),
+        "sv_bind_stream": ([vp, vp], st),
+        "sv_set_dense_pool": ([vp, vp, sz], st),
+        "sv_prepare": ([vp, vp, sz, C.POINTER(vp)], st),
+        "sv_program_free": ([vp], st),
+        "sv_program_info": ([vp, C.POINTER(ProgramStats)], st),
+        "sv_launch": ([vp, vp, vp, sz, u64, u64, u64], st),
+        "sv_run": ([vp, vp, sz, vp, sz, u64, u64, u64, vp], st),
+        "sv_get_creg": ([vp, vp], st),
+        "sv_get_trace": ([vp, vp, sz, C.POINTER(sz)], st),
+        "sv_sample": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, vp], st),
+        "sv_sample_state": ([vp, u64, u64, u64, u64, vp], st),
+        "sv_expval": ([vp, vp, sz, vp, vp], st),
+        "sv_get_amplitudes": ([vp, vp, sz, sz], st),
+        "sv_set_amplitudes": ([vp, vp, sz, sz], st),
+        "sv_state_buffer": ([vp, C.POINTER(vp), C.POINTER(sz)], st),
+        "sv_set_tuning": ([vp, i32, i32, i32], st),
+        "sv_sync": ([vp], st),
+        "sv_profile": ([vp, i32], st),
+        "sv_set_cache": ([vp, i32], st),
+        "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
+        "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
+        "sv_last_error": ([], C.c_char_p),
+        "sv_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise SVError(status, lib().sv_last_error().decode())
+
+
+def _ops(ops: np.ndarray) -> np.ndarray:
+    ops = np.ascontiguousarray(ops)
+    if ops.dtype != OP_DTYPE:
+        raise TypeError("ops must be an array of ir.OP_DTYPE records")
+    return ops
+
+
+def _f64(a) -> Optional[np.ndarray]:
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None or a.size == 0 else a.ctypes.data
+
+
+def _torch():
+    try:
+        import torch  # noqa: F401
+        return torch
+    except Exception:  # pragma: no cover - torch is part of the image
+        return None
+
+
+class Program:
+    """A lowered program (``sv_prepare``); launch it with :meth:`State.launch`."""
+
+    def __init__(self, handle: int, owner: "State"):
+        self._h = handle
+        self.owner = owner
+
+    @property
+    def stats(self) -> dict:
+        s = ProgramStats()
+        _check(lib().sv_program_info(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ProgramStats._fields_}
+
+    def free(self):
+        if self._h:
+            _check(lib().sv_program_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class State:
+    """A state vector of ``n`` qubits (``sv_create``) in |0...0>."""
+
+    def __init__(self, n: int, dtype: str = "c64", buffer=None, stream=None):
+        self.n = int(n)
+        self.dtype = dtype
+        self.dt = SV_C64 if dtype == "c64" else SV_C128
+        self.amp = np.complex64 if dtype == "c64" else np.complex128
+        torch = _torch()
+        n_int = max(self.n, 4)
+        self._buf = buffer
+        if self._buf is None and torch is not None and torch.cuda.is_available():
+            real = torch.float32 if dtype == "c64" else torch.float64
+            self._buf = torch.empty(2 << n_int, dtype=real, device="cuda")
+        ptr, nbytes = None, 0
+        if self._buf is not None:
+            ptr = self._buf.data_ptr()
+            nbytes = self._buf.numel() * self._buf.element_size()
+        h = C.c_void_p()
+        _check(lib().sv_create(self.n, self.dt, ptr, nbytes, C.byref(h)))
+        self._h = h.value
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        if stream is not None:
+            _check(lib().sv_bind_stream(self._h, stream))
+        self._pool = None
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- configuration
+    def bind_stream(self, stream) -> None:
+        _check(lib().sv_bind_stream(self._h, stream))
+
+    def set_dense_pool(self, pool) -> None:
+        p = np.ascontiguousarray(pool, dtype=np.complex128)
+        self._pool = p
+        _check(lib().sv_set_dense_pool(self._h, _ptr(p), p.size))
+
+    def set_cache(self, enable: bool) -> None:
+        _check(lib().sv_set_cache(self._h, 1 if enable else 0))
+
+    def set_tuning(self, tile_bits: int = 0, low_bits: int = 0, max_pass_gates: int = 0) -> None:
+        _check(lib().sv_set_tuning(self._h, tile_bits, low_bits, max_pass_gates))
+
+    # -------------------------------------------------------------- running
+    def prepare(self, ops: np.ndarray) -> Program:
+        ops = _ops(ops)
+        h = C.c_void_p()
+        _check(lib().sv_prepare(self._h, _ptr(ops), len(ops), C.byref(h)))
+        return Program(h.value, self)
+
+    def launch(self, prog: Program, dev_params=None, seed: int = 0, stream_id: int = 0, shot: int = 0) -> None:
+        """Asynchronous run with device-resident parameters (a CUDA tensor of float64 or None)."""
+        ptr, n = None, 0
+        if dev_params is not None:
+            ptr, n = dev_params.data_ptr(), dev_params.numel()
+        _check(lib().sv_launch(self._h, prog._h, ptr, n, seed, stream_id, shot))
+
+    def run(self, ops: np.ndarray, params=None, seed: int = 0, stream_id: int = 0, shot: int = 0,
+            wait: bool = True) -> Optional[int]:
+        ops = _ops(ops)
+        p = _f64(params)
+        creg = C.c_uint64(0)
+        _check(lib().sv_run(self._h, _ptr(ops), len(ops), _ptr(p), 0 if p is None else p.size,
+                            seed, stream_id, shot, C.byref(creg) if wait else None))
+        return int(creg.value) if wait else None
+
+    def creg(self) -> int:
+        v = C.c_uint64(0)
+        _check(lib().sv_get_creg(self._h, C.byref(v)))
+        return int(v.value)
+
+    def trace(self, max_draws: int = 4096) -> np.ndarray:
+        out = np.zeros(max_draws, dtype=DRAW_DTYPE)
+        n = C.c_size_t(0)
+        _check(lib().sv_get_trace(self._h, out.ctypes.data, max_draws, C.byref(n)))
+        return out[: min(n.value, max_draws)].copy()
+
+    def sample(self, ops: np.ndarray, shots: int, params=None, seed: int = 0, stream_id: int = 0,
+               terminal: bool = False):
+        ops = _ops(ops)
+        p = _f64(params)
+        cregs = np.zeros(shots, dtype=np.uint64)
+        bits = np.zeros(shots, dtype=np.uint64) if terminal else None
+        _check(lib().sv_sample(self._h, _ptr(ops), len(ops), _ptr(p), 0 if p is None else p.size, shots, seed,
+                               stream_id, _ptr(cregs), _ptr(bits)))
+        return cregs, bits
+
+    def sample_state(self, shots: int, seed: int = 0, stream_id: int = 0, shot0: int = 0) -> np.ndarray:
+        out = np.zeros(shots, dtype=np.uint64)
+        _check(lib().sv_sample_state(self._h, shots, seed, stream_id, shot0, _ptr(out)))
+        return out
+
+    def expval(self, terms: np.ndarray):
+        terms = np.ascontiguousarray(terms)
+        if terms.dtype != PAULI_DTYPE:
+            raise TypeError("terms must be an array of ir.PAULI_DTYPE records")
+        tot = C.c_double(0)
+        per = np.zeros(len(terms), dtype=np.float64)
+        _check(lib().sv_expval(self._h, _ptr(terms), len(terms), C.byref(tot), _ptr(per)))
+        return float(tot.value), per
+
+    def amplitudes(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        count = (1 << self.n) - first if count is None else count
+        out = np.empty(count, dtype=self.amp)
+        _check(lib().sv_get_amplitudes(self._h, out.ctypes.data, first, count))
+        return out
+
+    def set_amplitudes(self, values, first: int = 0) -> None:
+        v = np.ascontiguousarray(values, dtype=self.amp)
+        _check(lib().sv_set_amplitudes(self._h, v.ctypes.data, first, v.size))
+
+    def sync(self) -> None:
+        _check(lib().sv_sync(self._h))
+
+    def profile(self, enable: bool = True) -> None:
+        _check(lib().sv_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        ms, n, b = C.c_double(0), C.c_uint64(0), C.c_double(0)
+        _check(lib().sv_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(b)))
+        return {"ms": ms.value, "launches": int(n.value), "bytes": b.value}
+
+    def tensor(self):
+        """Zero-copy torch view (complex) of the state, or None without torch."""
+        if self._buf is None:
+            return None
+        torch = _torch()
+        return torch.view_as_complex(self._buf.view(-1, 2))[: 1 << self.n]
+
+
+def plan_info(ops: np.ndarray, n: int, dtype: str = "c64", pool=None, tile_bits: int = 0, low_bits: int = 0,
+              max_pass_gates: int = 0) -> dict:
+    """Host-only lowering statistics (``sv_plan_info``); needs no GPU."""
+    ops = _ops(ops)
+    p = None if pool is None else np.ascontiguousarray(pool, dtype=np.complex128)
+    s = ProgramStats()
+    _check(lib().sv_plan_info(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(p),
+                              0 if p is None else p.size, tile_bits, low_bits, max_pass_gates, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in ProgramStats._fields_}
+
+
+def version() -> str:
+    return lib().sv_version().decode()

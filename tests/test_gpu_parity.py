@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2604_11599_gb300 import workloads as W
+from paper_2604_11599_gb300.ir import Circuit, Gate
+
+from paritylib import AMP_TOL, EXP_TOL, BAND, compare_run
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["c64", "c128"]
+
+
+@pytest.fixture(scope="module")
+def svmod():
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import sv
+
+    return sv
+
+
+# --------------------------------------------------------------------------- static circuits
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 11, 12, 13, 15, 17])
+def test_static_every_gate(svmod, orc, dtype, n):
+    """Random circuits over the whole gate vocabulary incl. dense 1..4-qubit unitaries
+    and parameter references, several tiles and register stages."""
+    for seed in range(3):
+        k = min(n, 1 + (seed + n) % 4)
+        c = W.random_static(100 * n + seed, n, 60, dense_k=k, params=5)
+        params = np.random.default_rng(seed).uniform(-3, 3, size=5)
+        with svmod.State(n, dtype) as st:
+            st.set_dense_pool(c.pool)
+            compare_run(st, orc, c.ops, n, dtype, params=params, pool=c.pool)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("tile,low", [(10, 2), (10, 5), (12, 3), (12, 6), (13, 4), (14, 5)])
+def test_tuning_does_not_change_results(svmod, orc, dtype, tile, low):
+    n = 16
+    c = W.layered(3, n, layers=6)
+    with svmod.State(n, dtype) as st:
+        st.set_tuning(tile, low, 0)
+        compare_run(st, orc, c.ops, n, dtype, seed=1)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_max_pass_gates_one_gate_per_pass(svmod, orc, dtype):
+    n = 14
+    c = W.random_static(7, n, 50, params=0)
+    with svmod.State(n, dtype) as st:
+        st.set_tuning(0, 0, 1)
+        compare_run(st, orc, c.ops, n, dtype)
+
+
+# --------------------------------------------------------------------------- dynamic circuits
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [2, 4, 6, 9, 13, 16])
+def test_random_dynamic_programs(svmod, orc, dtype, n):
+    """Measures, resets, nested if/else on 1-3 bit predicates, loops, dense gates."""
+    stats = {}
+    with svmod.State(n, dtype) as st:
+        for seed in range(6):
+            c = W.random_dynamic(1000 * n + seed, n, n_ops=70, dense_k=min(n, 2))
+            st.set_dense_pool(c.pool)
+            for shot in range(4):
+                compare_run(st, orc, c.ops, n, dtype, seed=seed, stream=n, shot=shot, pool=c.pool, stats=stats)
+    assert stats["draws"] > 20
+
+
+def test_plain_small_config_records(svmod, orc):
+    """Plain path, complex128, n=5, 1,000 shots of the seeded feed-forward program:
+    every record bit-exact (near-threshold draws counted)."""
+    c = W.plain_small()
+    stats = {}
+    with svmod.State(5, "c128") as st:
+        for shot in range(1000):
+            compare_run(st, orc, c.ops, 5, "c128", seed=0, shot=shot, check_amps=(shot % 50 == 0), stats=stats)
+    assert stats["draws"] == 5000
+    assert stats.get("forced", 0) == 0
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [12, 18, 21])
+def test_layered_config_small_sizes(svmod, orc, dtype, n):
+    """The layered measure/reset/cond workload at sizes the oracle runs in seconds."""
+    c = W.layered(2, n, layers=20 if n <= 18 else 8)
+    with svmod.State(n, dtype) as st:
+        for shot in range(2):
+            compare_run(st, orc, c.ops, n, dtype, seed=0, shot=shot)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_conditional_reset_always_zero(svmod, dtype):
+    """Fig. 2 / Sec. IV-C conditional reset, 10^4 shots: |0> on every shot."""
+    for minus in (True, False):
+        c = W.conditional_reset(minus)
+        with svmod.State(1, dtype) as st:
+            ones = 0
+            for s in range(0, 10000, 97):
+                ones += st.run(c.ops, shot=s) & 1
+                a = st.amplitudes()
+                assert abs(a[1]) == 0 and abs(abs(a[0]) - 1) < AMP_TOL[dtype]
+            cregs, _ = st.sample(c.ops, 10000)
+            assert 4700 < int(cregs.sum()) < 5300
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_teleportation_uncompute(svmod, dtype):
+    rng = np.random.default_rng(4)
+    with svmod.State(3, dtype) as st:
+        seen = set()
+        for trial in range(5):
+            th, ph, la = rng.uniform(0, 2 * math.pi, size=3)
+            c = W.teleport_uncompute(th, ph, la)
+            for s in range(16):
+                seen.add(st.run(c.ops, shot=s, stream_id=trial))
+                a = st.amplitudes().reshape(2, 4)
+                assert np.sum(np.abs(a[1]) ** 2) < 10 * AMP_TOL[dtype] ** 2 + 1e-12
+        assert seen == {0, 1, 2, 3}
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_edge_programs(svmod, orc, dtype):
+    n = 15
+    cases = []
+    c = Circuit(n)  # empty program
+    cases.append(c)
+    c = Circuit(n)  # measurement first, then measure the same qubit again
+    c.measure(3, 0); c.measure(3, 1); c.reset(3); c.measure(3, 2)
+    cases.append(c)
+    c = Circuit(n)  # reset with outcome 1 on qubits outside the tile (tile-pair path)
+    for q in (14, 13, 12):
+        c.x(q)
+    c.h(14)
+    c.reset(14); c.reset(13); c.reset(12)
+    for q in range(5):
+        c.h(q)
+    c.measure(0, 0)
+    cases.append(c)
+    c = Circuit(n)  # a measurement group on more than four qubits
+    for q in range(n):
+        c.h(q)
+    for q in range(7):
+        c.measure(q, q)
+    c.cond(0b11, 0b01, lambda: c.x(9), lambda: c.z(9))
+    cases.append(c)
+    c = Circuit(n)  # predicate decided inside the same measurement group
+    c.h(0); c.h(1)
+    c.measure(0, 0)
+    c.cond(1, 1, lambda: c.measure(1, 1), lambda: c.reset(1))
+    c.h(2)
+    cases.append(c)
+    c = Circuit(n)  # loop(0), loop with only control flow, cond with empty then
+    c.loop(0, lambda: c.x(0))
+    c.h(5)
+    c.measure(5, 5)
+    c.cond(1 << 5, 1 << 5, lambda: None, lambda: c.x(6))
+    c.loop(3, lambda: c.cond(1 << 5, 0, lambda: (c.h(5), c.measure(5, 5))))
+    cases.append(c)
+    c = Circuit(n)  # program ending in a reset (final projector flush)
+    c.h(10); c.cx(10, 2); c.reset(10)
+    cases.append(c)
+    with svmod.State(n, dtype) as st:
+        for c in cases:
+            for shot in range(5):
+                compare_run(st, orc, c.ops, n, dtype, seed=3, shot=shot)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_errors_are_status_codes(svmod, dtype):
+    with svmod.State(4, dtype) as st:
+        c = Circuit(5)
+        c.x(4)
+        with pytest.raises(svmod.SVError, match="SV_ERR_ARG"):
+            st.run(c.ops)
+        c = Circuit(4)
+        c.rx(0, __import__("paper_2604_11599_gb300.ir", fromlist=["Param"]).Param(3))
+        with pytest.raises(svmod.SVError, match="SV_ERR_ARG"):
+            st.run(c.ops, params=[0.1])
+        c = Circuit(4)
+        c.measure(0, 64)
+        with pytest.raises(svmod.SVError, match="SV_ERR_ARG"):
+            st.run(c.ops)
+        ops = Circuit(4).cond(1, 1, lambda: None).ops
+        ops["then_len"] = 5
+        with pytest.raises(svmod.SVError, match="SV_ERR_ARG"):
+            st.run(ops)
+        # the handle stays usable after errors
+        c = Circuit(4)
+        c.x(1)
+        assert st.run(c.ops) == 0
+        assert abs(st.amplitudes()[2]) == pytest.approx(1.0)
+    with pytest.raises(svmod.SVError):
+        svmod.State(40, dtype)
+
+
+# --------------------------------------------------------------------------- sampling and expval
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [3, 10, 14])
+def test_terminal_samples_vs_oracle(svmod, orc, dtype, n):
+    c = W.random_static(55 + n, n, 40)
+    with svmod.State(n, dtype) as st:
+        st.run(c.ops)
+        got = st.sample_state(2000, seed=4, stream_id=1)
+    ref = orc.run(c.ops, n)
+    want, margin = orc.sample(ref.psi, 2000, seed=4, stream=1)
+    band = 1e-12 if dtype == "c128" else 1e-4
+    bad = (got != want) & (margin > band)
+    assert not bad.any(), f"{int(bad.sum())} samples differ away from CDF ties"
+    assert (got == want).mean() > 0.99
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sample_program_shots(svmod, orc, dtype):
+    c = W.plain_small(seed=3)
+    with svmod.State(5, dtype) as st:
+        cregs, bits = st.sample(c.ops, 200, seed=2, terminal=True)
+    rc, rb, margins = orc.run_shots(c.ops, 5, 200, seed=2, terminal=True)
+    ok = margins > BAND[dtype]
+    assert (cregs[ok] == rc[ok]).all()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [4, 11, 16])
+def test_expval_vs_oracle(svmod, orc, dtype, n):
+    c = W.random_static(77 + n, n, 60)
+    terms = W.heisenberg_fields(seed=9, n=n, n_terms=10 * n)
+    with svmod.State(n, dtype) as st:
+        st.run(c.ops)
+        tot, per = st.expval(terms)
+    ref = orc.run(c.ops, n)
+    rper, rtot = orc.expval(ref.psi, terms)
+    assert np.max(np.abs(per - rper)) <= EXP_TOL[dtype]
+    assert abs(tot - rtot) <= EXP_TOL[dtype] * max(1.0, float(np.abs(terms["coeff"]).sum()))
+
+
+def test_state_tensor_view_is_zero_copy(svmod):
+    import torch
+
+    with svmod.State(6, "c64") as st:
+        c = Circuit(6)
+        c.x(2)
+        st.run(c.ops)
+        t = st.tensor()
+        assert t.is_cuda and t.dtype == torch.complex64
+        assert abs(complex(t[4].item()) - 1) < 1e-7
