@@ -756,7 +756,7 @@ cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm) {
   } else {
     if (!attr_set[d])
       e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int((size_t(1) << MAX_TILE_BITS) * sizeof(double2)));
+                               int((size_t(1) << (MAX_TILE_BITS - 1)) * sizeof(double2)));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass<double>, PASS_THREADS,
                                                         (size_t(1) << m) * sizeof(double2));

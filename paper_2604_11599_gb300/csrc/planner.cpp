@@ -507,7 +507,8 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   P.n_int = std::max(n, 4);
   P.dtype = dtype;
   int tb = tune.tile_bits > 0 ? tune.tile_bits : 12;
-  tb = std::min(std::max(tb, 10), MAX_TILE_BITS);
+  // shared-memory tile: 2^14 x 8 B (complex64) or 2^13 x 16 B (complex128) at most
+  tb = std::min(std::max(tb, 10), dtype == SV_C64 ? MAX_TILE_BITS : MAX_TILE_BITS - 1);
   P.m = std::min(P.n_int, tb);
   int lb = tune.low_bits > 0 ? tune.low_bits : (dtype == SV_C64 ? 5 : 4);
   P.L = std::min(std::max(lb, 2), P.m);
@@ -581,8 +582,10 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     if (s.gates.empty() && !s.has_group) continue;
     b.emit_segment(s);
   }
-  // a projector left pending by a final measurement group is applied by a flush pass
-  if (!P.passes.empty() && P.passes.back().nc > 0) {
+  // A projector can still be pending at the end (a final measurement group,
+  // or later passes whose gates were all predicated off): a flush pass
+  // applies it.  When nothing is pending its CTAs return at once.
+  if (n_draws > 0) {
     P.needs_flush = true;
     std::vector<int> tq;
     for (int q = 0; q < P.m; ++q) tq.push_back(q);

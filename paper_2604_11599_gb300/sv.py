@@ -156,7 +156,7 @@ class State:
         torch = _torch()
         n_int = max(self.n, 4)
         self._buf = buffer
-        if self._buf is None and torch is not None and torch.cuda.is_available():
+        if self._buf is None and torch is not None and torch.cuda.is_available() and 1 <= self.n <= 34:
             real = torch.float32 if dtype == "c64" else torch.float64
             self._buf = torch.empty(2 << n_int, dtype=real, device="cuda")
         ptr, nbytes = None, 0
