@@ -198,6 +198,34 @@ sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t s
  */
 sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* total, double* per_term);
 
+/*
+ * Pauli expectation values that allocate no device memory.  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot let a
+ * library call cudaMalloc: applications whose device memory is entirely
+ * handed out by their own allocator or a fixed pool, and latency-critical
+ * loops that cannot afford cudaMalloc's implicit synchronisation with the
+ * device.  sv_expval allocates its scratch; this variant keeps it in a
+ * static array inside the library's device image instead (262,400 bytes on
+ * every GPU that loads libsv, held until the process exits).
+ *
+ *   dev_state  device pointer to 2^n amplitudes of `dtype` (16-byte aligned),
+ *              e.g. the buffer of a state created with sv_create; read only.
+ *   terms      host array of n_terms Pauli strings, read during the call;
+ *              n_terms <= 64 (larger requests return SV_ERR_ARG).
+ *   dev_out    caller-owned device array of n_terms doubles; receives
+ *              <P_t> for each term (no coefficient applied), in term order.
+ *   cuda_stream  stream to enqueue on (NULL: legacy default stream).
+ * Asynchronous: it returns once the work is enqueued.  The first call on a
+ * device looks up the static array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array, so calls that overlap on the GPU (e.g.
+ * on different streams) race and give wrong results; calls in stream order
+ * are safe.  Errors: SV_ERR_ARG for bad n, dtype, pointers, alignment or
+ * term count; SV_ERR_CUDA if a launch fails (message in sv_last_error()).
+ */
+sv_status sv_expval_static(const void* dev_state, int n, sv_dtype dtype, const sv_pauli* terms, size_t n_terms,
+                           double* dev_out, void* cuda_stream);
+
 /* Copy amplitudes [first, first+count) to / from host memory (amplitude-size elements). */
 sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count);
 sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count);

@@ -73,6 +73,11 @@ uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull
 
 }  // namespace
 
+namespace svapi {
+// lets other translation units report through sv_last_error()
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace svapi
+
 struct sv_program {
   sv_state* owner = nullptr;
   svp::Plan plan;

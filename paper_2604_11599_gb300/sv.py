@@ -70,6 +70,7 @@ def lib():
         "sv_sample": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, vp], st),
         "sv_sample_state": ([vp, u64, u64, u64, u64, vp], st),
         "sv_expval": ([vp, vp, sz, vp, vp], st),
+        "sv_expval_static": ([vp, i32, i32, vp, sz, vp, vp], st),
         "sv_get_amplitudes": ([vp, vp, sz, sz], st),
         "sv_set_amplitudes": ([vp, vp, sz, sz], st),
         "sv_state_buffer": ([vp, C.POINTER(vp), C.POINTER(sz)], st),
@@ -301,6 +302,18 @@ def plan_info(ops: np.ndarray, n: int, dtype: str = "c64", pool=None, tile_bits:
     _check(lib().sv_plan_info(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(p),
                               0 if p is None else p.size, tile_bits, low_bits, max_pass_gates, C.byref(s)))
     return {k: getattr(s, k) for k, _ in ProgramStats._fields_}
+
+
+def sv_expval_static(dev_state_ptr: int, n: int, dtype: str, terms: np.ndarray, dev_out_ptr: int,
+                     stream: Optional[int] = None) -> None:
+    """``sv_expval_static``: per-term <P_t> of a device-resident state into a
+    caller-owned device array, with no device allocation by the library (for
+    callers whose device memory is owned by their own allocator or pool)."""
+    terms = np.ascontiguousarray(terms)
+    if terms.dtype != PAULI_DTYPE:
+        raise TypeError("terms must be an array of ir.PAULI_DTYPE records")
+    _check(lib().sv_expval_static(dev_state_ptr, n, SV_C64 if dtype == "c64" else SV_C128, _ptr(terms), len(terms),
+                                  dev_out_ptr, stream))
 
 
 def version() -> str:
