@@ -125,7 +125,7 @@ typedef struct sv_program_stats {
 /*
  * Create a state of n qubits (1 <= n <= 34) in |0...0>.
  *   dev_buf  NULL: the library allocates 2^n amplitudes on the current device.
- *            Otherwise caller-owned device memory of `bytes` >= 2^max(n,4) *
+ *            Otherwise caller-owned device memory of `bytes` >= 2^max(n,10) *
  *            amplitude size, which must outlive the handle (e.g. a torch tensor).
  * On success *out receives the handle.  SV_ERR_ARG for bad n/dtype/size,
  * SV_ERR_OOM if allocation fails.

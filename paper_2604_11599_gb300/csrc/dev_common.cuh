@@ -28,31 +28,34 @@ template <typename V>
 __device__ __forceinline__ V cadd(V a, V b) { return mkc(a.x + b.x, a.y + b.y); }
 
 // ---------------------------------------------------------------------- shared-memory swizzle
-// Tile-local amplitude index x is stored at x ^ fold(x >> B), fold = XOR of the
-// B-bit groups, so tile-local bit p lands on bank bit (p mod B).  B = 4 for
-// 8-byte amplitudes (16 per 128-byte row), 3 for 16-byte amplitudes.  The map
-// is linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).
-template <typename T> struct SwzBits;
-template <> struct SwzBits<float> { static constexpr int B = 4; };
-template <> struct SwzBits<double> { static constexpr int B = 3; };
+// Tile layout in 16-byte granules: granule g at g ^ fold(g >> 3), fold = XOR
+// of 3-bit groups (the same map as tile_swizzle in sv_plan.h).  A = log2
+// amplitudes per granule.  Linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).
+template <typename T> struct GranuleBits;
+template <> struct GranuleBits<float> { static constexpr int A = 1; };
+template <> struct GranuleBits<double> { static constexpr int A = 0; };
 
 template <typename T>
 __device__ __forceinline__ uint32_t swz(uint32_t x) {
-  constexpr int B = SwzBits<T>::B;
-  uint32_t y = x >> B, f = 0;
+  constexpr int A = GranuleBits<T>::A;
+  uint32_t y = x >> (A + 3), f = 0;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    f ^= y & ((1u << B) - 1);
-    y >>= B;
+    f ^= y & 7u;
+    y >>= 3;
   }
-  return x ^ f;
+  return x ^ (f << A);
 }
 
-// scatter the low bits of v to the positions pos[0..nb-1]
-__device__ __forceinline__ uint32_t deposit_bits(uint32_t v, const uint8_t* pos, int nb) {
-  uint32_t out = 0;
-  for (int k = 0; k < nb; ++k) out |= ((v >> k) & 1u) << pos[k];
-  return out;
+// Ampere-style asynchronous 16-byte global -> shared copies (no register staging)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------------- Philox4x64-10

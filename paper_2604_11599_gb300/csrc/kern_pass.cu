@@ -167,45 +167,42 @@ __device__ __forceinline__ void g_d16(V* a, const V* m) {
   for (int r = 0; r < 16; ++r) a[r] = w[r];
 }
 
-#define SVK_1Q(FN)                  \
-  switch (g.p0) {                   \
-    case 0: FN<0>(a, mt); break;    \
-    case 1: FN<1>(a, mt); break;    \
-    case 2: FN<2>(a, mt); break;    \
-    default: FN<3>(a, mt); break;   \
-  }
+#define SVK_K1(OP, FN)                          \
+  case OP * 16 + 0: FN<0>(a, mt); break;        \
+  case OP * 16 + 4: FN<1>(a, mt); break;        \
+  case OP * 16 + 8: FN<2>(a, mt); break;        \
+  case OP * 16 + 12: FN<3>(a, mt); break;
 
-#define SVK_2Q(FN)                     \
-  switch (g.p0 * 4 + g.p1) {           \
-    case 1: FN<0, 1>(a, mt); break;    \
-    case 2: FN<0, 2>(a, mt); break;    \
-    case 3: FN<0, 3>(a, mt); break;    \
-    case 4: FN<1, 0>(a, mt); break;    \
-    case 6: FN<1, 2>(a, mt); break;    \
-    case 7: FN<1, 3>(a, mt); break;    \
-    case 8: FN<2, 0>(a, mt); break;    \
-    case 9: FN<2, 1>(a, mt); break;    \
-    case 11: FN<2, 3>(a, mt); break;   \
-    case 12: FN<3, 0>(a, mt); break;   \
-    case 13: FN<3, 1>(a, mt); break;   \
-    default: FN<3, 2>(a, mt); break;   \
-  }
+#define SVK_K2(OP, FN)                          \
+  case OP * 16 + 1: FN<0, 1>(a, mt); break;     \
+  case OP * 16 + 2: FN<0, 2>(a, mt); break;     \
+  case OP * 16 + 3: FN<0, 3>(a, mt); break;     \
+  case OP * 16 + 4: FN<1, 0>(a, mt); break;     \
+  case OP * 16 + 6: FN<1, 2>(a, mt); break;     \
+  case OP * 16 + 7: FN<1, 3>(a, mt); break;     \
+  case OP * 16 + 8: FN<2, 0>(a, mt); break;     \
+  case OP * 16 + 9: FN<2, 1>(a, mt); break;     \
+  case OP * 16 + 11: FN<2, 3>(a, mt); break;    \
+  case OP * 16 + 12: FN<3, 0>(a, mt); break;    \
+  case OP * 16 + 13: FN<3, 1>(a, mt); break;    \
+  case OP * 16 + 14: FN<3, 2>(a, mt); break;
 
+// one switch on key = op * 16 + p0 * 4 + p1 selects the gate and its register positions
 template <typename V>
-__device__ __forceinline__ void apply_gate(V* a, const DGate& g, const V* mt) {
-  switch (g.op) {
-    case OP_U: SVK_1Q(g_u) break;
-    case OP_R: SVK_1Q(g_r) break;
-    case OP_RX: SVK_1Q(g_rx) break;
-    case OP_D: SVK_1Q(g_d) break;
-    case OP_X: SVK_1Q(g_x) break;
-    case OP_CU: SVK_2Q(g_cu) break;
-    case OP_CX: SVK_2Q(g_cx) break;
-    case OP_CZ: SVK_2Q(g_cz) break;
-    case OP_CD: SVK_2Q(g_cd) break;
-    case OP_SWAP: SVK_2Q(g_swap) break;
-    case OP_U4: SVK_2Q(g_u4) break;
-    case OP_D16: g_d16(a, mt); break;
+__device__ __forceinline__ void apply_gate(V* a, uint32_t key, const V* mt) {
+  switch (key) {
+    SVK_K1(OP_U, g_u)
+    SVK_K1(OP_R, g_r)
+    SVK_K1(OP_RX, g_rx)
+    SVK_K1(OP_D, g_d)
+    SVK_K1(OP_X, g_x)
+    SVK_K2(OP_CU, g_cu)
+    SVK_K2(OP_CX, g_cx)
+    SVK_K2(OP_CZ, g_cz)
+    SVK_K2(OP_CD, g_cd)
+    SVK_K2(OP_SWAP, g_swap)
+    SVK_K2(OP_U4, g_u4)
+    case OP_D16 * 16: g_d16(a, mt); break;
     default: break;
   }
 }
@@ -377,264 +374,9 @@ __device__ __forceinline__ int transpose_slot(int lane) {
   return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PASS_THREADS) k_pass(PassArgs A, int pi) {
-  using V = typename CxT<T>::V;
-  using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tile = reinterpret_cast<V*>(smem_raw);
-  __shared__ DPass sp;
-  __shared__ DGate sg[MAX_PASS_GATES];
-  __shared__ uint8_t sact[MAX_PASS_GATES];
-  __shared__ __align__(16) V smat[MAX_PASS_MAT];
-  __shared__ uint64_t schunk[512];
-  __shared__ double ctab[16];
-  __shared__ double wsum[PASS_THREADS / 32][16];
-  __shared__ double tile16[16];
-  __shared__ int s_last;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int bd = blockDim.x;
-  if (tid == 0) sp = A.passes[pi];
-  if (tid < 16) ctab[tid] = 0.0;
-  __syncthreads();
-  const int m = sp.m, L = sp.L, n = A.n;
-
-  int act_any = 0;
-  for (int g = tid; g < int(sp.ng); g += bd) {
-    const DGate d = A.gates[sp.g0 + g];
-    sg[g] = d;
-    const uint8_t on = d.flag < 0 ? 1 : (A.flags[d.flag] ? 1 : 0);
-    sact[g] = on;
-    act_any |= on;
-  }
-  const bool any_gate = __syncthreads_or(act_any) != 0;
-  int need = 0;
-  if (sp.gk) {
-    if (sp.group_always) need = 1;
-    else
-      for (int c = tid; c < int(sp.nc); c += bd) {
-        const DScalar s = A.scalars[sp.c0 + c];
-        if (s.kind != S_COND && (s.flag < 0 || A.flags[s.flag])) need = 1;
-      }
-  }
-  const bool needed = __syncthreads_or(need) != 0;
-
-  const Ctrl* C = A.ctrl;
-  const uint64_t pm = C->pm, pv = C->pv, px = C->px;
-  const double ps = C->ps;
-  const bool ident = (pm == 0 && px == 0 && ps == 1.0);
-  const bool do_store = any_gate || (sp.flush && !ident);
-  const bool do_work = do_store || needed;
-  const bool need_ticket = sp.nc > 0 || (do_store && !ident);
-
-  if (do_work) {
-    if (any_gate)
-      for (int i = tid; i < int(sp.nmat); i += bd) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
-    const int hb = m - L;
-    for (int c = tid; c < (1 << hb); c += bd) {
-      uint64_t o = 0;
-      for (int k = 0; k < hb; ++k)
-        if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
-      schunk[c] = o;
-    }
-    __syncthreads();
-
-    uint64_t tmask = 0;
-    for (int j = 0; j < m; ++j) tmask |= 1ull << sp.tq[j];
-    const uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
-    const uint64_t omask = full & ~tmask;
-    const uint64_t ntiles = 1ull << (n - m);
-    const uint64_t xo = px & omask;  // part of the pending X that moves whole tiles
-    const bool pair = xo != 0;
-    const uint64_t xt = pair ? pext64(xo, omask) : 0;
-    const int hbit = pair ? __ffsll((long long)xt) - 1 : 0;
-    const uint64_t nunits = pair ? (ntiles >> 1) : ntiles;
-    const T sc = T(ps);
-    const int ngrp = 1 << (m - REG_BITS);
-    const uint32_t kmask = (1u << sp.kin) - 1;
-
-    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-      uint64_t tl[2];
-      int cnt = 1;
-      if (!pair) {
-        tl[0] = u;
-      } else {
-        const uint64_t lo = u & ((1ull << hbit) - 1);
-        const uint64_t t0 = ((u >> hbit) << (hbit + 1)) | lo;
-        const uint64_t t1 = t0 ^ xt;
-        const uint64_t b0 = pdep64(t0, omask);
-        const bool t0_reads = (((b0 ^ px) & pm & omask) == (pv & omask));
-        tl[0] = t0_reads ? t0 : t1;  // the tile that reads its partner goes first
-        tl[1] = t0_reads ? t1 : t0;
-        cnt = 2;
-      }
-      for (int k = 0; k < cnt; ++k) {
-        const uint64_t base = pdep64(tl[k], omask);
-        const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
-
-        // ---- load (with the pending projector)
-        if constexpr (sizeof(T) == 4) {
-          const int nvec = 1 << (m - 1), vl = L - 1;
-          const float4* gs = reinterpret_cast<const float4*>(A.state);
-          for (int v = tid; v < nvec; v += bd) {
-            const uint32_t ch = uint32_t(v) >> vl, w = uint32_t(v) & ((1u << vl) - 1);
-            const uint32_t loc = (ch << L) | (w << 1);
-            const uint64_t gi = base | schunk[ch] | (uint64_t(w) << 1);
-            float2 x0, x1;
-            if (zero_tile) {
-              x0 = x1 = make_float2(0.f, 0.f);
-            } else if (ident) {
-              const float4 q = __ldcg(gs + (gi >> 1));
-              x0 = make_float2(q.x, q.y);
-              x1 = make_float2(q.z, q.w);
-            } else {
-              const uint64_t s0 = gi ^ px;
-              const bool ok0 = (s0 & pm) == pv, ok1 = ((s0 ^ 1ull) & pm) == pv;
-              float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (ok0 || ok1) q = __ldcg(gs + (s0 >> 1));
-              const float2 e0 = make_float2(q.x, q.y), e1 = make_float2(q.z, q.w);
-              x0 = (s0 & 1) ? e1 : e0;
-              x1 = (s0 & 1) ? e0 : e1;
-              x0 = ok0 ? make_float2(x0.x * sc, x0.y * sc) : make_float2(0.f, 0.f);
-              x1 = ok1 ? make_float2(x1.x * sc, x1.y * sc) : make_float2(0.f, 0.f);
-            }
-            const uint32_t p = swz<T>(loc);
-            float4* dst = reinterpret_cast<float4*>(tile + (p & ~1u));
-            *dst = (p & 1) ? make_float4(x1.x, x1.y, x0.x, x0.y) : make_float4(x0.x, x0.y, x1.x, x1.y);
-          }
-        } else {
-          const int nvec = 1 << m;
-          const double2* gs = reinterpret_cast<const double2*>(A.state);
-          for (int v = tid; v < nvec; v += bd) {
-            const uint32_t ch = uint32_t(v) >> L, w = uint32_t(v) & ((1u << L) - 1);
-            const uint32_t loc = (ch << L) | w;
-            const uint64_t gi = base | schunk[ch] | uint64_t(w);
-            double2 x;
-            if (zero_tile) {
-              x = make_double2(0, 0);
-            } else if (ident) {
-              x = __ldcg(gs + gi);
-            } else {
-              const uint64_t s0 = gi ^ px;
-              if ((s0 & pm) == pv) {
-                x = __ldcg(gs + s0);
-                x.x *= sc;
-                x.y *= sc;
-              } else {
-                x = make_double2(0, 0);
-              }
-            }
-            tile[swz<T>(loc)] = x;
-          }
-        }
-        __syncthreads();
-
-        // ---- gate stages
-        if (any_gate) {
-          for (uint32_t si = 0; si < sp.ns; ++si) {
-            const DStage st = A.stages[sp.s0 + si];
-            uint32_t roff[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) roff[j] = swz<T>(deposit_bits(uint32_t(j), st.reg, REG_BITS));
-            for (int grp = tid; grp < ngrp; grp += bd) {
-              const uint32_t b = swz<T>(deposit_bits(uint32_t(grp), st.thr, m - REG_BITS));
-              V a[16];
-#pragma unroll
-              for (int j = 0; j < 16; ++j) a[j] = tile[b ^ roff[j]];
-              for (int g = st.g0; g < st.g0 + st.ng; ++g)
-                if (sact[g]) apply_gate(a, sg[g], smat + sg[g].mat);
-#pragma unroll
-              for (int j = 0; j < 16; ++j) tile[b ^ roff[j]] = a[j];
-            }
-            __syncthreads();
-          }
-        }
-
-        // ---- measurement-group table
-        if (needed) {
-          Acc acc[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
-          uint32_t roff[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) roff[j] = swz<T>(deposit_bits(uint32_t(j), sp.red_reg, REG_BITS));
-          for (int grp = tid; grp < ngrp; grp += bd) {
-            const uint32_t b = swz<T>(deposit_bits(uint32_t(grp), sp.red_thr, m - REG_BITS));
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const V x = tile[b ^ roff[j]];
-              acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
-            }
-          }
-          const Acc r = warp_transpose_reduce16(acc, lane);
-          if ((lane & 1) == 0) wsum[warp][transpose_slot(lane)] = double(r);
-          __syncthreads();
-          if (tid < 16) {
-            double s = 0;
-            for (int w = 0; w < bd / 32; ++w) s += wsum[w][tid];
-            tile16[tid] = s;
-          }
-          __syncthreads();
-          if (tid < (1 << sp.kin)) {
-            uint32_t ob = 0;
-            for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
-            double s = 0;
-            for (int j = 0; j < 16; ++j)
-              if ((uint32_t(j) & kmask) == uint32_t(tid)) s += tile16[j];
-            ctab[tid | (ob << sp.kin)] += s;
-          }
-        }
-
-        // ---- store
-        if (do_store) {
-          if constexpr (sizeof(T) == 4) {
-            const int nvec = 1 << (m - 1), vl = L - 1;
-            float4* gs = reinterpret_cast<float4*>(A.state);
-            for (int v = tid; v < nvec; v += bd) {
-              const uint32_t ch = uint32_t(v) >> vl, w = uint32_t(v) & ((1u << vl) - 1);
-              const uint32_t loc = (ch << L) | (w << 1);
-              const uint64_t gi = base | schunk[ch] | (uint64_t(w) << 1);
-              const uint32_t p = swz<T>(loc);
-              const float4 q = *reinterpret_cast<const float4*>(tile + (p & ~1u));
-              __stcg(gs + (gi >> 1), (p & 1) ? make_float4(q.z, q.w, q.x, q.y) : q);
-            }
-          } else {
-            const int nvec = 1 << m;
-            double2* gs = reinterpret_cast<double2*>(A.state);
-            for (int v = tid; v < nvec; v += bd) {
-              const uint32_t ch = uint32_t(v) >> L, w = uint32_t(v) & ((1u << L) - 1);
-              const uint32_t loc = (ch << L) | w;
-              const uint64_t gi = base | schunk[ch] | uint64_t(w);
-              __stcg(gs + gi, tile[swz<T>(loc)]);
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
-
-  if (!need_ticket) return;
-  if (needed && tid < 16) A.partials[blockIdx.x * 16 + tid] = ctab[tid];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned t = atomicAdd(&A.ctrl->ticket, 1u);
-    s_last = (t == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (needed && tid < 16) {
-    double s = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(A.partials + b * 16 + tid);
-    ctab[tid] = s;
-  }
-  __syncthreads();
-  if (tid != 0) return;
-
-  // ---- scalar phase: draws, classical register, predicates (one thread)
+// ---- scalar phase (one thread of the last CTA): draws, classical register, predicates
+__device__ __noinline__ void scalar_phase(const PassArgs& A, const DPass& sp, const double* ctab, bool do_store,
+                                          uint64_t pm, uint64_t pv, uint64_t px, double ps) {
   Ctrl* W = A.ctrl;
   uint64_t creg = W->creg, mc = W->m;
   uint64_t npm = do_store ? 0 : pm, npv = do_store ? 0 : pv, npx = do_store ? 0 : px;
@@ -707,18 +449,355 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassArgs A, int pi) {
   __threadfence();
 }
 
+// register offsets of a stage: off[j] = XOR of R[r] over the set bits r of j
+__device__ __forceinline__ void reg_offsets(const uint16_t* R, uint32_t (&off)[16]) {
+  off[0] = 0;
+#pragma unroll
+  for (int j = 1; j < 16; ++j) off[j] = off[j & (j - 1)] ^ R[__ffs(j) - 1];
+}
+
+template <int GB>
+__device__ __forceinline__ uint32_t group_base(const uint16_t* E, uint32_t g) {
+  uint32_t b = 0;
+#pragma unroll
+  for (int k = 0; k < GB; ++k)
+    if ((g >> k) & 1u) b ^= E[k];
+  return b;
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_pass(const PassArgs A, const int pi) {
+  using V = typename CxT<T>::V;
+  using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
+  constexpr int GB = M - REG_BITS;  // group-index bits of a stage
+  constexpr int NGRP = 1 << GB;     // 16-amplitude groups per tile
+  constexpr bool DB = (size_t(2) << M) * sizeof(V) <= size_t(128) * 1024;  // double-buffered tiles fit
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tile = reinterpret_cast<V*>(smem_raw);
+  __shared__ DPass sp;
+  __shared__ uint32_t sgk[MAX_PASS_GATES];  // key | active << 8 | matrix offset << 16
+  __shared__ __align__(16) V smat[MAX_PASS_MAT];
+  __shared__ uint64_t schunk[512];
+  __shared__ double ctab[16];
+  __shared__ double wsum[PASS_THREADS / 32][16];
+  __shared__ double tile16[16];
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) sp = A.passes[pi];
+  if (tid < 16) ctab[tid] = 0.0;
+  __syncthreads();
+  const int L = sp.L, n = A.n;
+
+  int act_any = 0;
+  for (int g = tid; g < int(sp.ng); g += PASS_THREADS) {
+    const DGate d = A.gates[sp.g0 + g];
+    const uint32_t on = d.flag < 0 ? 1u : (A.flags[d.flag] ? 1u : 0u);
+    sgk[g] = uint32_t(d.key) | (on << 8) | (d.mat << 16);
+    act_any |= int(on);
+  }
+  const bool any_gate = __syncthreads_or(act_any) != 0;
+  int need = 0;
+  if (sp.gk) {
+    if (sp.group_always) need = 1;
+    else
+      for (int c = tid; c < int(sp.nc); c += PASS_THREADS) {
+        const DScalar sc = A.scalars[sp.c0 + c];
+        if (sc.kind != S_COND && (sc.flag < 0 || A.flags[sc.flag])) need = 1;
+      }
+  }
+  const bool needed = __syncthreads_or(need) != 0;
+
+  const Ctrl* C = A.ctrl;
+  const uint64_t pm = C->pm, pv = C->pv, px = C->px;
+  const double ps = C->ps;
+  const bool ident = (pm == 0 && px == 0 && ps == 1.0);
+  const bool do_store = any_gate || (sp.flush && !ident);
+  const bool do_work = do_store || needed;
+  const bool need_ticket = sp.nc > 0 || (do_store && !ident);
+
+  if (do_work) {
+    if (any_gate)
+      for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
+    const int hb = M - L;
+    for (int c = tid; c < (1 << hb); c += PASS_THREADS) {
+      uint64_t o = 0;
+      for (int k = 0; k < hb; ++k)
+        if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
+      schunk[c] = o;
+    }
+    __syncthreads();
+
+    uint64_t tmask = 0;
+    for (int j = 0; j < M; ++j) tmask |= 1ull << sp.tq[j];
+    const uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t omask = full & ~tmask;
+    const uint64_t ntiles = 1ull << (n - M);
+    const uint64_t xo = px & omask;  // part of the pending X that moves whole tiles
+    const bool pair = xo != 0;
+    const uint64_t xt = pair ? pext64(xo, omask) : 0;
+    const int hbit = pair ? __ffsll((long long)xt) - 1 : 0;
+    const uint64_t nunits = pair ? (ntiles >> 1) : ntiles;
+    const T sc = T(ps);
+    const uint32_t kmask = (1u << sp.kin) - 1;
+
+    // tile-independent parts of this thread's load/store addresses
+    constexpr int VB = sizeof(T) == 4 ? 9 : 8;   // log2 amplitudes covered by one sweep of 256 threads
+    constexpr int NVT = 1 << (M - VB);           // 16-byte vectors per thread per tile
+    const int vl = sizeof(T) == 4 ? L - 1 : L;   // log2 vectors per contiguous chunk
+    const uint32_t wv = uint32_t(tid) & ((1u << vl) - 1u);
+    const uint32_t woff = sizeof(T) == 4 ? (wv << 1) : wv;  // amplitude offset inside the chunk
+    const uint32_t c0 = uint32_t(tid) >> vl;
+    const uint32_t q0 = swz<T>((c0 << L) | woff);
+
+    // Identity projector: raw 16-byte asynchronous copies keep the next tile in
+    // flight while the current one is processed (two shared-memory buffers).
+    // Otherwise the tile is loaded synchronously with the projector applied.
+    const bool pipe = DB && ident;
+    V* const buf0 = tile;
+    V* const buf1 = DB ? tile + (1 << M) : tile;
+    int cur = 0;
+    uint64_t bcur = 0;
+    if (pipe && uint64_t(blockIdx.x) < nunits) {
+      bcur = pdep64(blockIdx.x, omask);
+#pragma unroll
+      for (int k = 0; k < NVT; ++k) {
+        const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+        cp_async16(buf0 + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                   reinterpret_cast<const V*>(A.state) + (bcur | schunk[ch] | woff));
+      }
+    }
+    if (pipe) cp_async_commit();
+
+    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+      uint64_t tl[2] = {u, 0};
+      int cnt = 1;
+      if (pair) {
+        const uint64_t lo = u & ((1ull << hbit) - 1);
+        const uint64_t t0 = ((u >> hbit) << (hbit + 1)) | lo;
+        const uint64_t t1 = t0 ^ xt;
+        const uint64_t b0 = pdep64(t0, omask);
+        const bool t0_reads = (((b0 ^ px) & pm & omask) == (pv & omask));
+        tl[0] = t0_reads ? t0 : t1;  // the tile that reads its partner goes first
+        tl[1] = t0_reads ? t1 : t0;
+        cnt = 2;
+      }
+      for (int k2 = 0; k2 < cnt; ++k2) {
+        V* tb;
+        uint64_t base;
+        uint64_t bnext = 0;
+        if (pipe) {
+          base = bcur;
+          tb = cur ? buf1 : buf0;
+          const uint64_t un = u + gridDim.x;
+          if (un < nunits) {
+            bnext = pdep64(un, omask);
+            V* nb = cur ? buf0 : buf1;
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) {
+              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+              cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                         reinterpret_cast<const V*>(A.state) + (bnext | schunk[ch] | woff));
+            }
+          }
+          cp_async_commit();
+          cp_async_wait<1>();
+        } else {
+          tb = tile;
+          base = pdep64(tl[k2], omask);
+          const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
+          // a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv, else 0
+#pragma unroll
+          for (int k = 0; k < NVT; ++k) {
+            const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+            const uint64_t gi = base | schunk[ch] | woff;
+            const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+            if constexpr (sizeof(T) == 4) {
+              const float4* gs = reinterpret_cast<const float4*>(A.state);
+              float2 x0, x1;
+              if (zero_tile) {
+                x0 = x1 = make_float2(0.f, 0.f);
+              } else if (ident) {
+                const float4 q = __ldcg(gs + (gi >> 1));
+                x0 = make_float2(q.x, q.y);
+                x1 = make_float2(q.z, q.w);
+              } else {
+                const uint64_t s0 = gi ^ px;
+                const bool ok0 = (s0 & pm) == pv, ok1 = ((s0 ^ 1ull) & pm) == pv;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ok0 || ok1) q = __ldcg(gs + (s0 >> 1));
+                const float2 e0 = make_float2(q.x, q.y), e1 = make_float2(q.z, q.w);
+                x0 = (s0 & 1) ? e1 : e0;
+                x1 = (s0 & 1) ? e0 : e1;
+                x0 = ok0 ? make_float2(x0.x * sc, x0.y * sc) : make_float2(0.f, 0.f);
+                x1 = ok1 ? make_float2(x1.x * sc, x1.y * sc) : make_float2(0.f, 0.f);
+              }
+              *reinterpret_cast<float4*>(tile + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+            } else {
+              const double2* gs = reinterpret_cast<const double2*>(A.state);
+              double2 x;
+              if (zero_tile) {
+                x = make_double2(0, 0);
+              } else if (ident) {
+                x = __ldcg(gs + gi);
+              } else {
+                const uint64_t s0 = gi ^ px;
+                if ((s0 & pm) == pv) {
+                  x = __ldcg(gs + s0);
+                  x.x *= sc;
+                  x.y *= sc;
+                } else {
+                  x = make_double2(0, 0);
+                }
+              }
+              tile[p] = x;
+            }
+          }
+        }
+        __syncthreads();
+
+        // ---- gate stages
+        if (any_gate) {
+          for (uint32_t si = 0; si < sp.ns; ++si) {
+            const DStage st = A.stages[sp.s0 + si];
+            uint32_t off[16];
+            reg_offsets(st.R, off);
+            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+              const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
+              V a[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
+              for (int g = st.g0; g < st.g0 + st.ng; ++g) {
+                const uint32_t w = sgk[g];
+                if (w & 0x100u) apply_gate(a, w & 0xFFu, smat + (w >> 16));
+              }
+#pragma unroll
+              for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
+            }
+            __syncthreads();
+          }
+        }
+
+        // ---- measurement-group table
+        if (needed) {
+          Acc acc[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
+          uint32_t off[16];
+          reg_offsets(sp.red_R, off);
+          for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+            const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const V x = tb[b ^ off[j]];
+              acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
+            }
+          }
+          const Acc r = warp_transpose_reduce16(acc, lane);
+          if ((lane & 1) == 0) wsum[warp][transpose_slot(lane)] = double(r);
+          __syncthreads();
+          if (tid < 16) {
+            double s2 = 0;
+            for (int w = 0; w < PASS_THREADS / 32; ++w) s2 += wsum[w][tid];
+            tile16[tid] = s2;
+          }
+          __syncthreads();
+          if (tid < (1 << sp.kin)) {
+            uint32_t ob = 0;
+            for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
+            double s2 = 0;
+            for (int j = 0; j < 16; ++j)
+              if ((uint32_t(j) & kmask) == uint32_t(tid)) s2 += tile16[j];
+            ctab[tid | (ob << sp.kin)] += s2;
+          }
+        }
+
+        // ---- store
+        if (do_store) {
+#pragma unroll
+          for (int k = 0; k < NVT; ++k) {
+            const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+            const uint64_t gi = base | schunk[ch] | woff;
+            const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+            if constexpr (sizeof(T) == 4)
+              __stcg(reinterpret_cast<float4*>(A.state) + (gi >> 1), *reinterpret_cast<const float4*>(tb + p));
+            else
+              __stcg(reinterpret_cast<double2*>(A.state) + gi, tb[p]);
+          }
+        }
+        __syncthreads();
+        if (pipe) {
+          bcur = bnext;
+          cur ^= 1;
+        }
+      }
+    }
+    if (pipe) cp_async_wait<0>();
+  }
+
+  if (!need_ticket) return;
+  if (needed && tid < 16) A.partials[blockIdx.x * 16 + tid] = ctab[tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&A.ctrl->ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (needed && tid < 16) {
+    double s = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(A.partials + b * 16 + tid);
+    ctab[tid] = s;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
+}
+
 // ============================================================ host launchers
 
-template <typename T>
-static cudaError_t launch_pass_t(const PassArgs& a, int pi, int grid, int m, cudaStream_t s) {
+template <typename T, int M>
+static size_t pass_smem() {
   using V = typename CxT<T>::V;
-  const size_t smem = (size_t(1) << m) * sizeof(V);
-  k_pass<T><<<grid, PASS_THREADS, smem, s>>>(a, pi);
+  const size_t one = (size_t(1) << M) * sizeof(V);
+  return 2 * one <= size_t(128) * 1024 ? 2 * one : one;
+}
+
+template <typename T, int M>
+static cudaError_t launch_pass_tm(const PassArgs& a, int pi, int grid, cudaStream_t s) {
+  const size_t smem = pass_smem<T, M>();
+  k_pass<T, M><<<grid, PASS_THREADS, smem, s>>>(a, pi);
   return cudaGetLastError();
 }
 
+template <typename T, int M>
+static cudaError_t pass_attr_tm(int* per_sm) {
+  const size_t smem = pass_smem<T, M>();
+  cudaError_t e = cudaFuncSetAttribute(k_pass<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pass<T, M>, PASS_THREADS, smem);
+  return e;
+}
+
 cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s) {
-  return dtype == SV_C64 ? launch_pass_t<float>(a, pi, grid, m, s) : launch_pass_t<double>(a, pi, grid, m, s);
+  if (dtype == SV_C64) {
+    switch (m) {
+      case 10: return launch_pass_tm<float, 10>(a, pi, grid, s);
+      case 11: return launch_pass_tm<float, 11>(a, pi, grid, s);
+      case 12: return launch_pass_tm<float, 12>(a, pi, grid, s);
+      case 13: return launch_pass_tm<float, 13>(a, pi, grid, s);
+      case 14: return launch_pass_tm<float, 14>(a, pi, grid, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (m) {
+    case 10: return launch_pass_tm<double, 10>(a, pi, grid, s);
+    case 11: return launch_pass_tm<double, 11>(a, pi, grid, s);
+    case 12: return launch_pass_tm<double, 12>(a, pi, grid, s);
+    case 13: return launch_pass_tm<double, 13>(a, pi, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s) {
@@ -738,31 +817,31 @@ cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, c
 
 cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm) {
   static int cache[2][MAX_TILE_BITS + 1] = {};
-  static bool attr_set[2] = {false, false};
   const int d = dtype == SV_C64 ? 0 : 1;
+  if (m < 10 || m > MAX_TILE_BITS || (d == 1 && m > 13)) return cudaErrorInvalidValue;
   int& c = cache[d][m];
   if (c) {
     *blocks_per_sm = c;
     return cudaSuccess;
   }
-  cudaError_t e = cudaSuccess;
-  if (dtype == SV_C64) {
-    if (!attr_set[d])
-      e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int((size_t(1) << MAX_TILE_BITS) * sizeof(float2)));
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass<float>, PASS_THREADS,
-                                                        (size_t(1) << m) * sizeof(float2));
+  cudaError_t e;
+  if (d == 0) {
+    switch (m) {
+      case 10: e = pass_attr_tm<float, 10>(&c); break;
+      case 11: e = pass_attr_tm<float, 11>(&c); break;
+      case 12: e = pass_attr_tm<float, 12>(&c); break;
+      case 13: e = pass_attr_tm<float, 13>(&c); break;
+      default: e = pass_attr_tm<float, 14>(&c); break;
+    }
   } else {
-    if (!attr_set[d])
-      e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int((size_t(1) << (MAX_TILE_BITS - 1)) * sizeof(double2)));
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_pass<double>, PASS_THREADS,
-                                                        (size_t(1) << m) * sizeof(double2));
+    switch (m) {
+      case 10: e = pass_attr_tm<double, 10>(&c); break;
+      case 11: e = pass_attr_tm<double, 11>(&c); break;
+      case 12: e = pass_attr_tm<double, 12>(&c); break;
+      default: e = pass_attr_tm<double, 13>(&c); break;
+    }
   }
-  if (e == cudaSuccess) attr_set[d] = true;
-  if (c < 1) c = 1;
+  if (e != cudaSuccess || c < 1) c = 1;
   *blocks_per_sm = c;
   return e;
 }

@@ -202,21 +202,26 @@ struct Segment {
 int popc(uint64_t v) { return __builtin_popcountll(v); }
 
 // Orders the tile-local bits that receive thread-group index bits so that the
-// first lanes of a warp hit distinct shared-memory banks under the XOR
-// swizzle (bank bit of local bit p is p mod B).
-void order_thread_bits(const std::vector<int>& free_bits, int B, uint8_t* out) {
+// first lanes of a warp hit distinct shared-memory banks under the swizzle.
+// complex128 (A = 0): a quarter-warp (8 lanes x 16 B) is conflict-free when
+// its three lane bits fall in distinct classes p mod 3.  complex64 (A = 1): a
+// half-warp (16 lanes x 8 B) needs local bit 0 plus one bit of each class
+// (p - 1) mod 3.
+void order_thread_bits(const std::vector<int>& free_bits, int A, uint8_t* out) {
   std::vector<int> rest(free_bits);
   std::sort(rest.begin(), rest.end());
   std::vector<int> order;
-  for (int r = 0; r < B; ++r) {
-    for (size_t k = 0; k < rest.size(); ++k) {
-      if (rest[k] % B == r) {
+  auto take = [&](auto pred) {
+    for (size_t k = 0; k < rest.size(); ++k)
+      if (pred(rest[k])) {
         order.push_back(rest[k]);
         rest.erase(rest.begin() + long(k));
-        break;
+        return;
       }
-    }
-  }
+  };
+  if (A == 1) take([](int p) { return p == 0; });
+  for (int c = 0; c < 3; ++c)
+    take([&](int p) { return A == 1 ? (p >= 1 && (p - 1) % 3 == c) : (p % 3 == c); });
   for (int b : rest) order.push_back(b);
   for (size_t k = 0; k < order.size() && k < MAX_TILE_BITS; ++k) out[k] = uint8_t(order[k]);
 }
@@ -224,7 +229,7 @@ void order_thread_bits(const std::vector<int>& free_bits, int B, uint8_t* out) {
 struct Builder {
   Plan& P;
   const std::vector<Item>& items;
-  int B;  // swizzle bank bits (4: complex64, 3: complex128)
+  int B;  // log2 amplitudes per 16-byte granule (1: complex64, 0: complex128)
   int max_pass_gates;
 
   Builder(Plan& p, const std::vector<Item>& it, int b, int mpg) : P(p), items(it), B(b), max_pass_gates(mpg) {}
@@ -308,13 +313,15 @@ struct Builder {
       int rpos[MAX_TILE_BITS];
       for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
       for (int r = 0; r < REG_BITS; ++r) {
-        st.reg[r] = uint8_t(reg[r]);
+        st.R[r] = uint16_t(tile_swizzle(1u << reg[r], B));
         rpos[reg[r]] = r;
       }
       std::vector<int> freeb;
       for (int j = 0; j < m; ++j)
         if (rpos[j] < 0) freeb.push_back(j);
-      order_thread_bits(freeb, B, st.thr);
+      uint8_t thr[MAX_TILE_BITS] = {};
+      order_thread_bits(freeb, B, thr);
+      for (int k = 0; k < m - REG_BITS; ++k) st.E[k] = uint16_t(tile_swizzle(1u << thr[k], B));
       for (int idx : sg) {
         const Item& it = items[idx];
         DGate g{};
@@ -322,6 +329,7 @@ struct Builder {
         g.flag = it.flag;
         g.p0 = uint8_t(rpos[loc[it.q[0]]]);
         g.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;
+        g.key = uint8_t(it.op == OP_D16 ? OP_D16 * 16 : it.op * 16 + g.p0 * 4 + g.p1);
         g.mat = mat;
         const uint32_t out = P.n_mat + mat;
         if (it.gate >= 0) {
@@ -397,11 +405,13 @@ struct Builder {
           reg.push_back(j);
           used |= 1u << j;
         }
-      for (int r = 0; r < REG_BITS; ++r) ps.red_reg[r] = uint8_t(reg[r]);
+      for (int r = 0; r < REG_BITS; ++r) ps.red_R[r] = uint16_t(tile_swizzle(1u << reg[r], B));
       std::vector<int> freeb;
       for (int j = 0; j < m; ++j)
         if (!((used >> j) & 1)) freeb.push_back(j);
-      order_thread_bits(freeb, B, ps.red_thr);
+      uint8_t thr[MAX_TILE_BITS] = {};
+      order_thread_bits(freeb, B, thr);
+      for (int k = 0; k < m - REG_BITS; ++k) ps.red_E[k] = uint16_t(tile_swizzle(1u << thr[k], B));
 
       // which flags are decided inside this phase
       std::vector<int> decided_here;
@@ -504,7 +514,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     return SV_ERR_ARG;
   }
   P.n = n;
-  P.n_int = std::max(n, 4);
+  P.n_int = std::max(n, 10);  // small states are padded with qubits that stay |0>
   P.dtype = dtype;
   int tb = tune.tile_bits > 0 ? tune.tile_bits : 12;
   // shared-memory tile: 2^14 x 8 B (complex64) or 2^13 x 16 B (complex128) at most
@@ -513,6 +523,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   int lb = tune.low_bits > 0 ? tune.low_bits : (dtype == SV_C64 ? 5 : 4);
   P.L = std::min(std::max(lb, 2), P.m);
   P.L = std::max(P.L, P.m - 9);  // at most 2^9 gathered chunks per tile
+  P.L = std::min(P.L, dtype == SV_C64 ? 9 : 8);  // a warp-group of 256 threads covers whole chunks
 
   Unroller U;
   U.ops = ops;
@@ -577,7 +588,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     }
   }
 
-  Builder b(P, U.items, dtype == SV_C64 ? 4 : 3, tune.max_pass_gates);
+  Builder b(P, U.items, dtype == SV_C64 ? 1 : 0, tune.max_pass_gates);
   for (const Segment& s : segs) {
     if (s.gates.empty() && !s.has_group) continue;
     b.emit_segment(s);

@@ -147,7 +147,10 @@ sv_status upload_program(sv_state* h, sv_program* p) {
 
 int pass_grid(sv_state* h, int m) {
   int per_sm = 1;
-  svk::pass_occupancy(h->dtype, m, &per_sm);
+  if (svk::pass_occupancy(h->dtype, m, &per_sm) != cudaSuccess) {
+    cudaGetLastError();  // clear the non-sticky error of the failed query
+    return -1;
+  }
   const uint64_t tiles = 1ull << (h->n_int - m);
   const uint64_t want = uint64_t(h->sms) * uint64_t(per_sm);
   return int(std::min<uint64_t>(tiles, want));
@@ -180,6 +183,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
   SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
   if (!P.passes.empty()) {
     const int grid = pass_grid(h, P.m);
+    if (grid < 1) return fail(SV_ERR_CUDA, "pass kernel configuration failed for tile bits " + std::to_string(P.m));
     SV_CUDA(h->partials.reserve(size_t(grid) * 16));
     svk::PassArgs a{};
     a.state = h->state;
@@ -295,14 +299,14 @@ sv_status sv_create(int n, sv_dtype dtype, void* dev_buf, size_t bytes, sv_state
   if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
   std::unique_ptr<sv_state> h(new sv_state());
   h->n = n;
-  h->n_int = std::max(n, 4);
+  h->n_int = std::max(n, 10);  // small states are padded with qubits that stay |0>
   h->dtype = dtype;
   h->amp_bytes = dtype == SV_C64 ? 8 : 16;
   const size_t need = (size_t(1) << h->n_int) * h->amp_bytes;
   SV_CUDA(cudaGetDevice(&h->device));
   SV_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
   if (dev_buf) {
-    if (bytes < need) return fail(SV_ERR_ARG, "dev_buf smaller than 2^max(n,4) amplitudes");
+    if (bytes < need) return fail(SV_ERR_ARG, "dev_buf smaller than 2^max(n,10) amplitudes");
     if (reinterpret_cast<uintptr_t>(dev_buf) % 16) return fail(SV_ERR_ARG, "dev_buf must be 16-byte aligned");
     h->state = dev_buf;
   } else {

@@ -57,24 +57,42 @@ constexpr int PASS_THREADS = 256;
 constexpr int MAX_TILE_BITS = 14;
 constexpr int MAX_GROUP_Q = 4;
 constexpr int MAX_PASS_GATES = 128;
-constexpr int MAX_PASS_STAGES = 48;
 constexpr int MAX_PASS_MAT = 1024;  // complex entries staged in shared memory per pass
 constexpr int MAX_TRACE = 4096;     // draw records kept per trajectory
 
 // gate as the kernel sees it: positions are register-bit indices (0..3) of its stage
 struct DGate {
-  uint8_t op, p0, p1, pad;
+  uint8_t key;    // op * 16 + p0 * 4 + p1: one switch selects op and positions
+  uint8_t op, p0, p1;
   int32_t flag;   // -1: unconditional; else index into the flag array
   uint32_t mat;   // offset (complex entries) from the pass's matrix base
   uint32_t pad2;
 };
 
+// Register stage.  The tile is stored XOR-swizzled in shared memory (see
+// tile_swizzle); because the swizzle is linear over GF(2), the address of a
+// tile-local index is the XOR of the addresses of its set bits.  R[r] is the
+// address of register bit r, E[k] that of group-index bit k.
 struct DStage {
-  uint16_t g0, ng;                   // gate range (pass-relative)
-  uint8_t reg[REG_BITS];             // tile-local bit of register bit r
-  uint8_t thr[MAX_TILE_BITS];        // tile-local bits receiving the group index bits (m-4 used)
-  uint8_t pad[6];
+  uint16_t g0, ng;                       // gate range (pass-relative)
+  uint16_t R[REG_BITS];
+  uint16_t E[MAX_TILE_BITS - REG_BITS];
 };
+
+// Shared-memory layout of a tile, in 16-byte granules (one complex128 or two
+// complex64 amplitudes): granule g lives at g ^ fold(g >> 3), fold = XOR of
+// the 3-bit groups, so the 8 granules of every 128-byte row are permuted by
+// the higher index bits.  A = log2(amplitudes per granule) (1 for complex64,
+// 0 for complex128); amplitude pairs of complex64 stay adjacent, so a
+// 16-byte copy moves a granule verbatim.  The map is linear over GF(2).
+static inline uint32_t tile_swizzle(uint32_t x, int A) {
+  uint32_t y = x >> (A + 3), f = 0;
+  for (int k = 0; k < 5; ++k) {
+    f ^= y & 7u;
+    y >>= 3;
+  }
+  return x ^ (f << A);
+}
 
 struct DScalar {
   uint8_t kind;     // ScalarKind
@@ -102,9 +120,8 @@ struct DPass {
   uint8_t pad[2];
   uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
   uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
-  uint8_t red_reg[REG_BITS];      // reduction stage: register bit r <- tile-local bit
-  uint8_t red_thr[MAX_TILE_BITS]; // reduction stage: group-index bits
-  uint32_t pad2[2];
+  uint16_t red_R[REG_BITS];       // reduction stage: register-bit addresses
+  uint16_t red_E[MAX_TILE_BITS - REG_BITS];  // reduction stage: group-index-bit addresses
 };
 
 struct DJob {

@@ -155,7 +155,7 @@ class State:
         self.dt = SV_C64 if dtype == "c64" else SV_C128
         self.amp = np.complex64 if dtype == "c64" else np.complex128
         torch = _torch()
-        n_int = max(self.n, 4)
+        n_int = max(self.n, 10)  # the library pads small states to 10 qubits
         self._buf = buffer
         if self._buf is None and torch is not None and torch.cuda.is_available() and 1 <= self.n <= 34:
             real = torch.float32 if dtype == "c64" else torch.float64
