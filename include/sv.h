@@ -226,6 +226,41 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
 sv_status sv_expval_static(const void* dev_state, int n, sv_dtype dtype, const sv_pauli* terms, size_t n_terms,
                            double* dev_out, void* cuda_stream);
 
+/*
+ * Batched execution: many trajectories, of uneven qubit counts, in one
+ * persistent kernel launch (replayed from a CUDA graph).  Each CTA of the
+ * launch takes the next trajectory from a device work queue (longest first),
+ * runs its whole program on a private state slot -- feed-forward decided on
+ * the device -- and stores the classical register; trajectory t uses Philox
+ * stream stream_ids[t] and shot shots[t], so its record equals that of
+ * sv_run with the same (seed, stream_id, shot).  States are padded to at
+ * least 12 qubits.
+ *
+ * sv_batch_create        handle for one dtype; work is enqueued on cuda_stream.
+ * sv_batch_add_program   lowers an op list for n qubits with its parameters
+ *                        (copied; n_params doubles) and optional dense pool;
+ *                        *prog_id receives its index.
+ * sv_batch_set_items     the batch: n_items trajectories (program, stream id,
+ *                        shot); allocates the device work space (one state
+ *                        slot of 2^max(n) amplitudes per resident CTA).
+ * sv_batch_launch        asynchronous run of the current items.
+ * sv_batch_results       waits and copies the n_items classical registers.
+ * sv_batch_run           set_items + launch + results.
+ * Errors: SV_ERR_ARG for bad ids or sizes, SV_ERR_OOM when the work space
+ * does not fit, SV_ERR_NUMERIC if a trajectory met a zero-norm state.
+ */
+typedef struct sv_batch sv_batch;
+sv_status sv_batch_create(sv_dtype dtype, void* cuda_stream, sv_batch** out);
+sv_status sv_batch_add_program(sv_batch* b, int n, const sv_op* ops, size_t n_ops, const double* params,
+                               size_t n_params, const double* dense_pool, size_t n_complex, uint32_t* prog_id);
+sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                             size_t n_items);
+sv_status sv_batch_launch(sv_batch* b, uint64_t seed);
+sv_status sv_batch_results(sv_batch* b, uint64_t* creg_out);
+sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                       size_t n_items, uint64_t seed, uint64_t* creg_out);
+sv_status sv_batch_destroy(sv_batch* b);
+
 /* Copy amplitudes [first, first+count) to / from host memory (amplitude-size elements). */
 sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count);
 sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count);

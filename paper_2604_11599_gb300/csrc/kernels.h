@@ -41,6 +41,44 @@ cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, c
 cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s);
 cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm);
 
+// persistent batched execution: one CTA runs one trajectory at a time
+struct BatchProg {
+  const svp::DPass* passes;
+  const svp::DGate* gates;
+  const svp::DStage* stages;
+  const svp::DScalar* scalars;
+  const void* mats;
+  const svp::DScalar* init;
+  uint32_t npasses, ninit;
+};
+
+struct BatchItem {
+  uint32_t prog;    // index into the program table
+  uint32_t n_int;   // simulated qubits (>= 12)
+  uint64_t stream;  // Philox stream of the trajectory
+  uint64_t shot;
+  uint32_t out;     // output slot
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  const BatchItem* items;
+  uint32_t n_items;
+  const BatchProg* progs;
+  void* state_slots;  // [grid][slot_amps] amplitudes
+  uint64_t slot_amps;
+  uint8_t* flag_slots;  // [grid][slot_flags]
+  uint32_t slot_flags;
+  svp::Ctrl* ctrls;     // [grid]
+  unsigned* queue;      // next item (reset to 0 before the launch)
+  uint64_t seed;
+  uint64_t* creg_out;   // [n_items], indexed by BatchItem::out
+  int* status_out;      // first nonzero trajectory status
+};
+constexpr int BATCH_TILE_BITS = 12;
+cudaError_t launch_batch(int dtype, const BatchArgs& a, int grid, cudaStream_t s);
+cudaError_t batch_occupancy(int dtype, int* blocks_per_sm);
+
 // terminal sampling: block sums -> scan -> per-shot search
 struct SampleArgs {
   const void* state;

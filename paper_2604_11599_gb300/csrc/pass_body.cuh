@@ -1,0 +1,711 @@
+// pass_body.cuh -- device code of one state sweep, shared by the grid pass
+// kernel (kern_pass.cu) and the persistent batched kernel (kern_batch.cu).
+//
+// One pass sweeps the state once.  A tile is the 2^M amplitudes that share
+// the values of the n-M qubits outside the pass's tile set.  Tiles are read
+// with 16-byte coalesced copies (runs of 2^L contiguous amplitudes): with no
+// pending projector they stream in by cp.async, the next tile in flight while
+// the current one is processed; otherwise they are loaded with the pending
+// measurement projector applied on the way in (the collapse and 1/sqrt(p)
+// renormalisation of the previous measurement group, fused into this load).
+// In swizzled shared memory the tile is processed in stages: each thread
+// pulls 16 amplitudes (four register qubits) into registers, applies the
+// stage's gates there and writes them back.  If a measurement group follows,
+// the |amp|^2 table of its qubits is accumulated (FP32 within a warp for
+// complex64, FP64 across warps and CTAs) and one thread draws the outcomes
+// (Philox4x64-10 keyed on seed, stream, shot and draw index), updates the
+// classical register and evaluates the feed-forward predicates that follow
+// (Sec. III-C) -- all on the device.
+#pragma once
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace svk {
+using namespace svp;
+
+// ============================================================ gates on 16 registers
+// a[j] holds the amplitude whose register bits are j; template parameters
+// are register-bit positions, so every index below is a compile-time constant.
+
+template <int P, typename V>
+__device__ __forceinline__ void g_u(V* a, const V* m) {
+  const V m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = cmac2(m0, x, m1, y);
+    a[k] = cmac2(m2, x, m3, y);
+  }
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_r(V* a, const V* m) {
+  const auto r00 = m[0].x, r01 = m[1].x, r10 = m[2].x, r11 = m[3].x;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = mkc(fma(r00, x.x, r01 * y.x), fma(r00, x.y, r01 * y.y));
+    a[k] = mkc(fma(r10, x.x, r11 * y.x), fma(r10, x.y, r11 * y.y));
+  }
+}
+
+// RX: [c, -i s; -i s, c]
+template <int P, typename V>
+__device__ __forceinline__ void g_rx(V* a, const V* m) {
+  const auto c = m[0].x, s = m[1].x;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V x = a[j], y = a[k];
+    a[j] = mkc(fma(c, x.x, s * y.y), fma(c, x.y, -s * y.x));
+    a[k] = mkc(fma(s, x.y, c * y.x), fma(-s, x.x, c * y.y));
+  }
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_d(V* a, const V* m) {
+  const V d0 = m[0], d1 = m[1];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = cmul((j & (1 << P)) ? d1 : d0, a[j]);
+}
+
+template <int P, typename V>
+__device__ __forceinline__ void g_x(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cu(V* a, const V* m) {
+  const V m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << C)) || (j & (1 << T))) continue;
+    const int k = j | (1 << T);
+    const V x = a[j], y = a[k];
+    a[j] = cmac2(m0, x, m1, y);
+    a[k] = cmac2(m2, x, m3, y);
+  }
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cx(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << C)) || (j & (1 << T))) continue;
+    const int k = j | (1 << T);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+template <int A, int B, typename V>
+__device__ __forceinline__ void g_cz(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if ((j & (1 << A)) && (j & (1 << B))) a[j] = mkc(-a[j].x, -a[j].y);
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ void g_cd(V* a, const V* m) {
+  const V d0 = m[0], d1 = m[1];
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j & (1 << C)) a[j] = cmul((j & (1 << T)) ? d1 : d0, a[j]);
+}
+
+template <int A, int B, typename V>
+__device__ __forceinline__ void g_swap(V* a, const V*) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (!(j & (1 << A)) || (j & (1 << B))) continue;
+    const int k = (j ^ (1 << A)) | (1 << B);
+    const V t = a[j];
+    a[j] = a[k];
+    a[k] = t;
+  }
+}
+
+// dense 4x4; matrix index bit 0 <-> register bit P0, bit 1 <-> P1
+template <int P0, int P1, typename V>
+__device__ __forceinline__ void g_u4(V* a, const V* m) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if ((j & (1 << P0)) || (j & (1 << P1))) continue;
+    const int i0 = j, i1 = j | (1 << P0), i2 = j | (1 << P1), i3 = j | (1 << P0) | (1 << P1);
+    const V v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
+    a[i0] = cadd(cmac2(m[0], v0, m[1], v1), cmac2(m[2], v2, m[3], v3));
+    a[i1] = cadd(cmac2(m[4], v0, m[5], v1), cmac2(m[6], v2, m[7], v3));
+    a[i2] = cadd(cmac2(m[8], v0, m[9], v1), cmac2(m[10], v2, m[11], v3));
+    a[i3] = cadd(cmac2(m[12], v0, m[13], v1), cmac2(m[14], v2, m[15], v3));
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void g_d16(V* a, const V* m) {
+  V w[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    V acc = mkc(decltype(a[0].x)(0), decltype(a[0].x)(0));
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) acc = cadd(acc, cmac2(m[r * 16 + c], a[c], m[r * 16 + c + 1], a[c + 1]));
+    w[r] = acc;
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) a[r] = w[r];
+}
+
+#define SVK_K1(OP, FN)                          \
+  case OP * 16 + 0: FN<0>(a, mt); break;        \
+  case OP * 16 + 4: FN<1>(a, mt); break;        \
+  case OP * 16 + 8: FN<2>(a, mt); break;        \
+  case OP * 16 + 12: FN<3>(a, mt); break;
+
+#define SVK_K2(OP, FN)                          \
+  case OP * 16 + 1: FN<0, 1>(a, mt); break;     \
+  case OP * 16 + 2: FN<0, 2>(a, mt); break;     \
+  case OP * 16 + 3: FN<0, 3>(a, mt); break;     \
+  case OP * 16 + 4: FN<1, 0>(a, mt); break;     \
+  case OP * 16 + 6: FN<1, 2>(a, mt); break;     \
+  case OP * 16 + 7: FN<1, 3>(a, mt); break;     \
+  case OP * 16 + 8: FN<2, 0>(a, mt); break;     \
+  case OP * 16 + 9: FN<2, 1>(a, mt); break;     \
+  case OP * 16 + 11: FN<2, 3>(a, mt); break;    \
+  case OP * 16 + 12: FN<3, 0>(a, mt); break;    \
+  case OP * 16 + 13: FN<3, 1>(a, mt); break;    \
+  case OP * 16 + 14: FN<3, 2>(a, mt); break;
+
+// one switch on key = op * 16 + p0 * 4 + p1 selects the gate and its register positions
+template <typename V>
+__device__ __forceinline__ void apply_gate(V* a, uint32_t key, const V* mt) {
+  switch (key) {
+    SVK_K1(OP_U, g_u)
+    SVK_K1(OP_R, g_r)
+    SVK_K1(OP_RX, g_rx)
+    SVK_K1(OP_D, g_d)
+    SVK_K1(OP_X, g_x)
+    SVK_K2(OP_CU, g_cu)
+    SVK_K2(OP_CX, g_cx)
+    SVK_K2(OP_CZ, g_cz)
+    SVK_K2(OP_CD, g_cd)
+    SVK_K2(OP_SWAP, g_swap)
+    SVK_K2(OP_U4, g_u4)
+    case OP_D16 * 16: g_d16(a, mt); break;
+    default: break;
+  }
+}
+
+// ============================================================ gate matrices (FP64)
+// OpenQASM 3 standard-gate definitions; m = [m00 m01; m10 m11] of the target.
+static __device__ void std_gate_2x2(int gate, const double* t, double2* m) {
+  const double h = 0.70710678118654752440;
+  double c, s, sp, cp, sl, cl;
+  for (int k = 0; k < 4; ++k) m[k] = make_double2(0, 0);
+  switch (gate) {
+    case SV_H: case SV_CH: m[0] = m[1] = m[2] = make_double2(h, 0); m[3] = make_double2(-h, 0); break;
+    case SV_X: case SV_CX: m[1] = m[2] = make_double2(1, 0); break;
+    case SV_Y: case SV_CY: m[1] = make_double2(0, -1); m[2] = make_double2(0, 1); break;
+    case SV_Z: case SV_CZ: m[0] = make_double2(1, 0); m[3] = make_double2(-1, 0); break;
+    case SV_S: m[0] = make_double2(1, 0); m[3] = make_double2(0, 1); break;
+    case SV_SDG: m[0] = make_double2(1, 0); m[3] = make_double2(0, -1); break;
+    case SV_T: m[0] = make_double2(1, 0); m[3] = make_double2(h, h); break;
+    case SV_TDG: m[0] = make_double2(1, 0); m[3] = make_double2(h, -h); break;
+    case SV_SX:
+      m[0] = m[3] = make_double2(0.5, 0.5);
+      m[1] = m[2] = make_double2(0.5, -0.5);
+      break;
+    case SV_RX: case SV_CRX:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = m[3] = make_double2(c, 0);
+      m[1] = m[2] = make_double2(0, -s);
+      break;
+    case SV_RY: case SV_CRY:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = m[3] = make_double2(c, 0);
+      m[1] = make_double2(-s, 0);
+      m[2] = make_double2(s, 0);
+      break;
+    case SV_RZ: case SV_CRZ:
+      sincos(0.5 * t[0], &s, &c);
+      m[0] = make_double2(c, -s);
+      m[3] = make_double2(c, s);
+      break;
+    case SV_P: case SV_CP:
+      sincos(t[0], &s, &c);
+      m[0] = make_double2(1, 0);
+      m[3] = make_double2(c, s);
+      break;
+    case SV_U: case SV_CU:
+      sincos(0.5 * t[0], &s, &c);
+      sincos(t[1], &sp, &cp);
+      sincos(t[2], &sl, &cl);
+      m[0] = make_double2(c, 0);
+      m[1] = make_double2(-cl * s, -sl * s);
+      m[2] = make_double2(cp * s, sp * s);
+      m[3] = make_double2((cp * cl - sp * sl) * c, (sp * cl + cp * sl) * c);
+      break;
+    default: m[0] = m[3] = make_double2(1, 0); break;
+  }
+}
+
+
+static __device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
+  uint64_t out = 0;
+  for (uint64_t bb = 1; mask; bb <<= 1) {
+    const uint64_t low = mask & (~mask + 1);
+    if (v & bb) out |= low;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+static __device__ __forceinline__ uint64_t pext64(uint64_t v, uint64_t mask) {
+  uint64_t out = 0, bb = 1;
+  for (; mask; bb <<= 1) {
+    const uint64_t low = mask & (~mask + 1);
+    if (v & low) out |= bb;
+    mask &= mask - 1;
+  }
+  return out;
+}
+
+// 16 per-lane values -> lane holds the warp sum of slot(lane); 16 shuffles.
+template <typename A>
+__device__ __forceinline__ A warp_transpose_reduce16(A (&v)[16], int lane) {
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int o = 16 >> st, h = 8 >> st;
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const A send = up ? v[i] : v[i + h];
+      const A keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+static __device__ __forceinline__ int transpose_slot(int lane) {
+  return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
+}
+
+// ---- scalar phase (one thread of the last CTA): draws, classical register, predicates
+static __device__ __noinline__ void scalar_phase(const PassArgs& A, const DPass& sp, const double* ctab, bool do_store,
+                                          uint64_t pm, uint64_t pv, uint64_t px, double ps) {
+  Ctrl* W = A.ctrl;
+  uint64_t creg = W->creg, mc = W->m;
+  uint64_t npm = do_store ? 0 : pm, npv = do_store ? 0 : pv, npx = do_store ? 0 : px;
+  double nps = do_store ? 1.0 : ps;
+  double tab[16];
+  for (int e = 0; e < 16; ++e) tab[e] = ctab[e];
+  const int tsize = 1 << sp.gk;
+  bool drew = false;
+  for (uint32_t c = 0; c < sp.nc; ++c) {
+    const DScalar s = A.scalars[sp.c0 + c];
+    if (s.kind == S_COND) {
+      const bool par = s.flag < 0 || A.flags[s.flag];
+      const bool pred = (creg & s.mask) == s.value;
+      A.flags[s.f_then] = (par && pred) ? 1 : 0;
+      if (s.f_else >= 0) A.flags[s.f_else] = (par && !pred) ? 1 : 0;
+      continue;
+    }
+    if (!(s.flag < 0 || A.flags[s.flag])) continue;
+    double p0 = 0, p1 = 0;
+    for (int e = 0; e < tsize; ++e) {
+      if ((e >> s.tbit) & 1) p1 += tab[e];
+      else p0 += tab[e];
+    }
+    const double u = draw_uniform(W->seed, W->stream, W->shot, mc);
+    int o = 0;
+    if (!(p0 + p1 > 0)) W->status = SV_ERR_NUMERIC;
+    else o = (u >= p0 / (p0 + p1)) ? 1 : 0;
+    if (W->n_trace < MAX_TRACE) {
+      DTrace& tr = A.trace[W->n_trace];
+      tr.qubit = int(s.qubit);
+      tr.is_reset = s.kind == S_RESET;
+      tr.outcome = o;
+      tr.pad = 0;
+      tr.p0 = p0;
+      tr.p1 = p1;
+      tr.u = u;
+      W->n_trace = W->n_trace + 1;
+    }
+    ++mc;
+    const int bt = 1 << s.tbit;
+    for (int e = 0; e < tsize; ++e)
+      if (((e >> s.tbit) & 1) != o) tab[e] = 0;
+    if (s.kind == S_RESET && o)
+      for (int e = 0; e < tsize; ++e)
+        if (e & bt) {
+          tab[e ^ bt] = tab[e];
+          tab[e] = 0;
+        }
+    if (s.kind == S_MEASURE) creg = (creg & ~(1ull << s.cbit)) | (uint64_t(o) << s.cbit);
+    const uint64_t qb = 1ull << s.qubit;
+    const uint64_t xq = (npx >> s.qubit) & 1ull;
+    npm |= qb;
+    npv = (npv & ~qb) | ((uint64_t(o) ^ xq) << s.qubit);
+    if (s.kind == S_RESET && o) npx ^= qb;
+    drew = true;
+  }
+  if (drew) {
+    double mass = 0;
+    for (int e = 0; e < tsize; ++e) mass += tab[e];
+    if (mass > 0) nps *= 1.0 / sqrt(mass);
+    else W->status = SV_ERR_NUMERIC;
+  }
+  W->creg = creg;
+  W->m = mc;
+  W->pm = npm;
+  W->pv = npv;
+  W->px = npx;
+  W->ps = nps;
+  W->ticket = 0;
+  __threadfence();
+}
+
+// register offsets of a stage: off[j] = XOR of R[r] over the set bits r of j
+static __device__ __forceinline__ void reg_offsets(const uint16_t* R, uint32_t (&off)[16]) {
+  off[0] = 0;
+#pragma unroll
+  for (int j = 1; j < 16; ++j) off[j] = off[j & (j - 1)] ^ R[__ffs(j) - 1];
+}
+
+template <int GB>
+__device__ __forceinline__ uint32_t group_base(const uint16_t* E, uint32_t g) {
+  uint32_t b = 0;
+#pragma unroll
+  for (int k = 0; k < GB; ++k)
+    if ((g >> k) & 1u) b ^= E[k];
+  return b;
+}
+
+// Shared state of one pass (static shared memory of the kernel that runs it).
+template <typename T>
+struct PassShared {
+  DPass sp;
+  uint32_t sgk[MAX_PASS_GATES];  // key | active << 8 | matrix offset << 16
+  __align__(16) typename CxT<T>::V smat[MAX_PASS_MAT];
+  uint64_t schunk[512];          // global offset of each gathered chunk of the tile
+  double ctab[16];               // measurement-group table of this CTA
+  double wsum[PASS_THREADS / 32][16];
+  double tile16[16];
+  int s_last;
+};
+
+// One pass over the state.  GRID mode (CTA = false): the tiles are shared by
+// all CTAs of the launch and the last CTA to finish reduces the group table
+// and runs the scalar phase.  CTA mode (CTA = true): the calling CTA owns the
+// whole trajectory, walks every tile itself and runs the scalar phase after a
+// block barrier; used by the persistent batched kernel.
+template <typename T, int M, bool CTA>
+__device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T>& sh, void* smem_tiles) {
+  using V = typename CxT<T>::V;
+  using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
+  constexpr int GB = M - REG_BITS;  // group-index bits of a stage
+  constexpr int NGRP = 1 << GB;     // 16-amplitude groups per tile
+  constexpr bool DB = (size_t(2) << M) * sizeof(V) <= size_t(128) * 1024;  // double-buffered tiles fit
+  V* tile = reinterpret_cast<V*>(smem_tiles);
+  DPass& sp = sh.sp;
+  uint32_t* sgk = sh.sgk;
+  V* smat = sh.smat;
+  uint64_t* schunk = sh.schunk;
+  double* ctab = sh.ctab;
+  double* tile16 = sh.tile16;
+  const uint64_t ustart = CTA ? 0ull : uint64_t(blockIdx.x);
+  const uint64_t ustep = CTA ? 1ull : uint64_t(gridDim.x);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) sp = A.passes[pi];
+  if (tid < 16) ctab[tid] = 0.0;
+  __syncthreads();
+  const int L = sp.L, n = A.n;
+
+  int act_any = 0;
+  for (int g = tid; g < int(sp.ng); g += PASS_THREADS) {
+    const DGate d = A.gates[sp.g0 + g];
+    const uint32_t on = d.flag < 0 ? 1u : (A.flags[d.flag] ? 1u : 0u);
+    sgk[g] = uint32_t(d.key) | (on << 8) | (d.mat << 16);
+    act_any |= int(on);
+  }
+  const bool any_gate = __syncthreads_or(act_any) != 0;
+  int need = 0;
+  if (sp.gk) {
+    if (sp.group_always) need = 1;
+    else
+      for (int c = tid; c < int(sp.nc); c += PASS_THREADS) {
+        const DScalar sc = A.scalars[sp.c0 + c];
+        if (sc.kind != S_COND && (sc.flag < 0 || A.flags[sc.flag])) need = 1;
+      }
+  }
+  const bool needed = __syncthreads_or(need) != 0;
+
+  const Ctrl* C = A.ctrl;
+  const uint64_t pm = C->pm, pv = C->pv, px = C->px;
+  const double ps = C->ps;
+  const bool ident = (pm == 0 && px == 0 && ps == 1.0);
+  const bool do_store = any_gate || (sp.flush && !ident);
+  const bool do_work = do_store || needed;
+  const bool need_ticket = sp.nc > 0 || (do_store && !ident);
+
+  if (do_work) {
+    if (any_gate)
+      for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
+    const int hb = M - L;
+    for (int c = tid; c < (1 << hb); c += PASS_THREADS) {
+      uint64_t o = 0;
+      for (int k = 0; k < hb; ++k)
+        if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
+      schunk[c] = o;
+    }
+    __syncthreads();
+
+    uint64_t tmask = 0;
+    for (int j = 0; j < M; ++j) tmask |= 1ull << sp.tq[j];
+    const uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    const uint64_t omask = full & ~tmask;
+    const uint64_t ntiles = 1ull << (n - M);
+    const uint64_t xo = px & omask;  // part of the pending X that moves whole tiles
+    const bool pair = xo != 0;
+    const uint64_t xt = pair ? pext64(xo, omask) : 0;
+    const int hbit = pair ? __ffsll((long long)xt) - 1 : 0;
+    const uint64_t nunits = pair ? (ntiles >> 1) : ntiles;
+    const T sc = T(ps);
+    const uint32_t kmask = (1u << sp.kin) - 1;
+
+    // tile-independent parts of this thread's load/store addresses
+    constexpr int VB = sizeof(T) == 4 ? 9 : 8;   // log2 amplitudes covered by one sweep of 256 threads
+    constexpr int NVT = 1 << (M - VB);           // 16-byte vectors per thread per tile
+    const int vl = sizeof(T) == 4 ? L - 1 : L;   // log2 vectors per contiguous chunk
+    const uint32_t wv = uint32_t(tid) & ((1u << vl) - 1u);
+    const uint32_t woff = sizeof(T) == 4 ? (wv << 1) : wv;  // amplitude offset inside the chunk
+    const uint32_t c0 = uint32_t(tid) >> vl;
+    const uint32_t q0 = swz<T>((c0 << L) | woff);
+
+    // Identity projector: raw 16-byte asynchronous copies keep the next tile in
+    // flight while the current one is processed (two shared-memory buffers).
+    // Otherwise the tile is loaded synchronously with the projector applied.
+    const bool pipe = DB && ident;
+    V* const buf0 = tile;
+    V* const buf1 = DB ? tile + (1 << M) : tile;
+    int cur = 0;
+    uint64_t bcur = 0;
+    if (pipe && ustart < nunits) {
+      bcur = pdep64(ustart, omask);
+#pragma unroll
+      for (int k = 0; k < NVT; ++k) {
+        const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+        cp_async16(buf0 + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                   reinterpret_cast<const V*>(A.state) + (bcur | schunk[ch] | woff));
+      }
+    }
+    if (pipe) cp_async_commit();
+
+    for (uint64_t u = ustart; u < nunits; u += ustep) {
+      uint64_t tl[2] = {u, 0};
+      int cnt = 1;
+      if (pair) {
+        const uint64_t lo = u & ((1ull << hbit) - 1);
+        const uint64_t t0 = ((u >> hbit) << (hbit + 1)) | lo;
+        const uint64_t t1 = t0 ^ xt;
+        const uint64_t b0 = pdep64(t0, omask);
+        const bool t0_reads = (((b0 ^ px) & pm & omask) == (pv & omask));
+        tl[0] = t0_reads ? t0 : t1;  // the tile that reads its partner goes first
+        tl[1] = t0_reads ? t1 : t0;
+        cnt = 2;
+      }
+      for (int k2 = 0; k2 < cnt; ++k2) {
+        V* tb;
+        uint64_t base;
+        uint64_t bnext = 0;
+        if (pipe) {
+          base = bcur;
+          tb = cur ? buf1 : buf0;
+          const uint64_t un = u + ustep;
+          if (un < nunits) {
+            bnext = pdep64(un, omask);
+            V* nb = cur ? buf0 : buf1;
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) {
+              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+              cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                         reinterpret_cast<const V*>(A.state) + (bnext | schunk[ch] | woff));
+            }
+          }
+          cp_async_commit();
+          cp_async_wait<1>();
+        } else {
+          tb = tile;
+          base = pdep64(tl[k2], omask);
+          const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
+          // a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv, else 0
+#pragma unroll
+          for (int k = 0; k < NVT; ++k) {
+            const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+            const uint64_t gi = base | schunk[ch] | woff;
+            const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+            if constexpr (sizeof(T) == 4) {
+              const float4* gs = reinterpret_cast<const float4*>(A.state);
+              float2 x0, x1;
+              if (zero_tile) {
+                x0 = x1 = make_float2(0.f, 0.f);
+              } else if (ident) {
+                const float4 q = __ldcg(gs + (gi >> 1));
+                x0 = make_float2(q.x, q.y);
+                x1 = make_float2(q.z, q.w);
+              } else {
+                const uint64_t s0 = gi ^ px;
+                const bool ok0 = (s0 & pm) == pv, ok1 = ((s0 ^ 1ull) & pm) == pv;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ok0 || ok1) q = __ldcg(gs + (s0 >> 1));
+                const float2 e0 = make_float2(q.x, q.y), e1 = make_float2(q.z, q.w);
+                x0 = (s0 & 1) ? e1 : e0;
+                x1 = (s0 & 1) ? e0 : e1;
+                x0 = ok0 ? make_float2(x0.x * sc, x0.y * sc) : make_float2(0.f, 0.f);
+                x1 = ok1 ? make_float2(x1.x * sc, x1.y * sc) : make_float2(0.f, 0.f);
+              }
+              *reinterpret_cast<float4*>(tile + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+            } else {
+              const double2* gs = reinterpret_cast<const double2*>(A.state);
+              double2 x;
+              if (zero_tile) {
+                x = make_double2(0, 0);
+              } else if (ident) {
+                x = __ldcg(gs + gi);
+              } else {
+                const uint64_t s0 = gi ^ px;
+                if ((s0 & pm) == pv) {
+                  x = __ldcg(gs + s0);
+                  x.x *= sc;
+                  x.y *= sc;
+                } else {
+                  x = make_double2(0, 0);
+                }
+              }
+              tile[p] = x;
+            }
+          }
+        }
+        __syncthreads();
+
+        // ---- gate stages
+        if (any_gate) {
+          for (uint32_t si = 0; si < sp.ns; ++si) {
+            const DStage st = A.stages[sp.s0 + si];
+            uint32_t off[16];
+            reg_offsets(st.R, off);
+            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+              const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
+              V a[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
+              for (int g = st.g0; g < st.g0 + st.ng; ++g) {
+                const uint32_t w = sgk[g];
+                if (w & 0x100u) apply_gate(a, w & 0xFFu, smat + (w >> 16));
+              }
+#pragma unroll
+              for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
+            }
+            __syncthreads();
+          }
+        }
+
+        // ---- measurement-group table
+        if (needed) {
+          Acc acc[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
+          uint32_t off[16];
+          reg_offsets(sp.red_R, off);
+          for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+            const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const V x = tb[b ^ off[j]];
+              acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
+            }
+          }
+          const Acc r = warp_transpose_reduce16(acc, lane);
+          if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = double(r);
+          __syncthreads();
+          if (tid < 16) {
+            double s2 = 0;
+            for (int w = 0; w < PASS_THREADS / 32; ++w) s2 += sh.wsum[w][tid];
+            tile16[tid] = s2;
+          }
+          __syncthreads();
+          if (tid < (1 << sp.kin)) {
+            uint32_t ob = 0;
+            for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
+            double s2 = 0;
+            for (int j = 0; j < 16; ++j)
+              if ((uint32_t(j) & kmask) == uint32_t(tid)) s2 += tile16[j];
+            ctab[tid | (ob << sp.kin)] += s2;
+          }
+        }
+
+        // ---- store
+        if (do_store) {
+#pragma unroll
+          for (int k = 0; k < NVT; ++k) {
+            const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+            const uint64_t gi = base | schunk[ch] | woff;
+            const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+            if constexpr (sizeof(T) == 4)
+              __stcg(reinterpret_cast<float4*>(A.state) + (gi >> 1), *reinterpret_cast<const float4*>(tb + p));
+            else
+              __stcg(reinterpret_cast<double2*>(A.state) + gi, tb[p]);
+          }
+        }
+        __syncthreads();
+        if (pipe) {
+          bcur = bnext;
+          cur ^= 1;
+        }
+      }
+    }
+    if (pipe) cp_async_wait<0>();
+  }
+
+  if constexpr (CTA) {
+    if (need_ticket) {
+      __syncthreads();
+      if (tid == 0) scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
+    }
+    __syncthreads();
+  } else {
+    if (!need_ticket) return;
+    if (needed && tid < 16) A.partials[blockIdx.x * 16 + tid] = ctab[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned t = atomicAdd(&A.ctrl->ticket, 1u);
+      sh.s_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sh.s_last) return;
+    __threadfence();
+    if (needed && tid < 16) {
+      double s = 0;
+      for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(A.partials + b * 16 + tid);
+      ctab[tid] = s;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
+  }
+}
+
+}  // namespace svk

@@ -514,7 +514,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     return SV_ERR_ARG;
   }
   P.n = n;
-  P.n_int = std::max(n, 10);  // small states are padded with qubits that stay |0>
+  P.n_int = std::max(n, std::max(tune.min_qubits, 10));  // small states are padded with qubits that stay |0>
   P.dtype = dtype;
   int tb = tune.tile_bits > 0 ? tune.tile_bits : 12;
   // shared-memory tile: 2^14 x 8 B (complex64) or 2^13 x 16 B (complex128) at most

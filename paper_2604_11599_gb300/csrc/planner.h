@@ -14,6 +14,7 @@ struct Tuning {
   int tile_bits = 12;      // m: qubits held by one shared-memory tile
   int low_bits = -1;       // L: contiguous low qubits of every tile (-1: per dtype)
   int max_pass_gates = 0;  // 0: up to MAX_PASS_GATES
+  int min_qubits = 10;     // states are padded to at least this many qubits
 };
 
 struct Plan {

@@ -127,9 +127,8 @@ struct sv_state {
 
 namespace {
 
-sv_status upload_program(sv_state* h, sv_program* p) {
+sv_status upload_plan(cudaStream_t s, size_t amp_bytes, sv_program* p) {
   const svp::Plan& P = p->plan;
-  cudaStream_t s = h->stream;
   SV_CUDA(p->passes.upload(P.passes, s));
   SV_CUDA(p->gates.upload(P.gates, s));
   SV_CUDA(p->stages.upload(P.stages, s));
@@ -137,13 +136,15 @@ sv_status upload_program(sv_state* h, sv_program* p) {
   SV_CUDA(p->init.upload(P.init_items, s));
   SV_CUDA(p->jobs.upload(P.jobs, s));
   SV_CUDA(p->consts.upload(P.consts, s));
-  SV_CUDA(p->mats.reserve(size_t(std::max<uint32_t>(P.n_mat, 1)) * h->amp_bytes));
+  SV_CUDA(p->mats.reserve(size_t(std::max<uint32_t>(P.n_mat, 1)) * amp_bytes));
   SV_CUDA(p->flags.reserve(std::max<uint32_t>(P.n_flags, 1)));
   SV_CUDA(cudaMemsetAsync(p->flags.p, 0, std::max<uint32_t>(P.n_flags, 1), s));
   // the host copies above read pageable vectors; finish them before the plan can change
   SV_CUDA(cudaStreamSynchronize(s));
   return SV_OK;
 }
+
+sv_status upload_program(sv_state* h, sv_program* p) { return upload_plan(h->stream, h->amp_bytes, p); }
 
 int pass_grid(sv_state* h, int m) {
   int per_sm = 1;
@@ -570,6 +571,239 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
   for (size_t t = 0; t < n_terms; ++t) tot += terms[t].coeff * per[t];
   if (total) *total = tot;
   if (per_term) std::copy(per.begin(), per.end(), per_term);
+  return SV_OK;
+}
+
+// ------------------------------------------------------------------ batched execution
+
+}  // extern "C"
+
+struct sv_batch {
+  sv_dtype dtype = SV_C64;
+  size_t amp_bytes = 8;
+  int sms = 0, grid = 0;
+  cudaStream_t user = nullptr, own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<std::unique_ptr<sv_program>> progs;
+  std::vector<svk::BatchProg> hprogs;
+  std::vector<uint32_t> prog_nint, prog_flags;
+  DevBuf<svk::BatchProg> d_progs;
+  DevBuf<svk::BatchItem> d_items;
+  DevBuf<unsigned char> slots;
+  DevBuf<uint8_t> fslots;
+  DevBuf<Ctrl> ctrls;
+  DevBuf<unsigned> queue;
+  DevBuf<int> status;
+  DevBuf<uint64_t> cregs;
+  DevBuf<double> prm;
+  Ctrl* prep_ctrl = nullptr;
+  size_t n_items = 0;
+  uint64_t slot_amps = 0;
+  uint32_t slot_flags = 0;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t gkey = 0;
+  ~sv_batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (prep_ctrl) cudaFree(prep_ctrl);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (own) cudaStreamDestroy(own);
+  }
+};
+
+extern "C" {
+
+sv_status sv_batch_create(sv_dtype dtype, void* cuda_stream, sv_batch** out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  std::unique_ptr<sv_batch> b(new sv_batch());
+  b->dtype = dtype;
+  b->amp_bytes = dtype == SV_C64 ? 8 : 16;
+  int dev = 0;
+  SV_CUDA(cudaGetDevice(&dev));
+  SV_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+  b->user = static_cast<cudaStream_t>(cuda_stream);
+  SV_CUDA(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
+  SV_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  SV_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  if (cudaMalloc(&b->prep_ctrl, sizeof(Ctrl)) != cudaSuccess) return fail(SV_ERR_OOM, "batch control block");
+  int per_sm = 1;
+  if (svk::batch_occupancy(dtype, &per_sm) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SV_ERR_CUDA, "batched kernel configuration failed");
+  }
+  b->grid = b->sms * per_sm;
+  *out = b.release();
+  return SV_OK;
+}
+
+sv_status sv_batch_add_program(sv_batch* b, int n, const sv_op* ops, size_t n_ops, const double* params,
+                               size_t n_params, const double* dense_pool, size_t n_complex, uint32_t* prog_id) {
+  if (!b || !prog_id) return fail(SV_ERR_ARG, "null argument");
+  if (n_params && !params) return fail(SV_ERR_ARG, "params is NULL");
+  std::unique_ptr<sv_program> p(new sv_program());
+  svp::Tuning t;
+  t.tile_bits = svk::BATCH_TILE_BITS;
+  t.min_qubits = svk::BATCH_TILE_BITS;
+  std::string err;
+  sv_status st = svp::build_plan(n, b->dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, t, p->plan, err);
+  if (st != SV_OK) return fail(st, err);
+  const svp::Plan& P = p->plan;
+  if (n_params < P.n_params_needed) return fail(SV_ERR_ARG, "program references more parameters than given");
+  st = upload_plan(b->own, b->amp_bytes, p.get());
+  if (st != SV_OK) return st;
+  if (n_params) {
+    SV_CUDA(b->prm.reserve(n_params));
+    SV_CUDA(cudaMemcpyAsync(b->prm.p, params, n_params * sizeof(double), cudaMemcpyHostToDevice, b->own));
+  }
+  SV_CUDA(cudaMemsetAsync(b->prep_ctrl, 0, sizeof(Ctrl), b->own));
+  svk::PrepArgs pa{};
+  pa.jobs = p->jobs.p;
+  pa.njobs = int(P.jobs.size());
+  pa.params = n_params ? b->prm.p : nullptr;
+  pa.n_params = n_params;
+  pa.consts = p->consts.p;
+  pa.mats = p->mats.p;
+  pa.ctrl = b->prep_ctrl;
+  pa.init = p->init.p;
+  pa.ninit = 0;
+  pa.flags = p->flags.p;
+  SV_CUDA(svk::launch_prep(b->dtype, pa, b->own));
+  int32_t pst = 0;
+  SV_CUDA(cudaMemcpyAsync(&pst, &b->prep_ctrl->status, sizeof(pst), cudaMemcpyDeviceToHost, b->own));
+  SV_CUDA(cudaStreamSynchronize(b->own));
+  if (pst) return fail(SV_ERR_ARG, "parameter index out of range");
+  svk::BatchProg bp{};
+  bp.passes = p->passes.p;
+  bp.gates = p->gates.p;
+  bp.stages = p->stages.p;
+  bp.scalars = p->scalars.p;
+  bp.mats = p->mats.p;
+  bp.init = p->init.p;
+  bp.npasses = uint32_t(P.passes.size());
+  bp.ninit = uint32_t(P.init_items.size());
+  *prog_id = uint32_t(b->progs.size());
+  b->hprogs.push_back(bp);
+  b->prog_nint.push_back(uint32_t(P.n_int));
+  b->prog_flags.push_back(std::max<uint32_t>(P.n_flags, 1));
+  b->progs.push_back(std::move(p));
+  SV_CUDA(b->d_progs.upload(b->hprogs, b->own));
+  SV_CUDA(cudaStreamSynchronize(b->own));
+  return SV_OK;
+}
+
+sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                             size_t n_items) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  if (n_items && (!prog_ids || !stream_ids || !shots)) return fail(SV_ERR_ARG, "null item arrays");
+  if (n_items >= (size_t(1) << 32)) return fail(SV_ERR_ARG, "too many items");
+  std::vector<svk::BatchItem> items(n_items);
+  uint64_t max_nint = 0;
+  uint32_t max_flags = 1;
+  for (size_t i = 0; i < n_items; ++i) {
+    if (prog_ids[i] >= b->progs.size()) return fail(SV_ERR_ARG, "unknown program id");
+    svk::BatchItem& it = items[i];
+    it.prog = prog_ids[i];
+    it.n_int = b->prog_nint[prog_ids[i]];
+    it.stream = stream_ids[i];
+    it.shot = shots[i];
+    it.out = uint32_t(i);
+    max_nint = std::max<uint64_t>(max_nint, it.n_int);
+    max_flags = std::max(max_flags, b->prog_flags[prog_ids[i]]);
+  }
+  // longest trajectories first, so that the tail of the launch is short
+  std::stable_sort(items.begin(), items.end(),
+                   [](const svk::BatchItem& x, const svk::BatchItem& y) { return x.n_int > y.n_int; });
+  const uint64_t slot_amps = n_items ? (1ull << max_nint) : 1;
+  const size_t need = size_t(b->grid) * slot_amps * b->amp_bytes;
+  size_t free_b = 0, total_b = 0;
+  SV_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  if (need > b->slots.n && need - b->slots.n > free_b) return fail(SV_ERR_OOM, "batch work space exceeds free device memory");
+  if (cudaSuccess != b->slots.reserve(need)) return fail(SV_ERR_OOM, "batch state slots");
+  SV_CUDA(b->fslots.reserve(size_t(b->grid) * max_flags));
+  SV_CUDA(b->ctrls.reserve(size_t(b->grid)));
+  SV_CUDA(b->queue.reserve(1));
+  SV_CUDA(b->status.reserve(1));
+  SV_CUDA(b->cregs.reserve(std::max<size_t>(n_items, 1)));
+  SV_CUDA(b->d_items.upload(items, b->own));
+  SV_CUDA(cudaStreamSynchronize(b->own));
+  b->n_items = n_items;
+  b->slot_amps = slot_amps;
+  b->slot_flags = max_flags;
+  return SV_OK;
+}
+
+sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  svk::BatchArgs a{};
+  a.items = b->d_items.p;
+  a.n_items = uint32_t(b->n_items);
+  a.progs = b->d_progs.p;
+  a.state_slots = b->slots.p;
+  a.slot_amps = b->slot_amps;
+  a.flag_slots = b->fslots.p;
+  a.slot_flags = b->slot_flags;
+  a.ctrls = b->ctrls.p;
+  a.queue = b->queue.p;
+  a.seed = seed;
+  a.creg_out = b->cregs.p;
+  a.status_out = b->status.p;
+  uint64_t key = fnv1a(&a, sizeof(a));
+  key = fnv1a(&b->grid, sizeof(b->grid), key);
+  if (!b->gexec || key != b->gkey) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    SV_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned), b->own);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status.p, 0, sizeof(int), b->own);
+    if (e == cudaSuccess) e = svk::launch_batch(b->dtype, a, b->grid, b->own);
+    cudaError_t e2 = cudaStreamEndCapture(b->own, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e != cudaSuccess ? e : e2, "batch graph capture");
+    }
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+    b->gkey = key;
+  }
+  SV_CUDA(cudaEventRecord(b->ev_in, b->user));
+  SV_CUDA(cudaStreamWaitEvent(b->own, b->ev_in, 0));
+  SV_CUDA(cudaGraphLaunch(b->gexec, b->own));
+  SV_CUDA(cudaEventRecord(b->ev_out, b->own));
+  SV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return SV_OK;
+}
+
+sv_status sv_batch_results(sv_batch* b, uint64_t* creg_out) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  int st = 0;
+  if (b->n_items && creg_out)
+    SV_CUDA(cudaMemcpyAsync(creg_out, b->cregs.p, b->n_items * sizeof(uint64_t), cudaMemcpyDeviceToHost, b->own));
+  SV_CUDA(cudaMemcpyAsync(&st, b->status.p, sizeof(int), cudaMemcpyDeviceToHost, b->own));
+  SV_CUDA(cudaStreamSynchronize(b->own));
+  if (st == SV_ERR_NUMERIC) return fail(SV_ERR_NUMERIC, "a trajectory met a zero-norm state");
+  if (st) return fail(sv_status(st), "device reported an error");
+  return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                       size_t n_items, uint64_t seed, uint64_t* creg_out) {
+  sv_status st = sv_batch_set_items(b, prog_ids, stream_ids, shots, n_items);
+  if (st != SV_OK) return st;
+  st = sv_batch_launch(b, seed);
+  if (st != SV_OK) return st;
+  return sv_batch_results(b, creg_out);
+}
+
+sv_status sv_batch_destroy(sv_batch* b) {
+  if (!b) return SV_OK;
+  cudaStreamSynchronize(b->own);
+  delete b;
   return SV_OK;
 }
 

@@ -57,7 +57,7 @@ constexpr int PASS_THREADS = 256;
 constexpr int MAX_TILE_BITS = 14;
 constexpr int MAX_GROUP_Q = 4;
 constexpr int MAX_PASS_GATES = 128;
-constexpr int MAX_PASS_MAT = 1024;  // complex entries staged in shared memory per pass
+constexpr int MAX_PASS_MAT = 512;   // complex entries staged in shared memory per pass
 constexpr int MAX_TRACE = 4096;     // draw records kept per trajectory
 
 // gate as the kernel sees it: positions are register-bit indices (0..3) of its stage

@@ -80,6 +80,13 @@ def lib():
         "sv_set_cache": ([vp, i32], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
+        "sv_batch_create": ([i32, vp, C.POINTER(vp)], st),
+        "sv_batch_add_program": ([vp, i32, vp, sz, vp, sz, vp, sz, C.POINTER(C.c_uint32)], st),
+        "sv_batch_set_items": ([vp, vp, vp, vp, sz], st),
+        "sv_batch_launch": ([vp, u64], st),
+        "sv_batch_results": ([vp, vp], st),
+        "sv_batch_run": ([vp, vp, vp, vp, sz, u64, vp], st),
+        "sv_batch_destroy": ([vp], st),
         "sv_last_error": ([], C.c_char_p),
         "sv_version": ([], C.c_char_p),
     }
@@ -302,6 +309,68 @@ def plan_info(ops: np.ndarray, n: int, dtype: str = "c64", pool=None, tile_bits:
     _check(lib().sv_plan_info(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(p),
                               0 if p is None else p.size, tile_bits, low_bits, max_pass_gates, C.byref(s)))
     return {k: getattr(s, k) for k, _ in ProgramStats._fields_}
+
+
+class Batch:
+    """Many trajectories in one persistent launch (``sv_batch_*``)."""
+
+    def __init__(self, dtype: str = "c64", stream=None):
+        self.dtype = dtype
+        torch = _torch()
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        _check(lib().sv_batch_create(SV_C64 if dtype == "c64" else SV_C128, stream, C.byref(h)))
+        self._h = h.value
+        self.n_items = 0
+
+    def add_program(self, ops: np.ndarray, n: int, params=None, pool=None) -> int:
+        ops = _ops(ops)
+        p = _f64(params)
+        pl = None if pool is None or len(pool) == 0 else np.ascontiguousarray(pool, dtype=np.complex128)
+        pid = C.c_uint32(0)
+        _check(lib().sv_batch_add_program(self._h, n, _ptr(ops), len(ops), _ptr(p), 0 if p is None else p.size,
+                                          _ptr(pl), 0 if pl is None else pl.size, C.byref(pid)))
+        return int(pid.value)
+
+    def set_items(self, prog_ids, stream_ids, shots) -> None:
+        pr = np.ascontiguousarray(prog_ids, dtype=np.uint32)
+        sid = np.ascontiguousarray(stream_ids, dtype=np.uint64)
+        sh = np.ascontiguousarray(shots, dtype=np.uint64)
+        if not (pr.size == sid.size == sh.size):
+            raise ValueError("item arrays differ in length")
+        _check(lib().sv_batch_set_items(self._h, _ptr(pr), _ptr(sid), _ptr(sh), pr.size))
+        self.n_items = pr.size
+
+    def launch(self, seed: int = 0) -> None:
+        _check(lib().sv_batch_launch(self._h, seed))
+
+    def results(self) -> np.ndarray:
+        out = np.zeros(self.n_items, dtype=np.uint64)
+        _check(lib().sv_batch_results(self._h, _ptr(out)))
+        return out
+
+    def run(self, prog_ids, stream_ids, shots, seed: int = 0) -> np.ndarray:
+        self.set_items(prog_ids, stream_ids, shots)
+        self.launch(seed)
+        return self.results()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def sv_expval_static(dev_state_ptr: int, n: int, dtype: str, terms: np.ndarray, dev_out_ptr: int,
