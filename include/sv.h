@@ -261,6 +261,35 @@ sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* st
                        size_t n_items, uint64_t seed, uint64_t* creg_out);
 sv_status sv_batch_destroy(sv_batch* b);
 
+/*
+ * Energies and adjoint gradients of <H> = sum_t coeff_t <psi(theta)|P_t|psi(theta)>
+ * for many parameter sets of one static parameterised program (the VQE loop
+ * of Sec. IV-D: one lowered program, new parameters each call).  The program
+ * may contain gates and DENSE unitaries on <= 3 qubits only (no MEASURE,
+ * RESET, COND); parameters enter angles as scale * theta[pidx].
+ *
+ * sv_grad_create   lowers the program for n qubits and copies the Pauli terms.
+ * sv_grad_run      device pointers: params [P][n_params] doubles; writes
+ *                  val [P] (energies) and grad [P][n_params] (dE/dtheta),
+ *                  asynchronously on the handle's stream.  One persistent
+ *                  launch: each CTA runs whole parameter sets (forward sweep,
+ *                  lambda = H psi, backward sweep with the derivative
+ *                  accumulations), FP64 accumulation.
+ * sv_expval_grad_batch  the same with host arrays, waiting for the result.
+ * Errors: SV_ERR_ARG (bad sizes or masks, n_params below the largest index
+ * referenced, more than 1024 parameters), SV_ERR_UNSUPPORTED (program with
+ * measurement / control flow / 4-qubit dense gates), SV_ERR_OOM.
+ */
+typedef struct sv_grad sv_grad;
+sv_status sv_grad_create(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                         size_t n_complex, const sv_pauli* terms, size_t n_terms, void* cuda_stream, sv_grad** out);
+sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_t n_params, double* dev_val,
+                      double* dev_grad);
+sv_status sv_grad_destroy(sv_grad* g);
+sv_status sv_expval_grad_batch(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* params,
+                               size_t n_sets, size_t n_params, const sv_pauli* terms, size_t n_terms, double* val_out,
+                               double* grad_out, void* cuda_stream);
+
 /* Copy amplitudes [first, first+count) to / from host memory (amplitude-size elements). */
 sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count);
 sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count);

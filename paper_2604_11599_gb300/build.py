@@ -16,7 +16,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsv.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["kern_pass.cu", "kern_measure.cu", "kern_batch.cu", "sv_api.cu", "planner.cpp", "expval_static.cu"]
+SOURCES = ["kern_pass.cu", "kern_measure.cu", "kern_batch.cu", "kern_adjoint.cu", "sv_api.cu", "planner.cpp",
+           "expval_static.cu"]
 HEADERS = ["sv_plan.h", "kernels.h", "planner.h", "dev_common.cuh", "pass_body.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

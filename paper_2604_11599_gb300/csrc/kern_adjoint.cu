@@ -1,0 +1,280 @@
+// kern_adjoint.cu -- batched adjoint gradients of <H> for parameterised circuits.
+//
+// For a parameter set theta, E(theta) = <psi|H|psi> with psi = U_N ... U_1 |0>.
+// With phi_{k+1} = U_k phi_k and lambda_k = U_{k+1}^dagger ... U_N^dagger H psi,
+//   dE/d theta_p = sum over gates k using theta_p of 2 Re <lambda_k| dU_k |phi_k>
+//                = 2 Re <lambda_k| (dU_k U_k^dagger) |phi_{k+1}>,
+// so one backward sweep that starts from phi = psi, lambda = H psi and, gate
+// by gate in reverse, first accumulates Re <lambda| M_k |phi> (M_k = 2 * scale
+// * dU_k U_k^dagger) and then applies U_k^dagger to both phi and lambda gives
+// every entry (the adjoint differentiation method; Sec. II-D and IV-D of the
+// paper motivate runtime parameters for VQE loops).
+//
+// One CTA owns one parameter set at a time (persistent over a work queue):
+// forward passes in CTA mode, lambda = H psi by a grouped Pauli gather (also
+// giving E), then backward passes whose tiles hold phi and lambda side by side:
+// register bit 3 selects phi / lambda, so the gate templates apply U^dagger to
+// both at once and the accumulations pair each phi amplitude with its lambda.
+#include "pass_body.cuh"
+
+namespace svk {
+using namespace svp;
+
+template <typename T, int M>
+__global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
+  using V = typename CxT<T>::V;
+  using Acc = T;
+  constexpr int GB = M - ADJ_REG_BITS;  // group-index bits of a backward stage
+  constexpr int NGRP = 1 << GB;
+  constexpr int VB = sizeof(T) == 4 ? 9 : 8;
+  constexpr int NVT = 1 << (M - VB);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PassShared<T> sh;
+  __shared__ double gacc[MAX_ADJ_PARAMS];
+  __shared__ double wdot[PASS_THREADS / 32][MAX_PASS_DOTS];
+  __shared__ uint16_t sdslot[MAX_PASS_GATES];
+  __shared__ uint32_t sdotg[MAX_PASS_DOTS];
+  __shared__ double ered[PASS_THREADS / 32];
+  __shared__ unsigned s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t N = 1ull << J.n_int;
+  V* phi = reinterpret_cast<V*>(J.slots) + size_t(blockIdx.x) * 2 * J.slot_amps;
+  V* lam = phi + J.slot_amps;
+  Ctrl* C = J.ctrls + blockIdx.x;
+  uint8_t* flags = J.flag_slots + size_t(blockIdx.x) * J.slot_flags;
+
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(J.queue, 1u);
+    __syncthreads();
+    const unsigned set = s_item;
+    __syncthreads();
+    if (set >= J.nsets) break;
+
+    // ---- forward: psi = U |0>
+    for (uint64_t i = tid; i < N; i += PASS_THREADS) phi[i] = (i == 0) ? mkc(T(1), T(0)) : mkc(T(0), T(0));
+    if (tid == 0) {
+      C->creg = 0;
+      C->m = 0;
+      C->pm = C->pv = C->px = 0;
+      C->ps = 1.0;
+      C->ticket = 0;
+      C->status = 0;
+      C->n_trace = MAX_TRACE;
+    }
+    __threadfence_block();
+    __syncthreads();
+    PassArgs A = J.fwd;
+    A.state = phi;
+    A.ctrl = C;
+    A.flags = flags;
+    A.mats = reinterpret_cast<const V*>(J.fwd.mats) + uint64_t(set) * J.f_mat_stride;
+    A.n = J.n_int;
+    for (uint32_t pi = 0; pi < J.f_npasses; ++pi) pass_body<T, M, true>(A, int(pi), sh, smem_raw);
+
+    // ---- lambda = H psi and E = <psi|lambda>
+    {
+      // Hamiltonian terms staged in the (idle) dynamic shared memory; the
+      // 16-byte coefficients first so that they stay 16-byte aligned
+      double2* hc = reinterpret_cast<double2*>(smem_raw);
+      uint64_t* hz = reinterpret_cast<uint64_t*>(hc + J.nterms);
+      for (uint32_t t = tid; t < J.nterms; t += PASS_THREADS) {
+        hz[t] = J.hz[t];
+        hc[t] = J.hc[t];
+      }
+      __syncthreads();
+      double e = 0;
+      for (uint64_t i = tid; i < N; i += PASS_THREADS) {
+        Acc ar = 0, ai = 0;
+        for (uint32_t g = 0; g < J.ngroups; ++g) {
+          const uint64_t j = i ^ J.hx[g];
+          const V pj = phi[j];
+          double wr = 0, wi = 0;
+          for (uint32_t t = J.hg0[g]; t < J.hg0[g + 1]; ++t) {
+            const double sgn = (__popcll(j & hz[t]) & 1) ? -1.0 : 1.0;
+            wr += sgn * hc[t].x;
+            wi += sgn * hc[t].y;
+          }
+          ar += Acc(wr) * pj.x - Acc(wi) * pj.y;
+          ai += Acc(wr) * pj.y + Acc(wi) * pj.x;
+        }
+        lam[i] = mkc(ar, ai);
+        const V pi_ = phi[i];
+        e += double(pi_.x) * double(ar) + double(pi_.y) * double(ai);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if (lane == 0) ered[warp] = e;
+      for (uint32_t p = tid; p < J.n_params; p += PASS_THREADS) gacc[p] = 0.0;
+      __threadfence_block();
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0;
+        for (int w = 0; w < PASS_THREADS / 32; ++w) s += ered[w];
+        J.val_out[set] = s;
+      }
+    }
+
+    // ---- backward passes over phi and lambda
+    V* tphi = reinterpret_cast<V*>(smem_raw);
+    V* tlam = tphi + (1 << M);
+    const V* bm = reinterpret_cast<const V*>(J.b_mats) + uint64_t(set) * J.b_mat_stride;
+    for (uint32_t bp = 0; bp < J.b_npasses; ++bp) {
+      if (tid == 0) sh.sp = J.b_passes[bp];
+      __syncthreads();
+      const DPass& sp = sh.sp;
+      const int L = sp.L;
+      uint32_t ndots = 0;
+      for (int g = tid; g < int(sp.ng); g += PASS_THREADS) {
+        const DGate d = J.b_gates[sp.g0 + g];
+        sh.sgk[g] = uint32_t(d.key) | (1u << 8) | (d.mat << 16);
+        sdslot[g] = d.dslot;
+        if (d.op == OP_DOT || d.op == OP_CDOT) sdotg[d.dslot] = d.gidx;
+      }
+      for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) sh.smat[i] = bm[sp.mat0 + i];
+      for (int i = tid; i < (PASS_THREADS / 32) * MAX_PASS_DOTS; i += PASS_THREADS) (&wdot[0][0])[i] = 0.0;
+      const int hb = M - L;
+      for (int c = tid; c < (1 << hb); c += PASS_THREADS) {
+        uint64_t o = 0;
+        for (int k = 0; k < hb; ++k)
+          if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
+        sh.schunk[c] = o;
+      }
+      __syncthreads();
+      for (int g = 0; g < int(sp.ng); ++g) {
+        const uint32_t op = (sh.sgk[g] & 0xFFu) >> 4;
+        if (op == OP_DOT || op == OP_CDOT) ndots = max(ndots, uint32_t(sdslot[g]) + 1);
+      }
+      uint64_t tmask = 0;
+      for (int j = 0; j < M; ++j) tmask |= 1ull << sp.tq[j];
+      const uint64_t omask = (N - 1) & ~tmask;
+      const uint64_t ntiles = 1ull << (J.n_int - M);
+      const int vl = sizeof(T) == 4 ? L - 1 : L;
+      const uint32_t wv = uint32_t(tid) & ((1u << vl) - 1u);
+      const uint32_t woff = sizeof(T) == 4 ? (wv << 1) : wv;
+      const uint32_t c0 = uint32_t(tid) >> vl;
+      const uint32_t q0 = swz<T>((c0 << L) | woff);
+
+      for (uint64_t u = 0; u < ntiles; ++u) {
+        const uint64_t base = pdep64(u, omask);
+#pragma unroll
+        for (int k = 0; k < NVT; ++k) {
+          const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+          const uint64_t gi = base | sh.schunk[ch] | woff;
+          const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+          cp_async16(tphi + p, phi + gi);
+          cp_async16(tlam + p, lam + gi);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (uint32_t si = 0; si < sp.ns; ++si) {
+          const DStage st = J.b_stages[sp.s0 + si];
+          uint32_t off[8];
+          off[0] = 0;
+#pragma unroll
+          for (int j = 1; j < 8; ++j) off[j] = off[j & (j - 1)] ^ st.R[__ffs(j) - 1];
+          for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+            const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
+            V a[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              a[j] = tphi[b ^ off[j]];
+              a[j + 8] = tlam[b ^ off[j]];
+            }
+            for (int g = st.g0; g < st.g0 + st.ng; ++g) {
+              const uint32_t w = sh.sgk[g];
+              const uint32_t key = w & 0xFFu;
+              const uint32_t op = key >> 4;
+              const V* mt = sh.smat + (w >> 16);
+              if (op == OP_DOT || op == OP_CDOT) {
+                Acc r = apply_dot(a, key, mt);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+                if (lane == 0) wdot[warp][sdslot[g]] += double(r);
+              } else {
+                apply_gate(a, key, mt);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              tphi[b ^ off[j]] = a[j];
+              tlam[b ^ off[j]] = a[j + 8];
+            }
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < NVT; ++k) {
+          const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+          const uint64_t gi = base | sh.schunk[ch] | woff;
+          const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+          if constexpr (sizeof(T) == 4) {
+            __stcg(reinterpret_cast<float4*>(phi) + (gi >> 1), *reinterpret_cast<const float4*>(tphi + p));
+            __stcg(reinterpret_cast<float4*>(lam) + (gi >> 1), *reinterpret_cast<const float4*>(tlam + p));
+          } else {
+            __stcg(phi + gi, tphi[p]);
+            __stcg(lam + gi, tlam[p]);
+          }
+        }
+        __syncthreads();
+      }
+      // per-pass accumulators into the gradient (fixed order: warps, then dots)
+      if (tid == 0)
+        for (uint32_t d = 0; d < ndots; ++d) {
+          double s = 0;
+          for (int w = 0; w < PASS_THREADS / 32; ++w) s += wdot[w][d];
+          gacc[sdotg[d]] += s;
+        }
+      __syncthreads();
+    }
+    for (uint32_t p = tid; p < J.n_params; p += PASS_THREADS)
+      J.grad_out[uint64_t(set) * J.n_params + p] = gacc[p];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+static size_t adjoint_smem(uint32_t nterms) {
+  using V = typename CxT<T>::V;
+  const size_t tiles = 2 * (size_t(1) << BATCH_TILE_BITS) * sizeof(V);
+  const size_t terms = size_t(nterms) * (sizeof(uint64_t) + sizeof(double2));
+  return tiles > terms ? tiles : terms;
+}
+
+cudaError_t launch_adjoint(int dtype, const AdjArgs& a, int grid, cudaStream_t s) {
+  if (dtype == SV_C64) {
+    const size_t sm = adjoint_smem<float>(a.nterms);
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint<float, BATCH_TILE_BITS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    k_adjoint<float, BATCH_TILE_BITS><<<grid, PASS_THREADS, sm, s>>>(a);
+  } else {
+    const size_t sm = adjoint_smem<double>(a.nterms);
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint<double, BATCH_TILE_BITS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    k_adjoint<double, BATCH_TILE_BITS><<<grid, PASS_THREADS, sm, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_occupancy(int dtype, uint32_t nterms, int* blocks_per_sm) {
+  cudaError_t e;
+  if (dtype == SV_C64) {
+    const size_t sm = adjoint_smem<float>(nterms);
+    e = cudaFuncSetAttribute(k_adjoint<float, BATCH_TILE_BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_adjoint<float, BATCH_TILE_BITS>,
+                                                        PASS_THREADS, sm);
+  } else {
+    const size_t sm = adjoint_smem<double>(nterms);
+    e = cudaFuncSetAttribute(k_adjoint<double, BATCH_TILE_BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_adjoint<double, BATCH_TILE_BITS>,
+                                                        PASS_THREADS, sm);
+  }
+  if (e != cudaSuccess || *blocks_per_sm < 1) *blocks_per_sm = 1;
+  return e;
+}
+
+}  // namespace svk

@@ -7,10 +7,14 @@
 namespace svk {
 using namespace svp;
 
+// Matrix jobs of a plan from the run-time parameters (FP64, rounded to the
+// state precision).  blockIdx.y indexes parameter sets: set y reads
+// params + y * params_stride and writes mats + y * mats_stride.
 template <typename T>
 __global__ void k_prep(PrepArgs P) {
   using V = typename CxT<T>::V;
-  V* mats = reinterpret_cast<V*>(P.mats);
+  V* mats = reinterpret_cast<V*>(P.mats) + uint64_t(blockIdx.y) * P.mats_stride;
+  const double* params = P.params ? P.params + uint64_t(blockIdx.y) * P.params_stride : nullptr;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < P.njobs) {
     const DJob j = P.jobs[i];
@@ -21,34 +25,63 @@ __global__ void k_prep(PrepArgs P) {
       double t[3];
       for (int k = 0; k < 3; ++k) {
         if (j.pidx[k] >= 0) {
-          if (uint64_t(j.pidx[k]) < P.n_params) t[k] = j.angle[k] * P.params[j.pidx[k]];
-          else { t[k] = 0; P.ctrl->status = SV_ERR_ARG; }
+          if (uint64_t(j.pidx[k]) < P.n_params) t[k] = j.angle[k] * params[j.pidx[k]];
+          else {
+            t[k] = 0;
+            if (P.ctrl) P.ctrl->status = SV_ERR_ARG;
+          }
         } else {
           t[k] = j.angle[k];
         }
       }
       double2 m[4];
       std_gate_2x2(j.gate, t, m);
-      switch (j.op) {
-        case OP_U: case OP_CU:
-          for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(m[k].y));
-          break;
-        case OP_R:
-          for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(0));
-          break;
-        case OP_RX:  // m00 = c, m01 = -i s
-          mats[j.out] = mkc(T(m[0].x), T(0));
-          mats[j.out + 1] = mkc(T(-m[1].y), T(0));
-          break;
-        case OP_D: case OP_CD:
-          mats[j.out] = mkc(T(m[0].x), T(m[0].y));
-          mats[j.out + 1] = mkc(T(m[3].x), T(m[3].y));
-          break;
-        default: break;
+      if (j.kind == J_DERIV) {
+        // M = 2 * scale * (dU/da) * U^dagger: the gradient entry is Re <lambda| M |phi>
+        double2 d[4];
+        const int slot = int(j.len);
+        std_gate_deriv(j.gate, t, slot, d);
+        const double f = 2.0 * j.angle[slot];
+        for (int r = 0; r < 2; ++r)
+          for (int c = 0; c < 2; ++c) {
+            // (d U^dagger)[r][c] = sum_k d[r][k] conj(U[c][k])
+            double re = 0, im = 0;
+            for (int k = 0; k < 2; ++k) {
+              const double2 a = d[2 * r + k], b = m[2 * c + k];
+              re += a.x * b.x + a.y * b.y;
+              im += a.y * b.x - a.x * b.y;
+            }
+            mats[j.out + 2 * r + c] = mkc(T(f * re), T(f * im));
+          }
+      } else {
+        if (j.adj) {  // conjugate transpose
+          const double2 m01 = m[1];
+          m[1] = make_double2(m[2].x, -m[2].y);
+          m[2] = make_double2(m01.x, -m01.y);
+          m[0].y = -m[0].y;
+          m[3].y = -m[3].y;
+        }
+        switch (j.op) {
+          case OP_U: case OP_CU:
+            for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(m[k].y));
+            break;
+          case OP_R:
+            for (int k = 0; k < 4; ++k) mats[j.out + k] = mkc(T(m[k].x), T(0));
+            break;
+          case OP_RX:  // m00 = c, m01 = -i s
+            mats[j.out] = mkc(T(m[0].x), T(0));
+            mats[j.out + 1] = mkc(T(-m[1].y), T(0));
+            break;
+          case OP_D: case OP_CD:
+            mats[j.out] = mkc(T(m[0].x), T(m[0].y));
+            mats[j.out + 1] = mkc(T(m[3].x), T(m[3].y));
+            break;
+          default: break;
+        }
       }
     }
   }
-  if (i == 0) {
+  if (i == 0 && blockIdx.y == 0 && P.ctrl) {
     Ctrl* C = P.ctrl;
     C->creg = 0;
     C->seed = P.seed;
@@ -59,7 +92,6 @@ __global__ void k_prep(PrepArgs P) {
     C->ps = 1.0;
     C->ticket = 0;
     C->n_trace = 0;
-    if (C->status == 0) C->status = 0;
     for (int k = 0; k < P.ninit; ++k) {  // COND evaluations before the first measurement
       const DScalar s = P.init[k];
       const bool par = s.flag < 0 || P.flags[s.flag];
@@ -131,7 +163,7 @@ cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, c
 }
 
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s) {
-  const int blocks = p.njobs > 0 ? (p.njobs + 255) / 256 : 1;
+  const dim3 blocks(p.njobs > 0 ? (p.njobs + 255) / 256 : 1, p.nsets > 0 ? p.nsets : 1);
   if (dtype == SV_C64) k_prep<float><<<blocks, 256, 0, s>>>(p);
   else k_prep<double><<<blocks, 256, 0, s>>>(p);
   return cudaGetLastError();

@@ -34,6 +34,9 @@ struct PrepArgs {
   int ninit;
   uint8_t* flags;
   uint64_t seed, stream, shot;
+  uint32_t nsets;           // parameter sets (grid y); 0 or 1: one set
+  uint64_t params_stride;   // doubles between parameter sets
+  uint64_t mats_stride;     // complex entries between matrix sets
 };
 
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s);
@@ -78,6 +81,37 @@ struct BatchArgs {
 constexpr int BATCH_TILE_BITS = 12;
 cudaError_t launch_batch(int dtype, const BatchArgs& a, int grid, cudaStream_t s);
 cudaError_t batch_occupancy(int dtype, int* blocks_per_sm);
+
+// batched adjoint gradients: one CTA per parameter set (persistent)
+struct AdjArgs {
+  PassArgs fwd;  // forward plan (state, ctrl, flags, mats and n are set per CTA)
+  uint32_t f_npasses;
+  uint64_t f_mat_stride;  // complex entries per parameter set
+  const svp::DPass* b_passes;
+  const svp::DGate* b_gates;
+  const svp::DStage* b_stages;
+  uint32_t b_npasses;
+  const void* b_mats;
+  uint64_t b_mat_stride;
+  const uint64_t* hx;   // [ngroups] X mask of each term group
+  const uint32_t* hg0;  // [ngroups + 1] first term of each group
+  uint32_t ngroups;
+  const uint64_t* hz;   // [nterms] Z masks
+  const double2* hc;    // [nterms] coefficient * i^{|x&z|}
+  uint32_t nterms;
+  void* slots;          // [grid][2][slot_amps]: phi, lambda
+  uint64_t slot_amps;
+  svp::Ctrl* ctrls;
+  uint8_t* flag_slots;
+  uint32_t slot_flags;
+  unsigned* queue;
+  uint32_t nsets, n_params;
+  int n_int;
+  double* val_out;   // [nsets]
+  double* grad_out;  // [nsets][n_params]
+};
+cudaError_t launch_adjoint(int dtype, const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t adjoint_occupancy(int dtype, uint32_t nterms, int* blocks_per_sm);
 
 // terminal sampling: block sums -> scan -> per-shot search
 struct SampleArgs {

@@ -188,6 +188,53 @@ __device__ __forceinline__ void g_d16(V* a, const V* m) {
   case OP * 16 + 14: FN<3, 2>(a, mt); break;
 
 // one switch on key = op * 16 + p0 * 4 + p1 selects the gate and its register positions
+// ---- backward (adjoint) stages: phi in registers 0..7, lambda in 8..15
+// Re <lambda| M |phi> over the register pairs of position P (or of target T
+// where control C is 1).
+template <int P, typename V>
+__device__ __forceinline__ auto g_dot(const V* a, const V* m) -> decltype(a[0].x) {
+  decltype(a[0].x) r = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j & (1 << P)) continue;
+    const int k = j | (1 << P);
+    const V w0 = cmac2(m[0], a[j], m[1], a[k]);
+    const V w1 = cmac2(m[2], a[j], m[3], a[k]);
+    r += a[j + 8].x * w0.x + a[j + 8].y * w0.y + a[k + 8].x * w1.x + a[k + 8].y * w1.y;
+  }
+  return r;
+}
+
+template <int C, int T, typename V>
+__device__ __forceinline__ auto g_cdot(const V* a, const V* m) -> decltype(a[0].x) {
+  decltype(a[0].x) r = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (!(j & (1 << C)) || (j & (1 << T))) continue;
+    const int k = j | (1 << T);
+    const V w0 = cmac2(m[0], a[j], m[1], a[k]);
+    const V w1 = cmac2(m[2], a[j], m[3], a[k]);
+    r += a[j + 8].x * w0.x + a[j + 8].y * w0.y + a[k + 8].x * w1.x + a[k + 8].y * w1.y;
+  }
+  return r;
+}
+
+template <typename V>
+__device__ __forceinline__ auto apply_dot(const V* a, uint32_t key, const V* mt) -> decltype(a[0].x) {
+  switch (key) {
+    case OP_DOT * 16 + 0: return g_dot<0>(a, mt);
+    case OP_DOT * 16 + 4: return g_dot<1>(a, mt);
+    case OP_DOT * 16 + 8: return g_dot<2>(a, mt);
+    case OP_CDOT * 16 + 1: return g_cdot<0, 1>(a, mt);
+    case OP_CDOT * 16 + 2: return g_cdot<0, 2>(a, mt);
+    case OP_CDOT * 16 + 4: return g_cdot<1, 0>(a, mt);
+    case OP_CDOT * 16 + 6: return g_cdot<1, 2>(a, mt);
+    case OP_CDOT * 16 + 8: return g_cdot<2, 0>(a, mt);
+    case OP_CDOT * 16 + 9: return g_cdot<2, 1>(a, mt);
+    default: return 0;
+  }
+}
+
 template <typename V>
 __device__ __forceinline__ void apply_gate(V* a, uint32_t key, const V* mt) {
   switch (key) {
@@ -260,6 +307,57 @@ static __device__ void std_gate_2x2(int gate, const double* t, double2* m) {
   }
 }
 
+
+// d/d(angle[slot]) of the target matrix of a parametrised standard gate
+// (same conventions as std_gate_2x2); zero for gates without that angle.
+static __device__ void std_gate_deriv(int gate, const double* t, int slot, double2* d) {
+  double c, s, sp, cp, sl, cl;
+  for (int k = 0; k < 4; ++k) d[k] = make_double2(0, 0);
+  switch (gate) {
+    case SV_RX: case SV_CRX:
+      if (slot) break;
+      sincos(0.5 * t[0], &s, &c);
+      d[0] = d[3] = make_double2(-0.5 * s, 0);
+      d[1] = d[2] = make_double2(0, -0.5 * c);
+      break;
+    case SV_RY: case SV_CRY:
+      if (slot) break;
+      sincos(0.5 * t[0], &s, &c);
+      d[0] = d[3] = make_double2(-0.5 * s, 0);
+      d[1] = make_double2(-0.5 * c, 0);
+      d[2] = make_double2(0.5 * c, 0);
+      break;
+    case SV_RZ: case SV_CRZ:
+      if (slot) break;
+      sincos(0.5 * t[0], &s, &c);
+      d[0] = make_double2(-0.5 * s, -0.5 * c);  // (-i/2) e^{-i a/2}
+      d[3] = make_double2(-0.5 * s, 0.5 * c);   // (i/2) e^{i a/2}
+      break;
+    case SV_P: case SV_CP:
+      if (slot) break;
+      sincos(t[0], &s, &c);
+      d[3] = make_double2(-s, c);  // i e^{i a}
+      break;
+    case SV_U: case SV_CU:
+      sincos(0.5 * t[0], &s, &c);
+      sincos(t[1], &sp, &cp);
+      sincos(t[2], &sl, &cl);
+      if (slot == 0) {
+        d[0] = make_double2(-0.5 * s, 0);
+        d[1] = make_double2(-0.5 * cl * c, -0.5 * sl * c);
+        d[2] = make_double2(0.5 * cp * c, 0.5 * sp * c);
+        d[3] = make_double2(-0.5 * (cp * cl - sp * sl) * s, -0.5 * (sp * cl + cp * sl) * s);
+      } else if (slot == 1) {
+        d[2] = make_double2(-sp * s, cp * s);  // i e^{i phi} s
+        d[3] = make_double2(-(sp * cl + cp * sl) * c, (cp * cl - sp * sl) * c);
+      } else {
+        d[1] = make_double2(sl * s, -cl * s);  // -i e^{i lambda} s
+        d[3] = make_double2(-(sp * cl + cp * sl) * c, (cp * cl - sp * sl) * c);
+      }
+      break;
+    default: break;
+  }
+}
 
 static __device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
   uint64_t out = 0;

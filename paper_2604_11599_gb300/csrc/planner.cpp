@@ -231,6 +231,8 @@ struct Builder {
   const std::vector<Item>& items;
   int B;  // log2 amplitudes per 16-byte granule (1: complex64, 0: complex128)
   int max_pass_gates;
+  int reg_bits = REG_BITS;  // gate register bits per stage (ADJ_REG_BITS for backward plans)
+  bool adjoint = false;     // backward plan: derivative items, then U^dagger, per gate
 
   Builder(Plan& p, const std::vector<Item>& it, int b, int mpg) : P(p), items(it), B(b), max_pass_gates(mpg) {}
 
@@ -241,10 +243,33 @@ struct Builder {
     return off;
   }
 
+  void emit_job_deriv(const Item& it, int slot, uint32_t out) {
+    DJob j{};
+    j.kind = J_DERIV;
+    j.op = OP_DOT;
+    j.gate = uint8_t(it.gate);
+    for (int k = 0; k < 3; ++k) {
+      j.pidx[k] = it.pidx[k];
+      j.angle[k] = it.angle[k];
+    }
+    j.len = uint32_t(slot);
+    j.out = out;
+    P.jobs.push_back(j);
+  }
+
+  // parametrised angle slots of a gate item (gradient entries)
+  int n_dots(const Item& it) const {
+    if (!adjoint || it.gate < 0) return 0;
+    int d = 0;
+    for (int k = 0; k < 3; ++k) d += it.pidx[k] >= 0;
+    return d;
+  }
+
   void emit_job_gate(const Item& it, uint32_t out) {
     DJob j{};
     j.kind = J_GATE;
     j.op = it.op;
+    j.adj = adjoint ? 1 : 0;
     j.gate = uint8_t(it.gate);
     for (int k = 0; k < 3; ++k) {
       j.pidx[k] = it.pidx[k];
@@ -264,8 +289,19 @@ struct Builder {
     P.jobs.push_back(j);
   }
 
-  // matrix entries of an item once its stage register bits are known
-  int mat_len(const Item& it) const { return op_mat_len(it.op); }
+  // matrix entries of an item (with its derivative items in backward plans)
+  int mat_len(const Item& it) const { return op_mat_len(it.op) + 4 * n_dots(it); }
+
+  // conjugate transpose of a row-major K x K complex matrix (re, im pairs)
+  static std::vector<double> dagger(const double* m, int K) {
+    std::vector<double> v(2 * K * K);
+    for (int r = 0; r < K; ++r)
+      for (int c = 0; c < K; ++c) {
+        v[2 * (r * K + c)] = m[2 * (c * K + r)];
+        v[2 * (r * K + c) + 1] = -m[2 * (c * K + r) + 1];
+      }
+    return v;
+  }
 
   // Emit one pass: `chosen` gate items, tile bits `tq` (m entries), optional phase.
   void emit_pass(const std::vector<int>& chosen, const std::vector<int>& tq, const Segment* seg, bool flush) {
@@ -282,6 +318,7 @@ struct Builder {
     ps.s0 = uint32_t(P.stages.size());
     ps.mat0 = P.n_mat;
     uint32_t mat = 0;
+    uint32_t dots = 0;
 
     // stages: greedy, four register bits, dependency order preserved
     std::vector<int> rem(chosen);
@@ -292,7 +329,7 @@ struct Builder {
         const Item& it = items[idx];
         uint32_t lm = 0;
         for (int k = 0; k < it.nq; ++k) lm |= 1u << loc[it.q[k]];
-        if ((lm & blocked) || popc(S | lm) > REG_BITS) {
+        if ((lm & blocked) || popc(S | lm) > reg_bits) {
           blocked |= lm;
           left.push_back(idx);
           continue;
@@ -303,16 +340,15 @@ struct Builder {
       rem.swap(left);
       DStage st{};
       st.g0 = uint16_t(P.gates.size() - ps.g0);
-      st.ng = uint16_t(sg.size());
       // register bits: the stage's qubits, padded with the highest other local bits
       std::vector<int> reg;
       for (int j = 0; j < m; ++j)
         if ((S >> j) & 1) reg.push_back(j);
-      for (int j = m - 1; j >= 0 && int(reg.size()) < REG_BITS; --j)
+      for (int j = m - 1; j >= 0 && int(reg.size()) < reg_bits; --j)
         if (!((S >> j) & 1)) reg.push_back(j);
       int rpos[MAX_TILE_BITS];
       for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
-      for (int r = 0; r < REG_BITS; ++r) {
+      for (int r = 0; r < reg_bits; ++r) {
         st.R[r] = uint16_t(tile_swizzle(1u << reg[r], B));
         rpos[reg[r]] = r;
       }
@@ -321,9 +357,25 @@ struct Builder {
         if (rpos[j] < 0) freeb.push_back(j);
       uint8_t thr[MAX_TILE_BITS] = {};
       order_thread_bits(freeb, B, thr);
-      for (int k = 0; k < m - REG_BITS; ++k) st.E[k] = uint16_t(tile_swizzle(1u << thr[k], B));
+      for (int k = 0; k < m - reg_bits; ++k) st.E[k] = uint16_t(tile_swizzle(1u << thr[k], B));
       for (int idx : sg) {
         const Item& it = items[idx];
+        // backward plans: derivative accumulations before the gate's U^dagger
+        for (int k = 0; adjoint && it.gate >= 0 && k < 3; ++k) {
+          if (it.pidx[k] < 0) continue;
+          DGate d{};
+          d.op = it.nq == 2 ? OP_CDOT : OP_DOT;
+          d.flag = -1;
+          d.p0 = uint8_t(rpos[loc[it.q[0]]]);
+          d.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;
+          d.key = uint8_t(d.op * 16 + d.p0 * 4 + d.p1);
+          d.mat = mat;
+          d.dslot = uint16_t(dots++);
+          d.gidx = uint32_t(it.pidx[k]);
+          emit_job_deriv(it, k, P.n_mat + mat);
+          mat += 4;
+          P.gates.push_back(d);
+        }
         DGate g{};
         g.op = it.op;
         g.flag = it.flag;
@@ -336,7 +388,7 @@ struct Builder {
           emit_job_gate(it, out);
         } else if (it.op == OP_U || it.op == OP_U4) {
           const int K = it.op == OP_U ? 2 : 4;
-          std::vector<double> v(it.dense, it.dense + 2 * K * K);
+          std::vector<double> v = adjoint ? dagger(it.dense, K) : std::vector<double>(it.dense, it.dense + 2 * K * K);
           emit_job_const(it.op, v, out);
         } else {  // OP_D16: expand onto the four register bits
           const int k = it.nq;
@@ -347,6 +399,12 @@ struct Builder {
             gm |= 1u << ri[r];
           }
           const int K = 1 << k;
+          std::vector<double> du;
+          const double* dm = it.dense;
+          if (adjoint) {
+            du = dagger(it.dense, K);
+            dm = du.data();
+          }
           std::vector<double> v(2 * 256, 0.0);
           for (int a = 0; a < 16; ++a)
             for (int b = 0; b < 16; ++b) {
@@ -356,20 +414,22 @@ struct Builder {
                 la |= ((a >> ri[r]) & 1) << r;
                 lb |= ((b >> ri[r]) & 1) << r;
               }
-              v[2 * (a * 16 + b)] = it.dense[2 * (la * K + lb)];
-              v[2 * (a * 16 + b) + 1] = it.dense[2 * (la * K + lb) + 1];
+              v[2 * (a * 16 + b)] = dm[2 * (la * K + lb)];
+              v[2 * (a * 16 + b) + 1] = dm[2 * (la * K + lb) + 1];
             }
           emit_job_const(OP_D16, v, out);
         }
-        mat += uint32_t(mat_len(it));
+        mat += uint32_t(op_mat_len(it.op));
         P.gates.push_back(g);
       }
+      st.ng = uint16_t(P.gates.size() - ps.g0 - st.g0);  // gate records, derivative items included
       P.stages.push_back(st);
     }
     ps.ng = uint32_t(P.gates.size() - ps.g0);
     ps.ns = uint32_t(P.stages.size() - ps.s0);
     ps.nmat = mat;
     P.n_mat += mat;
+    P.max_dots = std::max(P.max_dots, dots);
     P.max_pass_mat = std::max(P.max_pass_mat, mat);
     P.max_stages = std::max(P.max_stages, ps.ns);
     P.max_gates = std::max(P.max_gates, ps.ng);
@@ -469,19 +529,23 @@ struct Builder {
     while (!rem.empty()) {
       uint64_t T = low, blocked = 0;
       std::vector<int> chosen, left;
-      uint32_t mat = 0;
+      uint32_t mat = 0, dots = 0, recs = 0;
       const size_t cap = max_pass_gates > 0 ? size_t(max_pass_gates) : size_t(MAX_PASS_GATES);
       for (int idx : rem) {
         const Item& it = items[idx];
         const uint64_t qm = it.qmask();
-        const uint32_t ml = uint32_t(op_mat_len(it.op));
-        if ((qm & blocked) || popc(T | qm) > m || chosen.size() >= cap || mat + ml > MAX_PASS_MAT) {
+        const uint32_t ml = uint32_t(mat_len(it));
+        const uint32_t nd = uint32_t(n_dots(it));
+        if ((qm & blocked) || popc(T | qm) > m || recs + 1 + nd > cap || mat + ml > MAX_PASS_MAT ||
+            dots + nd > MAX_PASS_DOTS) {
           blocked |= qm;
           left.push_back(idx);
           continue;
         }
         T |= qm;
         mat += ml;
+        dots += nd;
+        recs += 1 + nd;
         chosen.push_back(idx);
       }
       rem.swap(left);
@@ -615,6 +679,58 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   P.stats.plan_bytes = P.passes.size() * sizeof(DPass) + P.gates.size() * sizeof(DGate) +
                        P.stages.size() * sizeof(DStage) + (P.scalars.size() + P.init_items.size()) * sizeof(DScalar) +
                        P.jobs.size() * sizeof(DJob) + P.consts.size() * sizeof(double);
+  return SV_OK;
+}
+
+sv_status build_adjoint_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                             size_t dense_len, const Tuning& tune, Plan& fwd, Plan& bwd, std::string& err) {
+  sv_status st = build_plan(n, dtype, ops, n_ops, dense_pool, dense_len, tune, fwd, err);
+  if (st != SV_OK) return st;
+  if (fwd.stats.draws || fwd.n_flags) {
+    err = "adjoint gradients need a program without measurement, reset or COND";
+    return SV_ERR_UNSUPPORTED;
+  }
+  Unroller U;
+  U.ops = ops;
+  U.n_ops = n_ops;
+  U.n = n;
+  U.pool = dense_pool;
+  U.pool_len = dense_pool ? dense_len : 0;
+  if (!U.walk(0, n_ops, -1, 0)) {
+    err = U.err;
+    return U.st;
+  }
+  std::vector<Item> rev(U.items.rbegin(), U.items.rend());
+  for (const Item& it : rev) {
+    if (it.nq > ADJ_REG_BITS) {
+      err = "adjoint gradients support dense unitaries on at most 3 qubits";
+      return SV_ERR_UNSUPPORTED;
+    }
+    if (it.gate >= 0)
+      for (int k = 0; k < 3; ++k)
+        if (it.pidx[k] >= MAX_ADJ_PARAMS) {
+          err = "adjoint gradients support at most 1024 parameters";
+          return SV_ERR_UNSUPPORTED;
+        }
+  }
+  bwd = Plan{};
+  bwd.n = fwd.n;
+  bwd.n_int = fwd.n_int;
+  bwd.dtype = dtype;
+  bwd.m = fwd.m;
+  bwd.L = fwd.L;
+  bwd.n_params_needed = fwd.n_params_needed;
+  Builder b(bwd, rev, dtype == SV_C64 ? 1 : 0, tune.max_pass_gates);
+  b.reg_bits = ADJ_REG_BITS;
+  b.adjoint = true;
+  Segment seg;
+  for (size_t i = 0; i < rev.size(); ++i) seg.gates.push_back(int(i));
+  if (!seg.gates.empty()) b.emit_segment(seg);
+  bwd.stats.gates = fwd.stats.gates;
+  bwd.stats.passes = bwd.passes.size();
+  bwd.stats.stages = bwd.stages.size();
+  bwd.stats.tile_bits = bwd.m;
+  bwd.stats.low_bits = bwd.L;
   return SV_OK;
 }
 

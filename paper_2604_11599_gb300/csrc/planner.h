@@ -35,10 +35,19 @@ struct Plan {
   uint32_t max_stages = 0;
   uint32_t max_gates = 0;
   uint32_t max_scalars = 0;
+  uint32_t max_dots = 0;             // backward plans: derivative accumulators per pass
   bool needs_flush = false;
   sv_program_stats stats{};
   uint64_t n_params_needed = 0;      // 1 + the largest parameter index referenced
 };
+
+// Builds the forward plan and the backward (adjoint) plan of a static program
+// for gradients of <H>: `bwd` sweeps the reversed gate list with three gate
+// register bits per stage, each parametrised gate preceded by its derivative
+// accumulation items.  SV_ERR_UNSUPPORTED for programs with measurement,
+// reset, COND or dense 4-qubit gates.
+sv_status build_adjoint_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                             size_t dense_len, const Tuning& tune, Plan& fwd, Plan& bwd, std::string& err);
 
 // Builds a plan; returns SV_OK or an error with a message in `err`.
 sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,

@@ -807,6 +807,200 @@ sv_status sv_batch_destroy(sv_batch* b) {
   return SV_OK;
 }
 
+// ------------------------------------------------------------------ adjoint gradients
+
+}  // extern "C"
+
+struct sv_grad {
+  sv_dtype dtype = SV_C64;
+  size_t amp_bytes = 8;
+  int sms = 0, grid = 0;
+  cudaStream_t stream = nullptr;
+  sv_program fwd, bwd;
+  uint32_t n_params_needed = 0, ngroups = 0, nterms = 0;
+  DevBuf<unsigned char> fmats, bmats, slots;
+  DevBuf<uint64_t> hx, hz;
+  DevBuf<uint32_t> hg0;
+  DevBuf<double> hc;
+  DevBuf<Ctrl> ctrls;
+  DevBuf<uint8_t> fslots;
+  DevBuf<unsigned> queue;
+};
+
+extern "C" {
+
+sv_status sv_grad_create(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                         size_t n_complex, const sv_pauli* terms, size_t n_terms, void* cuda_stream, sv_grad** out) {
+  if (!out) return fail(SV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  if (n_terms && !terms) return fail(SV_ERR_ARG, "terms is NULL");
+  const uint64_t lim = n >= 64 ? ~0ull : ((1ull << n) - 1);
+  for (size_t t = 0; t < n_terms; ++t)
+    if ((terms[t].x_mask | terms[t].z_mask) & ~lim) return fail(SV_ERR_ARG, "Pauli term acts on a qubit >= n");
+  std::unique_ptr<sv_grad> g(new sv_grad());
+  g->dtype = dtype;
+  g->amp_bytes = dtype == SV_C64 ? 8 : 16;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  SV_CUDA(cudaGetDevice(&dev));
+  SV_CUDA(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev));
+  svp::Tuning t;
+  t.tile_bits = svk::BATCH_TILE_BITS;
+  t.min_qubits = svk::BATCH_TILE_BITS;
+  std::string err;
+  sv_status st = svp::build_adjoint_plan(n, dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, t,
+                                         g->fwd.plan, g->bwd.plan, err);
+  if (st != SV_OK) return fail(st, err);
+  st = upload_plan(g->stream, g->amp_bytes, &g->fwd);
+  if (st != SV_OK) return st;
+  st = upload_plan(g->stream, g->amp_bytes, &g->bwd);
+  if (st != SV_OK) return st;
+  g->n_params_needed = uint32_t(g->fwd.plan.n_params_needed);
+  // Hamiltonian grouped by X mask: per term Z mask and coeff * i^{|x&z|}
+  std::vector<uint64_t> keys;
+  std::map<uint64_t, std::vector<size_t>> groups;
+  for (size_t k = 0; k < n_terms; ++k) {
+    if (!groups.count(terms[k].x_mask)) keys.push_back(terms[k].x_mask);
+    groups[terms[k].x_mask].push_back(k);
+  }
+  std::vector<uint64_t> hx, hz;
+  std::vector<uint32_t> hg0;
+  std::vector<double> hc;
+  for (uint64_t x : keys) {
+    hx.push_back(x);
+    hg0.push_back(uint32_t(hz.size()));
+    for (size_t k : groups[x]) {
+      hz.push_back(terms[k].z_mask);
+      const int ph = __builtin_popcountll(x & terms[k].z_mask) & 3;
+      const double c = terms[k].coeff;
+      const double re[4] = {c, 0, -c, 0}, im[4] = {0, c, 0, -c};  // c * i^ph
+      hc.push_back(re[ph]);
+      hc.push_back(im[ph]);
+    }
+  }
+  hg0.push_back(uint32_t(hz.size()));
+  g->ngroups = uint32_t(hx.size());
+  g->nterms = uint32_t(hz.size());
+  SV_CUDA(g->hx.upload(hx, g->stream));
+  SV_CUDA(g->hz.upload(hz, g->stream));
+  SV_CUDA(g->hg0.upload(hg0, g->stream));
+  SV_CUDA(g->hc.upload(hc, g->stream));
+  SV_CUDA(cudaStreamSynchronize(g->stream));
+  int per_sm = 1;
+  if (svk::adjoint_occupancy(dtype, g->nterms, &per_sm) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SV_ERR_CUDA, "adjoint kernel configuration failed (too many Pauli terms?)");
+  }
+  g->grid = g->sms * per_sm;
+  *out = g.release();
+  return SV_OK;
+}
+
+sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_t n_params, double* dev_val,
+                      double* dev_grad) {
+  if (!g) return fail(SV_ERR_ARG, "null handle");
+  if (!n_sets) return SV_OK;
+  if (n_params < g->n_params_needed) return fail(SV_ERR_ARG, "n_params below the largest parameter index used");
+  if (n_params > size_t(svp::MAX_ADJ_PARAMS)) return fail(SV_ERR_ARG, "at most 1024 parameters");
+  if ((g->n_params_needed && !dev_params) || !dev_val || (n_params && !dev_grad))
+    return fail(SV_ERR_ARG, "null device array");
+  if (n_sets >= (size_t(1) << 31)) return fail(SV_ERR_ARG, "too many parameter sets");
+  const svp::Plan& F = g->fwd.plan;
+  const svp::Plan& B = g->bwd.plan;
+  const uint64_t fstride = std::max<uint32_t>(F.n_mat, 1), bstride = std::max<uint32_t>(B.n_mat, 1);
+  if (g->fmats.reserve(n_sets * fstride * g->amp_bytes) != cudaSuccess ||
+      g->bmats.reserve(n_sets * bstride * g->amp_bytes) != cudaSuccess)
+    return fail(SV_ERR_OOM, "per-set gate matrices");
+  const int grid = int(std::min<size_t>(size_t(g->grid), n_sets));
+  const uint64_t slot = 1ull << F.n_int;
+  if (g->slots.reserve(size_t(grid) * 2 * slot * g->amp_bytes) != cudaSuccess)
+    return fail(SV_ERR_OOM, "phi / lambda work space");
+  SV_CUDA(g->ctrls.reserve(size_t(grid)));
+  SV_CUDA(g->fslots.reserve(size_t(grid)));
+  SV_CUDA(g->queue.reserve(1));
+  cudaStream_t s = g->stream;
+  for (int which = 0; which < 2; ++which) {
+    sv_program& p = which == 0 ? g->fwd : g->bwd;
+    svk::PrepArgs pa{};
+    pa.jobs = p.jobs.p;
+    pa.njobs = int(p.plan.jobs.size());
+    pa.params = dev_params;
+    pa.n_params = n_params;
+    pa.consts = p.consts.p;
+    pa.mats = which == 0 ? g->fmats.p : g->bmats.p;
+    pa.nsets = uint32_t(n_sets);
+    pa.params_stride = n_params;
+    pa.mats_stride = which == 0 ? fstride : bstride;
+    if (pa.njobs) SV_CUDA(svk::launch_prep(g->dtype, pa, s));
+  }
+  SV_CUDA(cudaMemsetAsync(g->queue.p, 0, sizeof(unsigned), s));
+  svk::AdjArgs a{};
+  a.fwd.passes = g->fwd.passes.p;
+  a.fwd.gates = g->fwd.gates.p;
+  a.fwd.stages = g->fwd.stages.p;
+  a.fwd.scalars = g->fwd.scalars.p;
+  a.fwd.mats = g->fmats.p;
+  a.f_npasses = uint32_t(F.passes.size());
+  a.f_mat_stride = fstride;
+  a.b_passes = g->bwd.passes.p;
+  a.b_gates = g->bwd.gates.p;
+  a.b_stages = g->bwd.stages.p;
+  a.b_npasses = uint32_t(B.passes.size());
+  a.b_mats = g->bmats.p;
+  a.b_mat_stride = bstride;
+  a.hx = g->hx.p;
+  a.hg0 = g->hg0.p;
+  a.ngroups = g->ngroups;
+  a.hz = g->hz.p;
+  a.hc = reinterpret_cast<const double2*>(g->hc.p);
+  a.nterms = g->nterms;
+  a.slots = g->slots.p;
+  a.slot_amps = slot;
+  a.ctrls = g->ctrls.p;
+  a.flag_slots = g->fslots.p;
+  a.slot_flags = 1;
+  a.queue = g->queue.p;
+  a.nsets = uint32_t(n_sets);
+  a.n_params = uint32_t(n_params);
+  a.n_int = F.n_int;
+  a.val_out = dev_val;
+  a.grad_out = dev_grad;
+  SV_CUDA(svk::launch_adjoint(g->dtype, a, grid, s));
+  return SV_OK;
+}
+
+sv_status sv_grad_destroy(sv_grad* g) {
+  if (!g) return SV_OK;
+  cudaStreamSynchronize(g->stream);
+  delete g;
+  return SV_OK;
+}
+
+sv_status sv_expval_grad_batch(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* params,
+                               size_t n_sets, size_t n_params, const sv_pauli* terms, size_t n_terms, double* val_out,
+                               double* grad_out, void* cuda_stream) {
+  if (n_sets && (!val_out || (n_params && (!params || !grad_out)))) return fail(SV_ERR_ARG, "null host array");
+  sv_grad* g = nullptr;
+  sv_status st = sv_grad_create(n, dtype, ops, n_ops, nullptr, 0, terms, n_terms, cuda_stream, &g);
+  if (st != SV_OK) return st;
+  std::unique_ptr<sv_grad, sv_status (*)(sv_grad*)> guard(g, sv_grad_destroy);
+  DevBuf<double> dp, dv, dg;
+  SV_CUDA(dp.reserve(std::max<size_t>(n_sets * n_params, 1)));
+  SV_CUDA(dv.reserve(std::max<size_t>(n_sets, 1)));
+  SV_CUDA(dg.reserve(std::max<size_t>(n_sets * n_params, 1)));
+  cudaStream_t s = g->stream;
+  if (n_sets * n_params)
+    SV_CUDA(cudaMemcpyAsync(dp.p, params, n_sets * n_params * sizeof(double), cudaMemcpyHostToDevice, s));
+  st = sv_grad_run(g, dp.p, n_sets, n_params, dv.p, dg.p);
+  if (st != SV_OK) return st;
+  if (n_sets) SV_CUDA(cudaMemcpyAsync(val_out, dv.p, n_sets * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (n_sets * n_params)
+    SV_CUDA(cudaMemcpyAsync(grad_out, dg.p, n_sets * n_params * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SV_CUDA(cudaStreamSynchronize(s));
+  return SV_OK;
+}
+
 sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count) {
   if (!h || (count && !host_dst)) return fail(SV_ERR_ARG, "null argument");
   if (first + count > (size_t(1) << h->n) || first + count < first) return fail(SV_ERR_ARG, "range outside the state");

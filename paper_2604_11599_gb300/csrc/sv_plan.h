@@ -33,13 +33,17 @@ enum OpCode : uint8_t {
   OP_SWAP,  // swap p0 <-> p1
   OP_U4,    // dense 4x4 on (p0 = local bit 0, p1 = local bit 1): 16 complex
   OP_D16,   // dense 16x16 on the four register bits: 256 complex
+  // adjoint (backward) stages only: Re <lambda| M |phi> with phi in registers 0..7 and
+  // lambda in registers 8..15, accumulated for one gradient entry; M = dU/da * U^dagger
+  OP_DOT,   // M (4 complex) on p0
+  OP_CDOT,  // M on target p1 where control p0 is 1
   OP_COUNT
 };
 
 // number of complex matrix entries each op reads
 static inline int op_mat_len(int op) {
   switch (op) {
-    case OP_U: case OP_R: case OP_CU: return 4;
+    case OP_U: case OP_R: case OP_CU: case OP_DOT: case OP_CDOT: return 4;
     case OP_RX: case OP_D: case OP_CD: return 2;
     case OP_U4: return 16;
     case OP_D16: return 256;
@@ -49,7 +53,11 @@ static inline int op_mat_len(int op) {
 
 enum ScalarKind : uint8_t { S_MEASURE = 1, S_RESET = 2, S_COND = 3 };
 
-enum JobKind : uint8_t { J_GATE = 1, J_CONST = 2 };
+enum JobKind : uint8_t {
+  J_GATE = 1,   // gate matrix from its angles (adj = 1: its conjugate transpose)
+  J_CONST = 2,  // copy from the constant pool
+  J_DERIV = 3   // scale * (dU/d angle[slot]) * U^dagger of a one-qubit / controlled gate
+};
 
 constexpr int REG_BITS = 4;
 constexpr int REG_N = 16;
@@ -59,6 +67,9 @@ constexpr int MAX_GROUP_Q = 4;
 constexpr int MAX_PASS_GATES = 128;
 constexpr int MAX_PASS_MAT = 512;   // complex entries staged in shared memory per pass
 constexpr int MAX_TRACE = 4096;     // draw records kept per trajectory
+constexpr int ADJ_REG_BITS = 3;     // gate register bits of a backward stage (bit 3 selects phi / lambda)
+constexpr int MAX_PASS_DOTS = 64;   // derivative accumulators per backward pass
+constexpr int MAX_ADJ_PARAMS = 1024;
 
 // gate as the kernel sees it: positions are register-bit indices (0..3) of its stage
 struct DGate {
@@ -66,7 +77,10 @@ struct DGate {
   uint8_t op, p0, p1;
   int32_t flag;   // -1: unconditional; else index into the flag array
   uint32_t mat;   // offset (complex entries) from the pass's matrix base
-  uint32_t pad2;
+  uint16_t dslot; // OP_DOT / OP_CDOT: accumulator slot within the pass
+  uint16_t pad2;
+  uint32_t gidx;  // OP_DOT / OP_CDOT: gradient entry (parameter index)
+  uint32_t pad3;
 };
 
 // Register stage.  The tile is stored XOR-swizzled in shared memory (see
@@ -127,13 +141,14 @@ struct DPass {
 struct DJob {
   uint8_t kind;     // JobKind
   uint8_t op;       // OpCode the matrix is laid out for
-  uint8_t gate;     // IR gate enum (J_GATE)
-  uint8_t pad;
+  uint8_t gate;     // IR gate enum (J_GATE, J_DERIV)
+  uint8_t adj;      // J_GATE: 1 = write the conjugate transpose
+  
   int32_t pidx[3];
   double angle[3];
   uint32_t out;     // offset (complex entries) into the matrix pool
   uint32_t src;     // J_CONST: offset into the constant pool (complex entries)
-  uint32_t len;     // J_CONST: entries to copy
+  uint32_t len;     // J_CONST: entries to copy; J_DERIV: angle slot
   uint32_t pad2;
 };
 

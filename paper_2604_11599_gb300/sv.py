@@ -87,6 +87,10 @@ def lib():
         "sv_batch_results": ([vp, vp], st),
         "sv_batch_run": ([vp, vp, vp, vp, sz, u64, vp], st),
         "sv_batch_destroy": ([vp], st),
+        "sv_grad_create": ([i32, i32, vp, sz, vp, sz, vp, sz, vp, C.POINTER(vp)], st),
+        "sv_grad_run": ([vp, vp, sz, sz, vp, vp], st),
+        "sv_grad_destroy": ([vp], st),
+        "sv_expval_grad_batch": ([i32, i32, vp, sz, vp, sz, sz, vp, sz, vp, vp, vp], st),
         "sv_last_error": ([], C.c_char_p),
         "sv_version": ([], C.c_char_p),
     }
@@ -371,6 +375,66 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Grad:
+    """Energies and adjoint gradients of <H> for batches of parameter sets
+    (``sv_grad_*``); parameters and results live on the GPU as torch tensors."""
+
+    def __init__(self, ops: np.ndarray, n: int, terms: np.ndarray, dtype: str = "c64", pool=None, stream=None):
+        ops = _ops(ops)
+        terms = np.ascontiguousarray(terms)
+        if terms.dtype != PAULI_DTYPE:
+            raise TypeError("terms must be an array of ir.PAULI_DTYPE records")
+        torch = _torch()
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        pl = None if pool is None or len(pool) == 0 else np.ascontiguousarray(pool, dtype=np.complex128)
+        h = C.c_void_p()
+        _check(lib().sv_grad_create(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(pl),
+                                    0 if pl is None else pl.size, _ptr(terms), len(terms), stream, C.byref(h)))
+        self._h = h.value
+        self.n, self.dtype = n, dtype
+
+    def run(self, params):
+        """params: [P, n_params] float64 CUDA tensor -> (energies [P], gradients [P, n_params])."""
+        import torch
+
+        params = params.detach().contiguous()
+        if params.dtype != torch.float64 or not params.is_cuda or params.dim() != 2:
+            raise TypeError("params must be a 2-D float64 CUDA tensor")
+        P, n_params = params.shape
+        val = torch.empty(P, dtype=torch.float64, device=params.device)
+        grad = torch.empty(P, n_params, dtype=torch.float64, device=params.device)
+        _check(lib().sv_grad_run(self._h, params.data_ptr(), P, n_params, val.data_ptr(), grad.data_ptr()))
+        return val, grad
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_grad_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expval_grad_batch(ops: np.ndarray, n: int, params: np.ndarray, terms: np.ndarray, dtype: str = "c64"):
+    """``sv_expval_grad_batch`` with host arrays: (energies [P], gradients [P, n_params])."""
+    ops = _ops(ops)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    if p.ndim != 2:
+        raise ValueError("params must be [P, n_params]")
+    terms = np.ascontiguousarray(terms)
+    val = np.zeros(p.shape[0])
+    grad = np.zeros_like(p)
+    torch = _torch()
+    stream = torch.cuda.current_stream().cuda_stream if torch is not None and torch.cuda.is_available() else None
+    _check(lib().sv_expval_grad_batch(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(p),
+                                      p.shape[0], p.shape[1], _ptr(terms), len(terms), _ptr(val), _ptr(grad), stream))
+    return val, grad
 
 
 def sv_expval_static(dev_state_ptr: int, n: int, dtype: str, terms: np.ndarray, dev_out_ptr: int,
