@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batching / VQE / serving measurements")
     return ap.parse_args()
 
 
@@ -156,6 +157,87 @@ def oracle_sample(n, dtype, seconds, gates_cap=None):
     ups = k * float(1 << n) / dt
     return ups, f"first {k} gates (gate-only prefix) of the n={n} program, FP64, one trajectory", \
         oracle.get_threads(), dt
+
+
+def measure_forms(sv, torch):
+    """The three serving-style forms against the plain path on the same GPU
+    (bounded runs; the circuits are the seeded workloads of the tests)."""
+    import numpy as np
+
+    from paper_2604_11599_gb300 import serve, workloads as W
+
+    out = {}
+    # batching: 65,536 trajectories of the sequential feed-forward + RUS circuit, n = 12..20 (+1 ancilla)
+    wl = W.batching(seed=6, n_traj=65536)
+    with sv.Batch("c64") as b:
+        pid = {n: b.add_program(c.ops, n + 1) for n, c in wl.circuits.items()}
+        ids = np.array([pid[int(n)] for n in wl.traj_n])
+        b.set_items(ids, np.arange(len(ids)), np.zeros(len(ids)))
+        b.launch(0)
+        b.results()
+        t0 = time.perf_counter()
+        b.launch(0)
+        b.results()
+        tb = time.perf_counter() - t0
+    sample = wl.traj_n[:256]
+    states = {}
+    for n in sorted(set(int(v) for v in sample)):
+        states[n] = sv.State(n + 1, "c64")
+        states[n].run(wl.circuits[n].ops)
+    t0 = time.perf_counter()
+    for i, n in enumerate(sample):
+        states[int(n)].run(wl.circuits[int(n)].ops, seed=0, stream_id=i)
+    tp = time.perf_counter() - t0
+    for st in states.values():
+        st.close()
+    out["batching"] = {"workload": "65,536 trajectories, n~U{12..20}+ancilla, 10 layers, sequential feed-forward "
+                                   "+ loop(4) RUS, complex64, one persistent launch",
+                       "trajectories_per_s": len(ids) / tb, "plain_path_trajectories_per_s": 256 / tp,
+                       "plain_path_sample": "first 256 trajectories, one sv_run each", "seconds": tb}
+    # plain small program, 1,000 shots, complex128
+    c = W.plain_small()
+    with sv.State(5, "c128") as st:
+        st.sample(c.ops, 50)
+        t0 = time.perf_counter()
+        st.sample(c.ops, 1000)
+        tps = time.perf_counter() - t0
+    with sv.Batch("c128") as b:
+        p = b.add_program(c.ops, 5)
+        b.run([p] * 1000, np.zeros(1000), np.arange(1000))
+        t0 = time.perf_counter()
+        b.run([p] * 1000, np.zeros(1000), np.arange(1000))
+        tbs = time.perf_counter() - t0
+    out["plain_small_1000_shots"] = {"plain_path_shots_per_s": 1000 / tps, "batched_shots_per_s": 1000 / tbs}
+    # VQE: n=20 hardware-efficient ansatz, 320 parameters, 200 Pauli terms
+    c = W.hea(20, 8)
+    terms = W.heisenberg_fields(9, 20, 200)
+    vqe = {}
+    for dt, sets in (("c64", 1024), ("c128", 256)):
+        h = sv.Grad(c.ops, 20, terms, dt)
+        prm = torch.tensor(W.hea_params(8, sets, 320), device="cuda")
+        h.run(prm[:4])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.run(prm)
+        torch.cuda.synchronize()
+        dts = time.perf_counter() - t0
+        vqe[dt] = {"parameter_sets": sets, "gradient_sets_per_s": sets / dts, "seconds": dts}
+        h.close()
+    out["vqe_adjoint"] = vqe
+    # serving: a bounded slice of the Poisson request stream, server vs sequential plain path
+    stream = W.serving_stream(seed=10, gen_seed=11, rate=200.0, duration=1.0, n_lo=10, n_hi=22, d_lo=10,
+                              d_hi=40, max_shots=256)
+    reqs = serve.requests_from_stream(stream)
+    be = serve.GpuBackend("c64", seed=0)
+    srv = serve.Server(be)
+    srv.serve(reqs[:4])
+    _, st_srv = srv.serve(reqs)
+    srv.close()
+    _, st_seq = serve.serve_sequential(be, reqs)
+    out["serving"] = {"workload": f"{len(reqs)} requests (Poisson 200/s for 1 s), n log-uniform 10-22, depth "
+                                  "10-40 layers, 1-8 measures with cond/loop feed-forward, shots log-uniform 1-256",
+                      "server": st_srv, "sequential_plain_path": st_seq}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -272,6 +354,10 @@ def main():
     if dtype == "c128":
         roofline["note"] = "complex128 sweeps are FP64-ALU-bound on GB300"
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = measure_forms(sv, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ups, desc, threads, dt = oracle_sample(n, dtype, args.cpu_seconds)
@@ -289,7 +375,7 @@ def main():
                        "low_bits": stats["low_bits"], "l2": "inputs larger than L2 (state 2^n amplitudes)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (2 + stats["passes"]), "clocks": clk,
+            "gpu_launches": args.steps * (2 + stats["passes"]), "clocks": clk, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     st.close()

@@ -1,0 +1,30 @@
+"""Serving: each request's records are the same alone and in the mix (and on the plain path)."""
+import numpy as np
+import pytest
+
+from paper_2604_11599_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_alone_vs_mix_and_plain_path():
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import serve
+
+    stream = W.serving_stream(seed=10, gen_seed=11, rate=400.0, duration=1.0, n_lo=10, n_hi=24,
+                              d_lo=4, d_hi=16, max_shots=48, limit=64)
+    reqs = serve.requests_from_stream(stream)
+    assert any(r.n > 21 for r in reqs) and any(r.n <= 21 for r in reqs)
+    be = serve.GpuBackend("c64", seed=5)
+    srv = serve.Server(be, batch_max_n=21, large_workers=3)
+    mix, stats = srv.serve(reqs)
+    assert stats["requests"] == len(reqs)
+    for q in reqs[:12]:
+        q0 = serve.Req(q.rid, 0.0, q.n, q.ops, q.shots)
+        alone, _ = srv.serve([q0])
+        assert np.array_equal(alone[0].cregs, mix[q.rid].cregs), q.rid
+    for q in reqs[:6]:
+        assert np.array_equal(be.run_large(q), mix[q.rid].cregs), q.rid
+    srv.close()
