@@ -12,8 +12,9 @@ value     updates/s = (gates + measures + resets) * 2^n per step / device time,
           inputs resident (the lowered program is on the device), CUDA events
           on the launching stream, K steps after W warm-up steps.
 e2e       the same metric through sv_run with host buffers: every step lowers
-          the op list and copies the plan to the device, runs, and reads the
-          classical register back.
+          the op list and copies the plan to the device (program cache off;
+          compiled kernels are reused), runs, and reads the classical register
+          back.
 roofline  the state-sweep pass kernel (k_pass): algorithmic bytes (state read
           + written once per storing pass) / its event-timed duration,
           against the measured HBM copy bandwidth.
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batching / VQE / serving measurements")
+    ap.add_argument("--no-jit", action="store_true", help="use the generic pass kernels")
     return ap.parse_args()
 
 
@@ -291,7 +293,10 @@ def main():
     n, dtype = args.n, args.dtype
     c = circuit(n, dtype)
     st = sv.State(n, dtype)
+    st.set_jit(not args.no_jit)
     prog = st.prepare(c.ops)
+    st.launch(prog, seed=0, shot=999)  # first launch compiles the specialised kernels (once per program)
+    torch.cuda.synchronize()
     stats = prog.stats
     upd = float(stats["gates"] + stats["draws"]) * float(1 << n)
     stream = torch.cuda.current_stream()
@@ -348,7 +353,8 @@ def main():
     peaks, kind = measured_peaks()
     achieved = prof["bytes"] / (prof["ms"] / 1000.0) / 1e9 if prof["ms"] > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_pass",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "sv_jit_passes (k_pass specialised)" if stats["specialised"] else "k_pass",
                 "peak_kind": f"of {kind}", "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
                 "avg_launch_ms": prof["ms"] / max(1, prof["launches"])}
     if dtype == "c128":
@@ -373,6 +379,8 @@ def main():
                        "gates_per_step": stats["gates"], "draws_per_step": stats["draws"],
                        "passes_per_step": stats["passes"], "tile_bits": stats["tile_bits"],
                        "low_bits": stats["low_bits"], "l2": "inputs larger than L2 (state 2^n amplitudes)",
+                       "specialised_kernels": bool(stats["specialised"]),
+                       "compile_seconds": round(stats["compile_seconds"], 2),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * (2 + stats["passes"]), "clocks": clk, "forms": forms,

@@ -37,8 +37,10 @@
 #ifndef LIBSV_SV_H_
 #define LIBSV_SV_H_
 
+#ifndef __CUDACC_RTC__
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -120,7 +122,11 @@ typedef struct sv_program_stats {
   uint64_t flags;         /* device predicate slots                       */
   int32_t tile_bits, low_bits;
   uint64_t plan_bytes;    /* bytes of plan data copied to the device      */
+  int32_t specialised;    /* 1: passes run as kernels compiled for this program (sv_set_jit) */
+  double compile_seconds; /* time spent compiling them                    */
 } sv_program_stats;
+
+#ifndef __CUDACC_RTC__ /* device code compiled at run time needs the types above only */
 
 /*
  * Create a state of n qubits (1 <= n <= 34) in |0...0>.
@@ -317,6 +323,24 @@ sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, dou
  */
 sv_status sv_set_cache(sv_state* h, int enable);
 
+/*
+ * Per-program specialisation of the sweep kernels (off by default).  With it
+ * on, the first launch of a program compiles (NVRTC, sm_103a) one kernel per
+ * pass in which gate kinds, register positions and shared-memory addresses
+ * are constants; gate matrices and predicates stay run-time data.  If
+ * compilation fails the program keeps the generic kernels and
+ * sv_program_info reports specialised = 0.
+ */
+sv_status sv_set_jit(sv_state* h, int enable);
+
+/*
+ * Host-only check of the specialiser (no device touched): lowers the op list
+ * and compiles its specialised module to a cubin.  On failure the first
+ * log_len - 1 bytes of the compiler log are copied to log (nullable).
+ */
+sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                       size_t n_complex, char* log, size_t log_len);
+
 /* Wait for all work of h. */
 sv_status sv_sync(sv_state* h);
 
@@ -325,6 +349,8 @@ const char* sv_last_error(void);
 
 /* Library version string. */
 const char* sv_version(void);
+
+#endif /* __CUDACC_RTC__ */
 
 #ifdef __cplusplus
 }

@@ -1,7 +1,9 @@
 // dev_common.cuh -- device helpers shared by the libsv kernels.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "sv_plan.h"
 

@@ -1,0 +1,297 @@
+// jit.cpp -- NVRTC specialisation of the pass kernel for one lowered program.
+#include "jit.h"
+
+#include <cuda.h>
+#include <nvrtc.h>
+
+#include <chrono>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <thread>
+
+#include "jit_headers.inc"
+
+namespace svj {
+
+namespace {
+
+const char* op_template(int op) {
+  switch (op) {
+    case svp::OP_U: return "g_u";
+    case svp::OP_R: return "g_r";
+    case svp::OP_RX: return "g_rx";
+    case svp::OP_D: return "g_d";
+    case svp::OP_X: return "g_x";
+    case svp::OP_CU: return "g_cu";
+    case svp::OP_CX: return "g_cx";
+    case svp::OP_CZ: return "g_cz";
+    case svp::OP_CD: return "g_cd";
+    case svp::OP_SWAP: return "g_swap";
+    case svp::OP_U4: return "g_u4";
+    case svp::OP_D16: return "g_d16";
+    default: return nullptr;
+  }
+}
+
+bool two_qubit(int op) {
+  return op == svp::OP_CU || op == svp::OP_CX || op == svp::OP_CZ || op == svp::OP_CD || op == svp::OP_SWAP ||
+         op == svp::OP_U4;
+}
+
+// one straight-line stage program per pass
+void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
+  const svp::DPass& d = P.passes[pi];
+  const int GB = P.m - svp::REG_BITS;
+  o << "struct JS" << pi << " {\n"
+    << "  template <typename T, int M>\n"
+    << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {\n"
+    << "    using V = typename CxT<T>::V;\n"
+    << "    const int tid = threadIdx.x;\n";
+  for (uint32_t si = 0; si < d.ns; ++si) {
+    const svp::DStage& st = P.stages[d.s0 + si];
+    uint32_t off[16];
+    off[0] = 0;
+    for (int j = 1; j < 16; ++j) off[j] = off[j & (j - 1)] ^ st.R[__builtin_ctz(unsigned(j))];
+    o << "    for (int grp = tid; grp < " << (1 << GB) << "; grp += " << svp::PASS_THREADS << ") {\n"
+      << "      uint32_t b = 0;\n";
+    for (int k = 0; k < GB; ++k) o << "      if (grp & " << (1 << k) << ") b ^= " << st.E[k] << "u;\n";
+    o << "      V a[16];\n";
+    for (int j = 0; j < 16; ++j) o << "      a[" << j << "] = tb[b ^ " << off[j] << "u];\n";
+    for (uint32_t g = st.g0; g < uint32_t(st.g0) + st.ng; ++g) {
+      const svp::DGate& gt = P.gates[d.g0 + g];
+      const char* fn = op_template(gt.op);
+      if (!fn) continue;
+      std::ostringstream call;
+      call << fn;
+      if (gt.op == svp::OP_D16) call << "(a, smat + " << gt.mat << ")";
+      else if (two_qubit(gt.op)) call << "<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ")";
+      else call << "<" << int(gt.p0) << ">(a, smat + " << gt.mat << ")";
+      if (gt.flag >= 0) o << "      if (sgk[" << g << "] & 0x100u) " << call.str() << ";\n";
+      else o << "      " << call.str() << ";\n";
+    }
+    for (int j = 0; j < 16; ++j) o << "      tb[b ^ " << off[j] << "u] = a[" << j << "];\n";
+    o << "    }\n    __syncthreads();\n";
+  }
+  o << "  }\n};\n\n";
+}
+
+// Driver entry points, resolved through the runtime at first use so that the
+// library does not link libcuda (it loads where there is no driver, e.g. for
+// host-only checks).
+struct Driver {
+  CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
+  CUresult (*moduleUnload)(CUmodule) = nullptr;
+  CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
+  CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+  CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                           void**, void**) = nullptr;
+  CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+  bool ok = false;
+};
+
+template <typename F>
+bool resolve(const char* name, F& fn) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p)
+    return false;
+  fn = reinterpret_cast<F>(p);
+  return true;
+}
+
+const Driver& driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    d.ok = resolve("cuModuleLoadData", d.moduleLoadData) && resolve("cuModuleUnload", d.moduleUnload) &&
+           resolve("cuModuleGetFunction", d.moduleGetFunction) && resolve("cuFuncSetAttribute", d.funcSetAttribute) &&
+           resolve("cuLaunchKernel", d.launchKernel) && resolve("cuGetErrorString", d.getErrorString);
+  });
+  return d;
+}
+
+std::string cu_err(CUresult r) {
+  const char* s = nullptr;
+  if (driver().getErrorString) driver().getErrorString(r, &s);
+  return s ? s : ("driver error " + std::to_string(int(r)));
+}
+
+}  // namespace
+
+// Source of one module: the stage programs of passes [p0, p1) and one kernel
+// that selects among them by pass index (a uniform branch per CTA).
+std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
+  std::ostringstream o;
+  const bool c64 = P.dtype == SV_C64;
+  o << "// specialised passes " << p0 << ".." << p1 << ": n = " << P.n_int << ", tile bits " << P.m << ", "
+    << (c64 ? "complex64" : "complex128") << "\n"
+    << "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
+    << "typedef unsigned long long uint64_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+    << "typedef int int32_t;\ntypedef long long int64_t;\n"
+    << "#include \"pass_body.cuh\"\n\nnamespace svk {\n\n";
+  for (size_t pi = p0; pi < p1; ++pi)
+    if (P.passes[pi].ns) emit_stages(o, P, pi);
+  o << "struct JitStages {\n"
+    << "  template <typename T, int M>\n"
+    << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {\n"
+    << "    switch (A.pass) {\n";
+  for (size_t pi = p0; pi < p1; ++pi)
+    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M>(A, sp, sgk, smat, tb); break;\n";
+  o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
+  const char* T = c64 ? "float" : "double";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1)
+    << ") sv_jit_passes(const svk::PassArgs A) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+    << "  __shared__ svk::PassShared<" << T << "> sh;\n"
+    << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages>(A, A.pass, sh, smem_raw);\n}\n";
+  return o.str();
+}
+
+size_t chunk_count(const svp::Plan& P) {
+  const size_t passes = P.passes.size();
+  return passes ? std::min<size_t>(passes, 12) : 1;
+}
+
+std::string generate_source(const svp::Plan& P) { return generate_chunk(P, 0, P.passes.size()); }
+
+namespace {
+
+sv_status compile_source(const std::string& src, std::vector<char>& cubin, std::string& err) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "sv_jit_passes.cu", kJitHeaderCount, kJitHeaderSources,
+                         kJitHeaderNames) != NVRTC_SUCCESS) {
+    err = "nvrtcCreateProgram failed";
+    return SV_ERR_CUDA;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 2, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    err = std::string("NVRTC compile failed: ") + nvrtcGetErrorString(rc) + "\n" + log.substr(0, 4000);
+    return SV_ERR_CUDA;
+  }
+  size_t nbin = 0;
+  nvrtcGetCUBINSize(prog, &nbin);
+  cubin.assign(nbin, 0);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  return SV_OK;
+}
+
+// Compiles the module chunks in parallel (NVRTC programs are independent).
+sv_status compile_chunks(const svp::Plan& P, std::vector<std::vector<char>>& cubins, std::vector<size_t>& first,
+                         std::string& err) {
+  const size_t passes = P.passes.size(), k = chunk_count(P);
+  first.assign(k + 1, 0);
+  for (size_t c = 0; c <= k; ++c) first[c] = passes * c / k;
+  cubins.assign(k, {});
+  std::vector<sv_status> st(k, SV_OK);
+  std::vector<std::string> errs(k);
+  std::vector<std::thread> th;
+  for (size_t c = 0; c < k; ++c)
+    th.emplace_back([&, c] { st[c] = compile_source(generate_chunk(P, first[c], first[c + 1]), cubins[c], errs[c]); });
+  for (auto& t : th) t.join();
+  for (size_t c = 0; c < k; ++c)
+    if (st[c] != SV_OK) {
+      err = errs[c];
+      return st[c];
+    }
+  return SV_OK;
+}
+
+}  // namespace
+
+sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err) {
+  std::vector<std::vector<char>> cubins;
+  std::vector<size_t> first;
+  sv_status st = compile_chunks(P, cubins, first, err);
+  if (st == SV_OK && !cubins.empty()) cubin = cubins[0];
+  return st;
+}
+
+JitModule::~JitModule() {
+  for (void* m : modules)
+    if (m && driver().moduleUnload) driver().moduleUnload(static_cast<CUmodule>(m));
+}
+
+sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::string& err) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, std::shared_ptr<JitModule>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string all;
+  for (size_t c = 0, k = chunk_count(P), n = P.passes.size(); c < k; ++c)
+    all += generate_chunk(P, n * c / k, n * (c + 1) / k);
+  const auto key = std::make_pair(dev, std::hash<std::string>{}(all));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      out = it->second;
+      return SV_OK;
+    }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::vector<char>> cubins;
+  std::vector<size_t> first;
+  sv_status st = compile_chunks(P, cubins, first, err);
+  if (st != SV_OK) return st;
+  const Driver& D = driver();
+  if (!D.ok) {
+    err = "CUDA driver entry points unavailable";
+    return SV_ERR_CUDA;
+  }
+  std::unique_ptr<JitModule> J(new JitModule());
+  const size_t amp = P.dtype == SV_C64 ? 8 : 16;
+  const size_t one = (size_t(1) << P.m) * amp;
+  J->smem = 2 * one <= size_t(128) * 1024 ? 2 * one : one;
+  J->functions.assign(P.passes.size(), nullptr);
+  for (size_t c = 0; c < cubins.size(); ++c) {
+    CUmodule mod;
+    CUresult r = D.moduleLoadData(&mod, cubins[c].data());
+    if (r != CUDA_SUCCESS) {
+      err = "cuModuleLoadData: " + cu_err(r);
+      return SV_ERR_CUDA;
+    }
+    J->modules.push_back(mod);
+    CUfunction f;
+    r = D.moduleGetFunction(&f, mod, "sv_jit_passes");
+    if (r == CUDA_SUCCESS) r = D.funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
+    if (r != CUDA_SUCCESS) {
+      err = "loading a specialised module: " + cu_err(r);
+      return SV_ERR_CUDA;
+    }
+    for (size_t pi = first[c]; pi < first[c + 1]; ++pi) J->functions[pi] = f;
+  }
+  J->compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out = std::shared_ptr<JitModule>(std::move(J));
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() > 64) cache.clear();
+  cache[key] = out;
+  return SV_OK;
+}
+
+sv_status launch(const JitModule& J, int pass, const svk::PassArgs& a, int grid, cudaStream_t s, std::string& err) {
+  svk::PassArgs b = a;
+  b.pass = pass;
+  void* args[] = {&b};
+  const CUresult r = driver().launchKernel(static_cast<CUfunction>(J.functions[size_t(pass)]), unsigned(grid), 1, 1,
+                                    svp::PASS_THREADS, 1, 1, unsigned(J.smem), reinterpret_cast<CUstream>(s), args,
+                                    nullptr);
+  if (r != CUDA_SUCCESS) {
+    err = "specialised pass launch: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  return SV_OK;
+}
+
+}  // namespace svj

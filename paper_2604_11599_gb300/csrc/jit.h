@@ -1,0 +1,44 @@
+// jit.h -- per-program specialisation of the pass kernel (NVRTC).
+//
+// A lowered program fixes, for every pass, its gate kinds, their register
+// positions and the shared-memory addresses of every stage.  The specialiser
+// writes one kernel per pass in which those are compile-time constants: no
+// gate dispatch at run time, CX / X / SWAP become register renames and
+// addresses fold into immediates.  Gate matrices and predicate flags remain
+// run-time data, so the compiled module serves every parameter set and every
+// trajectory of the program (compiled once, run many).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "kernels.h"
+#include "planner.h"
+
+namespace svj {
+
+struct JitModule {
+  std::vector<void*> modules;      // CUmodule per chunk of passes
+  std::vector<void*> functions;    // CUfunction of each pass
+  size_t smem = 0;                 // dynamic shared memory per launch
+  double compile_seconds = 0;
+  ~JitModule();
+};
+
+// Source text of the specialised module (for tests and inspection of the generator).
+std::string generate_source(const svp::Plan& P);
+
+// NVRTC only (no device needed): the module's cubin.
+sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err);
+
+// compile_cubin + load into the current context.  Modules are cached for the
+// process by device and generated source, so a program lowered again reuses
+// its compiled kernels.
+sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::string& err);
+
+sv_status launch(const JitModule& J, int pass, const svk::PassArgs& a, int grid, cudaStream_t s, std::string& err);
+
+}  // namespace svj

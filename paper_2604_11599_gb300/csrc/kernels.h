@@ -1,7 +1,9 @@
 // kernels.h -- host-side launchers of the libsv kernels.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "../../include/sv.h"
 #include "sv_plan.h"
@@ -20,6 +22,7 @@ struct PassArgs {
   svp::DTrace* trace;
   double* partials;  // [grid][16]
   int n;             // simulated qubits
+  int pass;          // pass index (specialised kernels select their stage program by it)
 };
 
 struct PrepArgs {
@@ -39,10 +42,18 @@ struct PrepArgs {
   uint64_t mats_stride;     // complex entries between matrix sets
 };
 
+#ifndef __CUDACC_RTC__
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm);
+#endif
 
 // persistent batched execution: one CTA runs one trajectory at a time
 struct BatchProg {
@@ -79,8 +90,12 @@ struct BatchArgs {
   int* status_out;      // first nonzero trajectory status
 };
 constexpr int BATCH_TILE_BITS = 12;
+#ifndef __CUDACC_RTC__
 cudaError_t launch_batch(int dtype, const BatchArgs& a, int grid, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 cudaError_t batch_occupancy(int dtype, int* blocks_per_sm);
+#endif
 
 // batched adjoint gradients: one CTA per parameter set (persistent)
 struct AdjArgs {
@@ -110,8 +125,12 @@ struct AdjArgs {
   double* val_out;   // [nsets]
   double* grad_out;  // [nsets][n_params]
 };
+#ifndef __CUDACC_RTC__
 cudaError_t launch_adjoint(int dtype, const AdjArgs& a, int grid, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 cudaError_t adjoint_occupancy(int dtype, uint32_t nterms, int* blocks_per_sm);
+#endif
 
 // terminal sampling: block sums -> scan -> per-shot search
 struct SampleArgs {
@@ -123,8 +142,12 @@ struct SampleArgs {
   uint64_t shots, seed, stream, shot0;
   uint64_t* out;         // [shots]
 };
+#ifndef __CUDACC_RTC__
 cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t s);
+#endif
+#ifndef __CUDACC_RTC__
 uint64_t sample_blocks(int n);
+#endif
 
 // Pauli expectation values of one group of terms sharing an X mask
 struct ExpvalArgs {
@@ -138,6 +161,8 @@ struct ExpvalArgs {
   double* out;              // [nterms] (written by the last CTA)
   unsigned* ticket;
 };
+#ifndef __CUDACC_RTC__
 cudaError_t launch_expval_group(int dtype, const ExpvalArgs& a, int grid, cudaStream_t s);
+#endif
 
 }  // namespace svk

@@ -508,7 +508,38 @@ struct PassShared {
 // and runs the scalar phase.  CTA mode (CTA = true): the calling CTA owns the
 // whole trajectory, walks every tile itself and runs the scalar phase after a
 // block barrier; used by the persistent batched kernel.
-template <typename T, int M, bool CTA>
+// Data-driven register stages: every stage reads its register / group bit
+// addresses and gate records from the plan at run time.
+struct GenericStages {
+  template <typename T, int M>
+  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,
+                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {
+    using V = typename CxT<T>::V;
+    constexpr int GB = M - REG_BITS;
+    constexpr int NGRP = 1 << GB;
+    const int tid = threadIdx.x;
+    for (uint32_t si = 0; si < sp.ns; ++si) {
+      const DStage st = A.stages[sp.s0 + si];
+      uint32_t off[16];
+      reg_offsets(st.R, off);
+      for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+        const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
+        V a[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
+        for (int g = st.g0; g < st.g0 + st.ng; ++g) {
+          const uint32_t w = sgk[g];
+          if (w & 0x100u) apply_gate(a, w & 0xFFu, smat + (w >> 16));
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
+      }
+      __syncthreads();
+    }
+  }
+};
+
+template <typename T, int M, bool CTA, typename Stages = GenericStages>
 __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T>& sh, void* smem_tiles) {
   using V = typename CxT<T>::V;
   using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
@@ -699,26 +730,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         __syncthreads();
 
         // ---- gate stages
-        if (any_gate) {
-          for (uint32_t si = 0; si < sp.ns; ++si) {
-            const DStage st = A.stages[sp.s0 + si];
-            uint32_t off[16];
-            reg_offsets(st.R, off);
-            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
-              const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
-              V a[16];
-#pragma unroll
-              for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
-              for (int g = st.g0; g < st.g0 + st.ng; ++g) {
-                const uint32_t w = sgk[g];
-                if (w & 0x100u) apply_gate(a, w & 0xFFu, smat + (w >> 16));
-              }
-#pragma unroll
-              for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
-            }
-            __syncthreads();
-          }
-        }
+        if (any_gate) Stages::template run<T, M>(A, sp, sgk, smat, tb);
 
         // ---- measurement-group table
         if (needed) {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/sv.h"
+#include "jit.h"
 #include "kernels.h"
 #include "planner.h"
 
@@ -91,6 +92,8 @@ struct sv_program {
   DevBuf<unsigned char> mats;
   DevBuf<uint8_t> flags;
   bool cached = false;  // owned by the state's cache
+  std::shared_ptr<svj::JitModule> jit;  // specialised pass kernels (sv_set_jit)
+  bool jit_tried = false;
 };
 
 struct sv_state {
@@ -123,6 +126,7 @@ struct sv_state {
   size_t ev_used = 0;
   double prof_bytes = 0;
   bool use_cache = true;
+  bool use_jit = false;
 };
 
 namespace {
@@ -182,6 +186,12 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
   pa.shot = shot;
   SV_CUDA(svk::launch_prep(h->dtype, pa, s));
   SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
+  if (h->use_jit && !p->jit_tried) {
+    p->jit_tried = true;
+    std::string err;
+    if (svj::compile(P, p->jit, err) != SV_OK) p->jit.reset();  // generic kernels remain
+  }
+  const svj::JitModule* jm = h->use_jit ? p->jit.get() : nullptr;
   if (!P.passes.empty()) {
     const int grid = pass_grid(h, P.m);
     if (grid < 1) return fail(SV_ERR_CUDA, "pass kernel configuration failed for tile bits " + std::to_string(P.m));
@@ -208,7 +218,13 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
         }
         SV_CUDA(cudaEventRecord(h->events[h->ev_used], s));
       }
-      SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s));
+      if (jm) {
+        std::string err;
+        const sv_status st = svj::launch(*jm, int(i), a, grid, s, err);
+        if (st != SV_OK) return fail(st, err);
+      } else {
+        SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s));
+      }
       if (h->profiling) {
         SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));
         h->ev_used += 2;
@@ -411,6 +427,33 @@ sv_status sv_program_free(sv_program* p) {
 sv_status sv_program_info(const sv_program* p, sv_program_stats* out) {
   if (!p || !out) return fail(SV_ERR_ARG, "null argument");
   *out = p->plan.stats;
+  out->specialised = p->jit ? 1 : 0;
+  out->compile_seconds = p->jit ? p->jit->compile_seconds : 0.0;
+  return SV_OK;
+}
+
+sv_status sv_set_jit(sv_state* h, int enable) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->use_jit = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                       size_t n_complex, char* log, size_t log_len) {
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  svp::Plan P;
+  std::string err;
+  sv_status st = svp::build_plan(n, dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, svp::Tuning{}, P, err);
+  if (st == SV_OK) {
+    std::vector<char> cubin;
+    st = svj::compile_cubin(P, cubin, err);
+  }
+  if (log && log_len) {
+    const size_t k = std::min(err.size(), log_len - 1);
+    std::memcpy(log, err.data(), k);
+    log[k] = 0;
+  }
+  if (st != SV_OK) return fail(st, err);
   return SV_OK;
 }
 

@@ -15,7 +15,9 @@
 //                      Sec. III-C: predicates are read from the classical record
 //                      on the GPU, never on the host).
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
 
 namespace svp {
 
@@ -40,6 +42,7 @@ enum OpCode : uint8_t {
   OP_COUNT
 };
 
+#ifndef __CUDACC_RTC__
 // number of complex matrix entries each op reads
 static inline int op_mat_len(int op) {
   switch (op) {
@@ -50,6 +53,7 @@ static inline int op_mat_len(int op) {
     default: return 0;
   }
 }
+#endif
 
 enum ScalarKind : uint8_t { S_MEASURE = 1, S_RESET = 2, S_COND = 3 };
 
@@ -99,6 +103,7 @@ struct DStage {
 // the higher index bits.  A = log2(amplitudes per granule) (1 for complex64,
 // 0 for complex128); amplitude pairs of complex64 stay adjacent, so a
 // 16-byte copy moves a granule verbatim.  The map is linear over GF(2).
+#ifndef __CUDACC_RTC__
 static inline uint32_t tile_swizzle(uint32_t x, int A) {
   uint32_t y = x >> (A + 3), f = 0;
   for (int k = 0; k < 5; ++k) {
@@ -107,6 +112,7 @@ static inline uint32_t tile_swizzle(uint32_t x, int A) {
   }
   return x ^ (f << A);
 }
+#endif
 
 struct DScalar {
   uint8_t kind;     // ScalarKind

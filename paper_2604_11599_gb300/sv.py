@@ -40,7 +40,7 @@ class ProgramStats(C.Structure):
     _fields_ = [("records", C.c_uint64), ("unrolled_ops", C.c_uint64), ("gates", C.c_uint64),
                 ("draws", C.c_uint64), ("passes", C.c_uint64), ("stages", C.c_uint64),
                 ("flags", C.c_uint64), ("tile_bits", C.c_int32), ("low_bits", C.c_int32),
-                ("plan_bytes", C.c_uint64)]
+                ("plan_bytes", C.c_uint64), ("specialised", C.c_int32), ("compile_seconds", C.c_double)]
 
 
 _lib = None
@@ -78,6 +78,8 @@ def lib():
         "sv_sync": ([vp], st),
         "sv_profile": ([vp, i32], st),
         "sv_set_cache": ([vp, i32], st),
+        "sv_set_jit": ([vp, i32], st),
+        "sv_jit_check": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
         "sv_batch_create": ([i32, vp, C.POINTER(vp)], st),
@@ -210,6 +212,10 @@ class State:
         p = np.ascontiguousarray(pool, dtype=np.complex128)
         self._pool = p
         _check(lib().sv_set_dense_pool(self._h, _ptr(p), p.size))
+
+    def set_jit(self, enable: bool) -> None:
+        """Per-program specialised sweep kernels (compiled on a program's first launch)."""
+        _check(lib().sv_set_jit(self._h, 1 if enable else 0))
 
     def set_cache(self, enable: bool) -> None:
         _check(lib().sv_set_cache(self._h, 1 if enable else 0))
@@ -447,6 +453,18 @@ def sv_expval_static(dev_state_ptr: int, n: int, dtype: str, terms: np.ndarray, 
         raise TypeError("terms must be an array of ir.PAULI_DTYPE records")
     _check(lib().sv_expval_static(dev_state_ptr, n, SV_C64 if dtype == "c64" else SV_C128, _ptr(terms), len(terms),
                                   dev_out_ptr, stream))
+
+
+def jit_check(ops: np.ndarray, n: int, dtype: str = "c64", pool=None) -> str:
+    """Compiles a program's specialised module on the host (no GPU); returns the log, raises on failure."""
+    ops = _ops(ops)
+    pl = None if pool is None or len(pool) == 0 else np.ascontiguousarray(pool, dtype=np.complex128)
+    buf = C.create_string_buffer(8192)
+    st = lib().sv_jit_check(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(pl),
+                            0 if pl is None else pl.size, buf, 8192)
+    if st != 0:
+        raise SVError(st, buf.value.decode(errors="replace"))
+    return buf.value.decode(errors="replace")
 
 
 def version() -> str:

@@ -58,6 +58,28 @@ def test_max_pass_gates_one_gate_per_pass(svmod, orc, dtype):
         compare_run(st, orc, c.ops, n, dtype)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_specialised_kernels_parity(svmod, orc, dtype):
+    """Per-program compiled pass kernels (sv_set_jit) give the same records and
+    amplitudes as the oracle, for static, dense and dynamic programs."""
+    import torch
+
+    cases = [(W.layered(2, 16, layers=6), 16, 0), (W.random_static(21, 14, 80, dense_k=3, params=3), 14, 3),
+             (W.random_dynamic(9, 15, n_ops=70, dense_k=2), 15, 0)]
+    for c, n, npar in cases:
+        params = np.random.default_rng(n).uniform(-2, 2, size=npar) if npar else None
+        with svmod.State(n, dtype) as st:
+            st.set_jit(True)
+            st.set_dense_pool(c.pool)
+            for shot in range(3):
+                compare_run(st, orc, c.ops, n, dtype, params=params, seed=4, shot=shot, pool=c.pool)
+            prog = st.prepare(c.ops)
+            dp = None if params is None else torch.tensor(params, device="cuda")
+            st.launch(prog, dp, seed=4, shot=0)
+            st.sync()
+            assert prog.stats["specialised"] == 1
+
+
 # --------------------------------------------------------------------------- dynamic circuits
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n", [2, 4, 6, 9, 13, 16])
