@@ -662,19 +662,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         if (pipe) {
           base = bcur;
           tb = cur ? buf1 : buf0;
-          const uint64_t un = u + ustep;
-          if (un < nunits) {
-            bnext = pdep64(un, omask);
-            V* nb = cur ? buf0 : buf1;
-#pragma unroll
-            for (int k = 0; k < NVT; ++k) {
-              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
-              cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
-                         reinterpret_cast<const V*>(A.state) + (bnext | schunk[ch] | woff));
-            }
-          }
-          cp_async_commit();
-          cp_async_wait<1>();
+          cp_async_wait<0>();  // this tile's copies, issued one iteration earlier
         } else {
           tb = tile;
           base = pdep64(tl[k2], omask);
@@ -727,7 +715,23 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             }
           }
         }
+        // All threads: this tile has landed, and every thread is done with the
+        // previous tile, so the other buffer can be refilled.
         __syncthreads();
+        if (pipe) {
+          const uint64_t un = u + ustep;
+          if (un < nunits) {
+            bnext = pdep64(un, omask);
+            V* nb = cur ? buf0 : buf1;
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) {
+              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+              cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                         reinterpret_cast<const V*>(A.state) + (bnext | schunk[ch] | woff));
+            }
+          }
+          cp_async_commit();
+        }
 
         // ---- gate stages
         if (any_gate) Stages::template run<T, M>(A, sp, sgk, smat, tb);
@@ -779,10 +783,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
               __stcg(reinterpret_cast<double2*>(A.state) + gi, tb[p]);
           }
         }
-        __syncthreads();
         if (pipe) {
+          // no barrier: the next iteration's barrier orders these reads before
+          // that buffer is refilled
           bcur = bnext;
           cur ^= 1;
+        } else {
+          __syncthreads();
         }
       }
     }
