@@ -58,8 +58,17 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     o << "    for (int grp = tid; grp < " << (1 << GB) << "; grp += " << svp::PASS_THREADS << ") {\n"
       << "      uint32_t b = 0;\n";
     for (int k = 0; k < GB; ++k) o << "      if (grp & " << (1 << k) << ") b ^= " << st.E[k] << "u;\n";
+    // complex64 with register bit 0 on tile bit 0: amplitude pairs share a
+    // 16-byte granule (the swizzle never touches bit 0), one access per pair
+    const bool pairs = P.dtype == SV_C64 && st.R[0] == 1;
     o << "      V a[16];\n";
-    for (int j = 0; j < 16; ++j) o << "      a[" << j << "] = tb[b ^ " << off[j] << "u];\n";
+    if (pairs) {
+      for (int j = 0; j < 16; j += 2)
+        o << "      { const float4 q = *reinterpret_cast<const float4*>(tb + (b ^ " << off[j] << "u)); a[" << j
+          << "] = make_float2(q.x, q.y); a[" << j + 1 << "] = make_float2(q.z, q.w); }\n";
+    } else {
+      for (int j = 0; j < 16; ++j) o << "      a[" << j << "] = tb[b ^ " << off[j] << "u];\n";
+    }
     for (uint32_t g = st.g0; g < uint32_t(st.g0) + st.ng; ++g) {
       const svp::DGate& gt = P.gates[d.g0 + g];
       const char* fn = op_template(gt.op);
@@ -72,7 +81,13 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (gt.flag >= 0) o << "      if (sgk[" << g << "] & 0x100u) " << call.str() << ";\n";
       else o << "      " << call.str() << ";\n";
     }
-    for (int j = 0; j < 16; ++j) o << "      tb[b ^ " << off[j] << "u] = a[" << j << "];\n";
+    if (pairs) {
+      for (int j = 0; j < 16; j += 2)
+        o << "      *reinterpret_cast<float4*>(tb + (b ^ " << off[j] << "u)) = make_float4(a[" << j << "].x, a[" << j
+          << "].y, a[" << j + 1 << "].x, a[" << j + 1 << "].y);\n";
+    } else {
+      for (int j = 0; j < 16; ++j) o << "      tb[b ^ " << off[j] << "u] = a[" << j << "];\n";
+    }
     o << "    }\n    __syncthreads();\n";
   }
   o << "  }\n};\n\n";

@@ -340,11 +340,15 @@ struct Builder {
       rem.swap(left);
       DStage st{};
       st.g0 = uint16_t(P.gates.size() - ps.g0);
-      // register bits: the stage's qubits, padded with the highest other local bits
+      // register bits: the stage's qubits (ascending), padded with local bit 0
+      // when it is free (complex64: amplitude pairs then share a 16-byte
+      // granule, so specialised kernels move them with one access), then with
+      // the highest other local bits
       std::vector<int> reg;
+      if (B == 1 && !(S & 1u) && popc(S) < reg_bits) reg.push_back(0);
       for (int j = 0; j < m; ++j)
         if ((S >> j) & 1) reg.push_back(j);
-      for (int j = m - 1; j >= 0 && int(reg.size()) < reg_bits; --j)
+      for (int j = m - 1; j >= 1 && int(reg.size()) < reg_bits; --j)
         if (!((S >> j) & 1)) reg.push_back(j);
       int rpos[MAX_TILE_BITS];
       for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
