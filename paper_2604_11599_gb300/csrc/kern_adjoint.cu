@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
       const uint32_t c0 = uint32_t(tid) >> vl;
       const uint32_t q0 = swz<T>((c0 << L) | woff);
 
-      for (uint64_t u = 0; u < ntiles; ++u) {
-        const uint64_t base = pdep64(u, omask);
+      const uint64_t s1 = omask & (~omask + 1);  // deposit of 1: the lowest outer bit
+      uint64_t base = 0;
+      for (uint64_t u = 0; u < ntiles; ++u, base = spread_add(base, s1, omask)) {
 #pragma unroll
         for (int k = 0; k < NVT; ++k) {
           const uint32_t ch = c0 + (uint32_t(k) << (VB - L));

@@ -369,6 +369,13 @@ static __device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
   return out;
 }
 
+// x + y in the spread domain of mask (x and y hold bits of mask only): the
+// gaps are filled with ones so that carries cross them.  For x = pdep(a, mask)
+// and y = pdep(b, mask) the result is pdep(a + b, mask), modulo 2^popc(mask).
+static __device__ __forceinline__ uint64_t spread_add(uint64_t x, uint64_t y, uint64_t mask) {
+  return ((x | ~mask) + y) & mask;
+}
+
 static __device__ __forceinline__ uint64_t pext64(uint64_t v, uint64_t mask) {
   uint64_t out = 0, bb = 1;
   for (; mask; bb <<= 1) {
@@ -545,7 +552,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
   constexpr int GB = M - REG_BITS;  // group-index bits of a stage
   constexpr int NGRP = 1 << GB;     // 16-amplitude groups per tile
-  constexpr bool DB = (size_t(2) << M) * sizeof(V) <= size_t(128) * 1024;  // double-buffered tiles fit
+  // tile buffers of the copy pipeline (NBUF - 1 tiles in flight): two when they
+  // fit in 128 KiB, else one.  A third buffer measured no faster.
+  constexpr size_t TILE_BYTES = (size_t(1) << M) * sizeof(V);
+  constexpr int NBUF = 2 * TILE_BYTES <= size_t(128) * 1024 ? 2 : 1;
+  constexpr bool DB = NBUF > 1;
   V* tile = reinterpret_cast<V*>(smem_tiles);
   DPass& sp = sh.sp;
   uint32_t* sgk = sh.sgk;
@@ -627,20 +638,28 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     // flight while the current one is processed (two shared-memory buffers).
     // Otherwise the tile is loaded synchronously with the projector applied.
     const bool pipe = DB && ident;
-    V* const buf0 = tile;
-    V* const buf1 = DB ? tile + (1 << M) : tile;
     int cur = 0;
-    uint64_t bcur = 0;
-    if (pipe && ustart < nunits) {
-      bcur = pdep64(ustart, omask);
+    // Tile bases advance by masked addition instead of a bit-by-bit deposit per tile.
+    const uint64_t sstep = pdep64(ustep, omask);
+    const uint64_t sahead = pdep64(uint64_t(NBUF - 1) * ustep, omask);
+    uint64_t bcur = pdep64(ustart, omask);
+    auto buffer = [&](int k) { return tile + size_t(k) * (size_t(1) << M); };
+    if (pipe) {  // prologue: the first NBUF - 1 tiles of this CTA, one commit group each
+      for (int k = 0; k < NBUF - 1; ++k) {
+        const uint64_t uk = ustart + uint64_t(k) * ustep;
+        if (uk < nunits) {
+          const uint64_t bk = pdep64(uk, omask);
+          V* dst = buffer(k);
 #pragma unroll
-      for (int k = 0; k < NVT; ++k) {
-        const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
-        cp_async16(buf0 + (q0 ^ swz<T>(uint32_t(k) << VB)),
-                   reinterpret_cast<const V*>(A.state) + (bcur | schunk[ch] | woff));
+          for (int v = 0; v < NVT; ++v) {
+            const uint32_t ch = c0 + (uint32_t(v) << (VB - L));
+            cp_async16(dst + (q0 ^ swz<T>(uint32_t(v) << VB)),
+                       reinterpret_cast<const V*>(A.state) + (bk | schunk[ch] | woff));
+          }
+        }
+        cp_async_commit();
       }
     }
-    if (pipe) cp_async_commit();
 
     for (uint64_t u = ustart; u < nunits; u += ustep) {
       uint64_t tl[2] = {u, 0};
@@ -658,14 +677,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       for (int k2 = 0; k2 < cnt; ++k2) {
         V* tb;
         uint64_t base;
-        uint64_t bnext = 0;
         if (pipe) {
           base = bcur;
-          tb = cur ? buf1 : buf0;
-          cp_async_wait<0>();  // this tile's copies, issued one iteration earlier
+          tb = buffer(cur);
+          cp_async_wait<NBUF - 2>();  // this tile's group; the NBUF - 2 newer ones may still fly
         } else {
           tb = tile;
-          base = pdep64(tl[k2], omask);
+          base = pair ? pdep64(tl[k2], omask) : bcur;
           const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
           // a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv, else 0
 #pragma unroll
@@ -718,16 +736,16 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         // All threads: this tile has landed, and every thread is done with the
         // previous tile, so the other buffer can be refilled.
         __syncthreads();
-        if (pipe) {
-          const uint64_t un = u + ustep;
+        if (pipe) {  // refill the buffer processed one iteration ago with the tile NBUF - 1 ahead
+          const uint64_t un = u + uint64_t(NBUF - 1) * ustep;
           if (un < nunits) {
-            bnext = pdep64(un, omask);
-            V* nb = cur ? buf0 : buf1;
+            const uint64_t bn = spread_add(bcur, sahead, omask);
+            V* nb = buffer((cur + NBUF - 1) % NBUF);
 #pragma unroll
             for (int k = 0; k < NVT; ++k) {
               const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
               cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
-                         reinterpret_cast<const V*>(A.state) + (bnext | schunk[ch] | woff));
+                         reinterpret_cast<const V*>(A.state) + (bn | schunk[ch] | woff));
             }
           }
           cp_async_commit();
@@ -785,13 +803,13 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         }
         if (pipe) {
           // no barrier: the next iteration's barrier orders these reads before
-          // that buffer is refilled
-          bcur = bnext;
-          cur ^= 1;
+          // this buffer is refilled
+          cur = (cur + 1) % NBUF;
         } else {
           __syncthreads();
         }
       }
+      bcur = spread_add(bcur, sstep, omask);
     }
     if (pipe) cp_async_wait<0>();
   }
