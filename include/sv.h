@@ -124,6 +124,10 @@ typedef struct sv_program_stats {
   uint64_t plan_bytes;    /* bytes of plan data copied to the device      */
   int32_t specialised;    /* 1: passes run as kernels compiled for this program (sv_set_jit) */
   double compile_seconds; /* time spent compiling them                    */
+  uint64_t block_barriers; /* per tile, summed over passes: block-wide barriers after the tile
+                              copy and after each stage                      */
+  uint64_t warp_barriers;  /* the same steps where a warp barrier suffices (every warp keeps
+                              to its own amplitudes across the step; checked at lowering)  */
 } sv_program_stats;
 
 #ifndef __CUDACC_RTC__ /* device code compiled at run time needs the types above only */

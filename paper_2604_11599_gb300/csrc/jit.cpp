@@ -88,7 +88,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     } else {
       for (int j = 0; j < 16; ++j) o << "      tb[b ^ " << off[j] << "u] = a[" << j << "];\n";
     }
-    o << "    }\n    __syncthreads();\n";
+    o << "    }\n    " << (st.bar ? "__syncthreads();" : "__syncwarp();") << "\n";
   }
   o << "  }\n};\n\n";
 }

@@ -541,7 +541,8 @@ struct GenericStages {
 #pragma unroll
         for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
       }
-      __syncthreads();
+      if (st.bar) __syncthreads();
+      else __syncwarp();
     }
   }
 };
@@ -733,9 +734,12 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             }
           }
         }
-        // All threads: this tile has landed, and every thread is done with the
-        // previous tile, so the other buffer can be refilled.
-        __syncthreads();
+        // This tile has landed, and every thread is done with the previous
+        // tile, so its buffer can be refilled.  When the first stage keeps the
+        // copies' warp bits, each warp reads only what its own lanes copied and
+        // refills only what its own lanes stored: a warp barrier suffices.
+        if (pipe && any_gate && !sp.bar_in) __syncwarp();
+        else __syncthreads();
         if (pipe) {  // refill the buffer processed one iteration ago with the tile NBUF - 1 ahead
           const uint64_t un = u + uint64_t(NBUF - 1) * ustep;
           if (un < nunits) {

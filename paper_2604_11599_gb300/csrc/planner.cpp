@@ -321,6 +321,8 @@ struct Builder {
     uint32_t dots = 0;
 
     // stages: greedy, four register bits, dependency order preserved
+    std::vector<uint32_t> stS;
+    std::vector<std::vector<int>> stG;
     std::vector<int> rem(chosen);
     while (!rem.empty()) {
       uint32_t S = 0, blocked = 0;
@@ -338,30 +340,129 @@ struct Builder {
         sg.push_back(idx);
       }
       rem.swap(left);
-      DStage st{};
-      st.g0 = uint16_t(P.gates.size() - ps.g0);
-      // register bits: the stage's qubits (ascending), padded with local bit 0
-      // when it is free (complex64: amplitude pairs then share a 16-byte
-      // granule, so specialised kernels move them with one access), then with
-      // the highest other local bits
+      stS.push_back(S);
+      stG.push_back(sg);
+    }
+
+    // Warp ownership.  With 2^m >= 16 * PASS_THREADS every thread holds one
+    // group per 256, so the warp index (thread bits 5..7) is three group bits:
+    // a warp touches only the amplitudes whose tile bits there equal its index.
+    // The tile copies map thread bit t to tile bit t + B, so their warp bits are
+    // B+5, B+6, B+7.  Two consecutive steps (copy, stages, copy back) with the
+    // same ordered warp bits need only a warp barrier between them.
+    const bool warp_local = !adjoint && m >= 12 && PASS_THREADS == 256;
+    const int W0[3] = {B + 5, B + 6, B + 7};
+    const uint32_t w0m = (1u << W0[0]) | (1u << W0[1]) | (1u << W0[2]);
+    int Wcur[3] = {W0[0], W0[1], W0[2]};
+    const int K = int(stS.size());
+    std::vector<uint8_t> bar_before(size_t(K) + 1, 1);
+    for (int si = 0; si < K; ++si) {
+      const uint32_t S = stS[size_t(si)];
+      const uint32_t wcm = (1u << Wcur[0]) | (1u << Wcur[1]) | (1u << Wcur[2]);
+      // Lanes are conflict-free in shared memory when their bits reach every
+      // class of the swizzle's 3-bit fold (complex64 8-byte accesses also
+      // need local bit 0; with bit 0 a register bit, pairs move as 16 bytes).
+      auto lanes_ok = [&](uint32_t fm, bool pairs) {
+        bool cls[3] = {false, false, false};
+        for (int j = 0; j < m; ++j)
+          if ((fm >> j) & 1) {
+            if (B == 0) cls[j % 3] = true;
+            else if (j >= 1) cls[(j - 1) % 3] = true;
+          }
+        return cls[0] && cls[1] && cls[2] && (B == 0 || pairs || (fm & 1u));
+      };
+      const uint32_t all = (m >= 32) ? ~0u : ((1u << m) - 1u);
+      // register bits: the stage's qubits, padded with local bit 0 when it is
+      // free (complex64: amplitude pairs then share a 16-byte granule, so
+      // specialised kernels move them with one access), then with the highest
+      // other local bits that keep the lanes conflict-free and, where possible,
+      // stay off the warp bits; ascending, so local bit 0 is register bit 0
       std::vector<int> reg;
-      if (B == 1 && !(S & 1u) && popc(S) < reg_bits) reg.push_back(0);
+      uint32_t rm = S;
       for (int j = 0; j < m; ++j)
         if ((S >> j) & 1) reg.push_back(j);
-      for (int j = m - 1; j >= 1 && int(reg.size()) < reg_bits; --j)
-        if (!((S >> j) & 1)) reg.push_back(j);
+      if (B == 1 && !(S & 1u) && popc(S) < reg_bits) {
+        reg.push_back(0);
+        rm |= 1u;
+      }
+      for (int pass = 0; pass < 3; ++pass)
+        for (int j = m - 1; j >= 1 && int(reg.size()) < reg_bits; --j) {
+          if ((rm >> j) & 1) continue;
+          const uint32_t r2 = rm | (1u << j);
+          if (pass < 2 && !lanes_ok(all & ~r2 & ~(warp_local ? wcm : 0u), B == 1 && (r2 & 1u))) continue;
+          if (pass == 0 && warp_local && (((wcm | w0m) >> j) & 1)) continue;
+          reg.push_back(j);
+          rm = r2;
+        }
+      std::sort(reg.begin(), reg.end());
+      const bool pairs = B == 1 && (rm & 1u);
+      const uint32_t fm = all & ~rm;
+      const bool can_be_clean = lanes_ok(fm, pairs);
+
+      int W[3] = {-1, -1, -1};
+      if (warp_local) {
+        if (!(rm & wcm) && (!can_be_clean || lanes_ok(fm & ~wcm, pairs))) {
+          for (int i = 0; i < 3; ++i) W[i] = Wcur[i];
+          bar_before[size_t(si)] = 0;
+        } else {
+          // the triple that stays out of the following stages longest and keeps
+          // the lanes conflict-free; ties go to the copies' warp bits, so the
+          // run can end warp-locally
+          int run[MAX_TILE_BITS] = {};
+          for (int j = 0; j < m; ++j)
+            while (si + 1 + run[j] < K && !((stS[size_t(si + 1 + run[j])] >> j) & 1)) ++run[j];
+          int best = -1;
+          uint32_t bestm = 0;
+          for (int a = 0; a < m; ++a)
+            for (int b = a + 1; b < m; ++b)
+              for (int c = b + 1; c < m; ++c) {
+                const uint32_t tm = (1u << a) | (1u << b) | (1u << c);
+                if ((tm & rm) || (B == 1 && (tm & 1u))) continue;
+                if (can_be_clean && !lanes_ok(fm & ~tm, pairs)) continue;
+                const int r = std::min(run[a], std::min(run[b], run[c]));
+                const int score = 8 * r + (si + 1 + r == K && tm == w0m ? 4 : 0) + popc(tm & w0m);
+                if (score > best) {
+                  best = score;
+                  bestm = tm;
+                }
+              }
+          if (best < 0)  // cannot happen for m >= 12 (8 free bits); keep any three
+            for (int j = m - 1; j >= 1 && popc(bestm) < 3; --j)
+              if (!((rm >> j) & 1)) bestm |= 1u << j;
+          if (bestm == w0m) {
+            for (int i = 0; i < 3; ++i) W[i] = W0[i];
+          } else {
+            int i = 0;
+            for (int j = 0; j < m; ++j)
+              if ((bestm >> j) & 1) W[i++] = j;
+          }
+        }
+        for (int i = 0; i < 3; ++i) Wcur[i] = W[i];
+      }
+
+      DStage st{};
+      st.g0 = uint16_t(P.gates.size() - ps.g0);
       int rpos[MAX_TILE_BITS];
       for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
       for (int r = 0; r < reg_bits; ++r) {
-        st.R[r] = uint16_t(tile_swizzle(1u << reg[r], B));
-        rpos[reg[r]] = r;
+        st.R[r] = uint16_t(tile_swizzle(1u << reg[size_t(r)], B));
+        rpos[reg[size_t(r)]] = r;
       }
       std::vector<int> freeb;
       for (int j = 0; j < m; ++j)
-        if (rpos[j] < 0) freeb.push_back(j);
+        if (rpos[j] < 0 && !(warp_local && (j == W[0] || j == W[1] || j == W[2]))) freeb.push_back(j);
       uint8_t thr[MAX_TILE_BITS] = {};
       order_thread_bits(freeb, B, thr);
-      for (int k = 0; k < m - reg_bits; ++k) st.E[k] = uint16_t(tile_swizzle(1u << thr[k], B));
+      std::vector<int> ebits;
+      if (warp_local) {
+        for (int k = 0; k < 5; ++k) ebits.push_back(thr[k]);
+        for (int i = 0; i < 3; ++i) ebits.push_back(W[i]);
+        for (size_t k = 5; k < freeb.size(); ++k) ebits.push_back(thr[k]);
+      } else {
+        for (size_t k = 0; k < freeb.size(); ++k) ebits.push_back(thr[k]);
+      }
+      for (int k = 0; k < m - reg_bits; ++k) st.E[k] = uint16_t(tile_swizzle(1u << ebits[size_t(k)], B));
+      const std::vector<int>& sg = stG[size_t(si)];
       for (int idx : sg) {
         const Item& it = items[idx];
         // backward plans: derivative accumulations before the gate's U^dagger
@@ -427,8 +528,16 @@ struct Builder {
         P.gates.push_back(g);
       }
       st.ng = uint16_t(P.gates.size() - ps.g0 - st.g0);  // gate records, derivative items included
+      st.bar = 1;
       P.stages.push_back(st);
     }
+    // barrier flags: a block barrier wherever the warp bits change; after the
+    // last stage unless it ends on the copies' warp bits without a group table
+    const bool tail_local = warp_local && K > 0 && Wcur[0] == W0[0] && Wcur[1] == W0[1] && Wcur[2] == W0[2] &&
+                            !(seg && seg->has_group);
+    bar_before[size_t(K)] = tail_local ? 0 : 1;
+    for (int si = 0; si < K; ++si) P.stages[ps.s0 + size_t(si)].bar = bar_before[size_t(si) + 1];
+    ps.bar_in = K > 0 ? bar_before[0] : 1;
     ps.ng = uint32_t(P.gates.size() - ps.g0);
     ps.ns = uint32_t(P.stages.size() - ps.s0);
     ps.nmat = mat;
@@ -570,6 +679,74 @@ struct Builder {
 
 }  // namespace
 
+// Checks the barrier flags of every pass against the thread -> amplitude maps
+// of the kernels (the tile copy: 16-byte vector k of thread t at chunk
+// (t >> vl) + (k << (VB - L)), offset (t & (2^vl - 1)) << B; a stage: group g
+// of thread g mod 256 at XOR of E over the bits of g, its 16 amplitudes at
+// XOR of R over the register index).  Every stage must touch each amplitude
+// once, and wherever only a warp barrier separates two steps (copy -> first
+// stage, stage -> stage, last stage -> copy back) both must give every
+// amplitude to the same warp.  Returns the number of violations.
+int check_barriers(const Plan& P, uint64_t* warp_syncs, uint64_t* block_syncs) {
+  const int B = P.dtype == SV_C64 ? 1 : 0;
+  int bad = 0;
+  *warp_syncs = *block_syncs = 0;
+  for (const DPass& ps : P.passes) {
+    if (ps.ns == 0) continue;
+    const int m = ps.m, L = ps.L, T = 1 << m;
+    std::vector<int8_t> copy_own(size_t(T), -1);
+    const int VB = B ? 9 : 8, NVT = 1 << (m - VB), vl = B ? L - 1 : L;
+    for (int t = 0; t < PASS_THREADS; ++t) {
+      const uint32_t wv = uint32_t(t) & ((1u << vl) - 1u);
+      const uint32_t woff = B ? (wv << 1) : wv;
+      for (int k = 0; k < NVT; ++k) {
+        const uint32_t ch = (uint32_t(t) >> vl) + (uint32_t(k) << (VB - L));
+        const uint32_t a = tile_swizzle((ch << L) | woff, B);
+        for (int e = 0; e <= B; ++e) copy_own[a ^ uint32_t(e)] = int8_t(t >> 5);
+      }
+    }
+    std::vector<std::vector<int8_t>> own(ps.ns, std::vector<int8_t>(size_t(T), -1));
+    for (uint32_t si = 0; si < ps.ns; ++si) {
+      const DStage& st = P.stages[ps.s0 + si];
+      std::vector<int> cnt(size_t(T), 0);
+      for (int g = 0; g < (T >> REG_BITS); ++g) {
+        uint32_t b = 0;
+        for (int k = 0; k < m - REG_BITS; ++k)
+          if ((g >> k) & 1) b ^= st.E[k];
+        for (int j = 0; j < (1 << REG_BITS); ++j) {
+          uint32_t a = b;
+          for (int r = 0; r < REG_BITS; ++r)
+            if ((j >> r) & 1) a ^= st.R[r];
+          if (a >= uint32_t(T)) {
+            ++bad;
+            continue;
+          }
+          ++cnt[a];
+          own[si][a] = int8_t((g % PASS_THREADS) >> 5);
+        }
+      }
+      for (int a = 0; a < T; ++a) bad += cnt[size_t(a)] != 1;
+    }
+    auto same = [&](const std::vector<int8_t>& x, const std::vector<int8_t>& y) { return x == y; };
+    if (ps.bar_in) ++*block_syncs;
+    else {
+      ++*warp_syncs;
+      bad += !same(copy_own, own[0]);
+    }
+    for (uint32_t si = 0; si < ps.ns; ++si) {
+      const DStage& st = P.stages[ps.s0 + si];
+      if (st.bar) {
+        ++*block_syncs;
+        continue;
+      }
+      ++*warp_syncs;
+      if (si + 1 < ps.ns) bad += !same(own[si], own[si + 1]);
+      else bad += !same(own[si], copy_own) || ps.gk != 0;
+    }
+  }
+  return bad;
+}
+
 sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const double* dense_pool, size_t dense_len,
                      const Tuning& tune, Plan& P, std::string& err) {
   P = Plan{};
@@ -683,6 +860,11 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   P.stats.plan_bytes = P.passes.size() * sizeof(DPass) + P.gates.size() * sizeof(DGate) +
                        P.stages.size() * sizeof(DStage) + (P.scalars.size() + P.init_items.size()) * sizeof(DScalar) +
                        P.jobs.size() * sizeof(DJob) + P.consts.size() * sizeof(double);
+  const int bad = check_barriers(P, &P.stats.warp_barriers, &P.stats.block_barriers);
+  if (bad) {
+    err = "internal: " + std::to_string(bad) + " stage barrier flags fail the ownership check";
+    return SV_ERR_UNSUPPORTED;
+  }
   return SV_OK;
 }
 

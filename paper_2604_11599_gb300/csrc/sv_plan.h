@@ -94,7 +94,8 @@ struct DGate {
 struct DStage {
   uint16_t g0, ng;                       // gate range (pass-relative)
   uint16_t R[REG_BITS];
-  uint16_t E[MAX_TILE_BITS - REG_BITS];
+  uint16_t E[MAX_TILE_BITS - REG_BITS];  // E[5..7] select the warp (tiles of >= 12 bits)
+  uint16_t bar;                          // 1: block barrier after the stage, 0: warp barrier suffices
 };
 
 // Shared-memory layout of a tile, in 16-byte granules (one complex128 or two
@@ -137,7 +138,8 @@ struct DPass {
   uint8_t kin;            // how many of the group bits are tile bits (table bits 0..kin-1)
   uint8_t group_always;   // 1: the table is needed whatever the flags say
   uint8_t flush;          // 1: final pass that only applies a pending projector
-  uint8_t pad[2];
+  uint8_t bar_in;         // 1: block barrier between the tile copy and the first stage
+  uint8_t pad;
   uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
   uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
   uint16_t red_R[REG_BITS];       // reduction stage: register-bit addresses

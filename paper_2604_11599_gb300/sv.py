@@ -40,7 +40,8 @@ class ProgramStats(C.Structure):
     _fields_ = [("records", C.c_uint64), ("unrolled_ops", C.c_uint64), ("gates", C.c_uint64),
                 ("draws", C.c_uint64), ("passes", C.c_uint64), ("stages", C.c_uint64),
                 ("flags", C.c_uint64), ("tile_bits", C.c_int32), ("low_bits", C.c_int32),
-                ("plan_bytes", C.c_uint64), ("specialised", C.c_int32), ("compile_seconds", C.c_double)]
+                ("plan_bytes", C.c_uint64), ("specialised", C.c_int32), ("compile_seconds", C.c_double),
+                ("block_barriers", C.c_uint64), ("warp_barriers", C.c_uint64)]
 
 
 _lib = None

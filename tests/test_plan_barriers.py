@@ -1,0 +1,37 @@
+"""Host-only checks of the stage barrier plan: lowering verifies, for every
+pass, that wherever a stage hands over to the next step with only a warp
+barrier, both steps give each amplitude of the tile to the same warp (and that
+every stage touches each amplitude exactly once); a failure raises."""
+import pytest
+
+from paper_2604_11599_gb300 import sv
+from paper_2604_11599_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("tile", [0, 10, 11, 12, 13, 14])
+def test_barrier_plan_verifies_on_random_programs(dtype, tile):
+    if dtype == "c128" and tile == 14:
+        pytest.skip("complex128 tiles stop at 13 bits")
+    warp = 0
+    for seed in range(6):
+        for n in (12, 15, 19, 24):
+            progs = [W.random_static(seed * 31 + n, n, 120, dense_k=1 + seed % 4, params=3),
+                     W.random_dynamic(seed * 17 + n, n, n_ops=90, dense_k=2),
+                     W.layered(seed, n, layers=8)]
+            for c in progs:
+                s = sv.plan_info(c.ops, n, dtype, pool=c.pool, tile_bits=tile)
+                assert s["block_barriers"] + s["warp_barriers"] >= s["stages"]
+                if s["tile_bits"] < 12:
+                    assert s["warp_barriers"] == 0
+                warp += s["warp_barriers"]
+    if tile in (0, 12, 13, 14):
+        assert warp > 0
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_layered_passes_use_warp_barriers(dtype):
+    n = 30
+    s = sv.plan_info(W.layered(5, n, layers=20).ops, n, dtype)
+    total = s["block_barriers"] + s["warp_barriers"]
+    assert s["warp_barriers"] >= 0.3 * total
