@@ -338,6 +338,20 @@ sv_status sv_set_cache(sv_state* h, int enable);
 sv_status sv_set_jit(sv_state* h, int enable);
 
 /*
+ * Dense four-qubit unitaries (DENSE records on 4 qubits) on the tensor cores
+ * (on by default).  Applies to complex64 states swept in 2^12-amplitude tiles
+ * (the default), generic and specialised kernels: each such gate becomes a
+ * 2^(n-4) x 32 by 32 x 32 real product (the 32 x 32 real form of the 16 x 16
+ * complex unitary) on kind::tf32 MMAs, each operand split into a TF32 high
+ * and low part with three products accumulated in FP32 (FP32-level accuracy).
+ * Off, or in other configurations, the gate runs on the FP32 / FP64 pipes.
+ * The paper gives no kernel for dense gates; this is a GB300 design choice.
+ * SV_ERR_ARG for a NULL handle.  A tensor-core completion wait that runs out
+ * makes the run report SV_ERR_TIMEOUT.
+ */
+sv_status sv_set_dense_tc(sv_state* h, int enable);
+
+/*
  * Host-only check of the specialiser (no device touched): lowers the op list
  * and compiles its specialised module to a cubin.  On failure the first
  * log_len - 1 bytes of the compiler log are copied to log (nullable).

@@ -20,9 +20,10 @@ SOURCES = ["kern_pass.cu", "kern_measure.cu", "kern_batch.cu", "kern_adjoint.cu"
            "expval_static.cu", "jit.cpp"]
 # headers compiled again at run time by the pass specialiser (jit.cpp); embedded as strings
 JIT_HEADERS = [("pass_body.cuh", "csrc/pass_body.cuh"), ("dev_common.cuh", "csrc/dev_common.cuh"),
+               ("dev_tc.cuh", "csrc/dev_tc.cuh"),
                ("kernels.h", "csrc/kernels.h"), ("sv_plan.h", "csrc/sv_plan.h"),
                ("../../include/sv.h", "../include/sv.h")]
-HEADERS = ["sv_plan.h", "kernels.h", "planner.h", "dev_common.cuh", "pass_body.cuh", "jit.h"]
+HEADERS = ["sv_plan.h", "kernels.h", "planner.h", "dev_common.cuh", "dev_tc.cuh", "pass_body.cuh", "jit.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,7 +46,8 @@ def _embed_jit_headers() -> str:
     """Writes _build/jit_headers.inc: the device headers as string literals."""
     out = os.path.join(BUILD, "jit_headers.inc")
     srcs = [os.path.normpath(os.path.join(HERE, rel)) for _, rel in JIT_HEADERS]
-    if os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(p) for p in srcs):
+    # the header list lives in this file, so it counts as a source too
+    if os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(p) for p in srcs + [__file__]):
         return out
     parts = ["// generated by build.py from the device headers", "static const char* const kJitHeaderNames[] = {"]
     parts += [f'    "{name}",' for name, _ in JIT_HEADERS]

@@ -30,7 +30,7 @@ const char* op_template(int op) {
     case svp::OP_CD: return "g_cd";
     case svp::OP_SWAP: return "g_swap";
     case svp::OP_U4: return "g_u4";
-    case svp::OP_D16: return "g_d16";
+    case svp::OP_D16: return "d16_apply";
     default: return nullptr;
   }
 }
@@ -47,7 +47,8 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
   o << "struct JS" << pi << " {\n"
     << "  template <typename T, int M>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
-    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
+    << "                                             TcCtx& tc) {\n"
     << "    using V = typename CxT<T>::V;\n"
     << "    const int tid = threadIdx.x;\n";
   for (uint32_t si = 0; si < d.ns; ++si) {
@@ -75,7 +76,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (!fn) continue;
       std::ostringstream call;
       call << fn;
-      if (gt.op == svp::OP_D16) call << "(a, smat + " << gt.mat << ")";
+      if (gt.op == svp::OP_D16) call << "<T, M>(a, smat + " << gt.mat << ", tb, tc)";
       else if (two_qubit(gt.op)) call << "<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ")";
       else call << "<" << int(gt.p0) << ">(a, smat + " << gt.mat << ")";
       if (gt.flag >= 0) o << "      if (sgk[" << g << "] & 0x100u) " << call.str() << ";\n";
@@ -153,10 +154,11 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   o << "struct JitStages {\n"
     << "  template <typename T, int M>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
-    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
+    << "                                             TcCtx& tc) {\n"
     << "    switch (A.pass) {\n";
   for (size_t pi = p0; pi < p1; ++pi)
-    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M>(A, sp, sgk, smat, tb); break;\n";
+    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M>(A, sp, sgk, smat, tb, tc); break;\n";
   o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
   const char* T = c64 ? "float" : "double";
   o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1)

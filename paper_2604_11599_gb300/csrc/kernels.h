@@ -23,6 +23,7 @@ struct PassArgs {
   double* partials;  // [grid][16]
   int n;             // simulated qubits
   int pass;          // pass index (specialised kernels select their stage program by it)
+  int dense_tc;      // 1: dense four-qubit gates of complex64 2^12-amplitude tiles on the tensor cores
 };
 
 struct PrepArgs {

@@ -18,6 +18,7 @@
 // (Sec. III-C) -- all on the device.
 #pragma once
 #include "dev_common.cuh"
+#include "dev_tc.cuh"
 #include "kernels.h"
 
 namespace svk {
@@ -165,6 +166,92 @@ __device__ __forceinline__ void g_d16(V* a, const V* m) {
   }
 #pragma unroll
   for (int r = 0; r < 16; ++r) a[r] = w[r];
+}
+
+// Dense 16 x 16 unitary on the register qubits of every group of a
+// 2^12-amplitude complex64 tile, on the tensor cores (dev_tc.cuh).  Collective:
+// all 256 threads call it together, each holding its group (= its thread
+// index) in a[].  Once every thread has read its group the tile buffer tb is
+// free, so it holds the A operand, 128 rows at a time: the TF32 high parts in
+// its first 16 KiB, the low parts in the next 16 KiB.  Rows 0..127 (warps 0-3)
+// go to accumulator columns 0..31, rows 128..255 (warps 4-7) to 32..63; warp w
+// reads its rows back from tensor-memory lanes 32 (w mod 4) ... + 31.
+template <typename V>
+__device__ __forceinline__ void d16_tc(V* a, const V* m, V* tb, TcCtx& tc) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  TcShared& s = *tc.s;
+  unsigned char* stage = reinterpret_cast<unsigned char*>(tb);
+  unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[0]);
+  unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[1]);
+  tc_fence_before();
+  __syncthreads();  // every group read from the tile; previous results read from tensor memory
+  {  // Bt entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]
+    const int r = tid >> 4, c = tid & 15;
+    const V u = m[r * 16 + c];
+    const float e[4] = {u.x, -u.y, u.y, u.x};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t off = cm_off(uint32_t(2 * r + (q >> 1)), uint32_t(2 * c + (q & 1)));
+      const float hi = tf32_hi(e[q]);
+      *reinterpret_cast<float*>(bt0 + off) = hi;
+      *reinterpret_cast<float*>(bt1 + off) = e[q] - hi;
+    }
+  }
+  constexpr uint32_t IDESC = idesc_tf32(128, 32);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    if ((tid >> 7) == h) {
+      const uint32_t row = uint32_t(tid & 127);
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {  // K elements 4kc..4kc+3: amplitudes 2kc, 2kc+1 (re, im)
+        const V x0 = a[2 * kc], x1 = a[2 * kc + 1];
+        const float4 hi = make_float4(tf32_hi(x0.x), tf32_hi(x0.y), tf32_hi(x1.x), tf32_hi(x1.y));
+        const float4 lo = make_float4(x0.x - hi.x, x0.y - hi.y, x1.x - hi.z, x1.y - hi.w);
+        const uint32_t off = cm_off(row, uint32_t(4 * kc));
+        *reinterpret_cast<float4*>(stage + off) = hi;
+        *reinterpret_cast<float4*>(stage + 16384 + off) = lo;
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && tc.ok) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(stage), b0 = smem_u32(bt0), b1 = smem_u32(bt1);
+      const uint32_t d = tc.tmem + uint32_t(32 * h);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // K = 8 per MMA; three products per k-step
+        const uint32_t ko = uint32_t(k) * 256u;
+        mma_tf32(d, smem_desc(a0 + ko, 128, 1024), smem_desc(b0 + ko, 128, 1024), IDESC, k > 0 ? 1u : 0u);
+        mma_tf32(d, smem_desc(a0 + ko, 128, 1024), smem_desc(b1 + ko, 128, 1024), IDESC, 1u);
+        mma_tf32(d, smem_desc(a0 + 16384 + ko, 128, 1024), smem_desc(b0 + ko, 128, 1024), IDESC, 1u);
+      }
+      mma_commit(&s.bar);
+    }
+    // after a wait ran out, no further MMAs or waits (the barriers stay): the
+    // pass ends quickly and the run reports SV_ERR_TIMEOUT
+    if (tc.ok && !mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS)) tc.ok = false;
+    ++tc.phase;
+    tc_fence_after();
+  }
+  uint32_t r[32];
+  tmem_ld32(tc.tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(32 * (warp >> 2)), r);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+}
+
+// A dense four-qubit unitary: on the tensor cores where the pass enabled them
+// (complex64, 2^12-amplitude tiles), else on the FP32 / FP64 pipes.
+template <typename T, int M, typename V>
+__device__ __forceinline__ void d16_apply(V* a, const V* m, V* tb, TcCtx& tc) {
+  if constexpr (sizeof(T) == 4 && M == 12) {
+    if (tc.on) {
+      d16_tc(a, m, tb, tc);
+      return;
+    }
+  }
+  g_d16(a, m);
 }
 
 #define SVK_K1(OP, FN)                          \
@@ -508,6 +595,7 @@ struct PassShared {
   double wsum[PASS_THREADS / 32][16];
   double tile16[16];
   int s_last;
+  TcShared tc;                   // tensor-core path of dense gates
 };
 
 // One pass over the state.  GRID mode (CTA = false): the tiles are shared by
@@ -520,7 +608,7 @@ struct PassShared {
 struct GenericStages {
   template <typename T, int M>
   static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,
-                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb) {
+                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb, TcCtx& tc) {
     using V = typename CxT<T>::V;
     constexpr int GB = M - REG_BITS;
     constexpr int NGRP = 1 << GB;
@@ -536,7 +624,9 @@ struct GenericStages {
         for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
         for (int g = st.g0; g < st.g0 + st.ng; ++g) {
           const uint32_t w = sgk[g];
-          if (w & 0x100u) apply_gate(a, w & 0xFFu, smat + (w >> 16));
+          if (!(w & 0x100u)) continue;
+          if ((w & 0xFFu) == OP_D16 * 16u) d16_apply<T, M>(a, smat + (w >> 16), tb, tc);
+          else apply_gate(a, w & 0xFFu, smat + (w >> 16));
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
@@ -601,6 +691,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const bool do_work = do_store || needed;
   const bool need_ticket = sp.nc > 0 || (do_store && !ident);
 
+  TcCtx tc{&sh.tc, 0u, 0u, false, true};
   if (do_work) {
     if (any_gate)
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
@@ -611,7 +702,26 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
       schunk[c] = o;
     }
+    // Dense four-qubit gates on the tensor cores: this CTA takes 64 columns of
+    // tensor memory (two 128 x 32 FP32 accumulators) and an mbarrier for the
+    // MMA completions, and gives both back after the tile loop.
+    if constexpr (sizeof(T) == 4 && M == 12 && !CTA) tc.on = A.dense_tc != 0 && sp.dense != 0 && any_gate;
+    if (tc.on) {
+      if (warp == 0) {
+        tmem_alloc(&sh.tc.tmem, TC_TMEM_COLS);
+        tmem_relinquish();
+      }
+      if (tid == 0) {
+        mbar_init(&sh.tc.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      }
+      tc_fence_before();
+    }
     __syncthreads();
+    if (tc.on) {
+      tc_fence_after();
+      tc.tmem = sh.tc.tmem;
+    }
 
     uint64_t tmask = 0;
     for (int j = 0; j < M; ++j) tmask |= 1ull << sp.tq[j];
@@ -756,7 +866,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         }
 
         // ---- gate stages
-        if (any_gate) Stages::template run<T, M>(A, sp, sgk, smat, tb);
+        if (any_gate) Stages::template run<T, M>(A, sp, sgk, smat, tb, tc);
 
         // ---- measurement-group table
         if (needed) {
@@ -816,6 +926,15 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       bcur = spread_add(bcur, sstep, omask);
     }
     if (pipe) cp_async_wait<0>();
+    if (tc.on) {
+      if (!tc.ok) atomicCAS(&A.ctrl->status, 0, int32_t(SV_ERR_TIMEOUT));
+      tc_fence_before();
+      __syncthreads();  // every tensor-memory read of this CTA is complete
+      if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tc.tmem, TC_TMEM_COLS);
+      }
+    }
   }
 
   if constexpr (CTA) {

@@ -483,6 +483,7 @@ struct Builder {
         }
         DGate g{};
         g.op = it.op;
+        if (it.op == OP_D16) ps.dense = 1;
         g.flag = it.flag;
         g.p0 = uint8_t(rpos[loc[it.q[0]]]);
         g.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;

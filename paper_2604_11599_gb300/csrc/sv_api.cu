@@ -127,6 +127,7 @@ struct sv_state {
   double prof_bytes = 0;
   bool use_cache = true;
   bool use_jit = false;
+  bool dense_tc = true;  // dense four-qubit gates on the tensor cores where the kernel supports it
 };
 
 namespace {
@@ -208,6 +209,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
     a.trace = h->trace;
     a.partials = h->partials.p;
     a.n = h->n_int;
+    a.dense_tc = h->dense_tc ? 1 : 0;
     const double sbytes = double(1ull << h->n_int) * double(h->amp_bytes);
     for (size_t i = 0; i < P.passes.size(); ++i) {
       if (h->profiling) {
@@ -435,6 +437,12 @@ sv_status sv_program_info(const sv_program* p, sv_program_stats* out) {
 sv_status sv_set_jit(sv_state* h, int enable) {
   if (!h) return fail(SV_ERR_ARG, "null handle");
   h->use_jit = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_set_dense_tc(sv_state* h, int enable) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->dense_tc = enable != 0;
   return SV_OK;
 }
 

@@ -80,6 +80,7 @@ def lib():
         "sv_profile": ([vp, i32], st),
         "sv_set_cache": ([vp, i32], st),
         "sv_set_jit": ([vp, i32], st),
+        "sv_set_dense_tc": ([vp, i32], st),
         "sv_jit_check": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
@@ -217,6 +218,10 @@ class State:
     def set_jit(self, enable: bool) -> None:
         """Per-program specialised sweep kernels (compiled on a program's first launch)."""
         _check(lib().sv_set_jit(self._h, 1 if enable else 0))
+
+    def set_dense_tc(self, enable: bool) -> None:
+        """Dense four-qubit gates on the tensor cores (complex64, 2^12-amplitude tiles; on by default)."""
+        _check(lib().sv_set_dense_tc(self._h, 1 if enable else 0))
 
     def set_cache(self, enable: bool) -> None:
         _check(lib().sv_set_cache(self._h, 1 if enable else 0))

@@ -392,6 +392,30 @@ _ALL_2Q = ("CX", "CY", "CZ", "SWAP", "CH")
 _ALL_2Q_ANG = ("CP", "CRX", "CRY", "CRZ")
 
 
+def haar_unitary(r: np.random.Generator, k: int) -> np.ndarray:
+    """A 2^k x 2^k unitary from the QR decomposition of a complex Gaussian
+    matrix, phases of R's diagonal folded in (Haar-distributed)."""
+    a = r.normal(size=(1 << k, 1 << k)) + 1j * r.normal(size=(1 << k, 1 << k))
+    qm, rm = np.linalg.qr(a)
+    return qm * (np.diag(rm) / np.abs(np.diag(rm)))
+
+
+def dense_layers(seed: int, n: int, layers: int = 8, k: int = 4) -> Circuit:
+    """Layers of dense k-qubit unitaries: each layer partitions the qubits at
+    random into groups of k and applies a Haar-random unitary to each group;
+    the n mod k qubits left over get a random RX/RY/RZ."""
+    r = rng(seed)
+    c = Circuit(n)
+    for _ in range(layers):
+        perm = [int(v) for v in r.permutation(n)]
+        for g in range(n // k):
+            c.dense(perm[g * k:(g + 1) * k], haar_unitary(r, k))
+        for q in perm[(n // k) * k:]:
+            kind = int(r.integers(3))
+            (c.rx, c.ry, c.rz)[kind](q, float(r.uniform(0.0, TWO_PI)))
+    return c
+
+
 def random_static(seed: int, n: int, depth: int, dense_k: int = 0, params: int = 0) -> Circuit:
     """Random circuit over the whole gate vocabulary (optionally with dense
     k-qubit unitaries drawn from QR of a complex Gaussian, and parameter refs)."""
@@ -407,10 +431,7 @@ def random_static(seed: int, n: int, depth: int, dense_k: int = 0, params: int =
         u = r.random()
         if dense_k and n >= dense_k and u < 0.1:
             qs = [int(v) for v in r.choice(n, size=dense_k, replace=False)]
-            a = r.normal(size=(1 << dense_k, 1 << dense_k)) + 1j * r.normal(size=(1 << dense_k, 1 << dense_k))
-            qm, rm = np.linalg.qr(a)
-            qm = qm * (np.diag(rm) / np.abs(np.diag(rm)))
-            c.dense(qs, qm)
+            c.dense(qs, haar_unitary(r, dense_k))
         elif n >= 2 and u < 0.35:
             a, b = (int(v) for v in r.choice(n, size=2, replace=False))
             if r.random() < 0.5:

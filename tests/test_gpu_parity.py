@@ -80,6 +80,37 @@ def test_specialised_kernels_parity(svmod, orc, dtype):
             assert prog.stats["specialised"] == 1
 
 
+@pytest.mark.parametrize("jit", [False, True])
+def test_dense4_tensor_cores_parity(svmod, orc, jit):
+    """Dense four-qubit unitaries on the tensor cores (complex64, 2^12-amplitude
+    tiles): oracle parity, and a result that differs from the FP32-pipe path at
+    the rounding level only (so the tensor-core path is the one that ran)."""
+    for n in (12, 14, 17):
+        c = W.dense_layers(40 + n, n, layers=4)
+        with svmod.State(n, "c64") as st:
+            st.set_jit(jit)
+            st.set_dense_pool(c.pool)
+            compare_run(st, orc, c.ops, n, "c64", pool=c.pool)
+            a_tc = st.amplitudes()
+            st.set_dense_tc(False)
+            compare_run(st, orc, c.ops, n, "c64", pool=c.pool)
+            a_alu = st.amplitudes()
+        assert not np.array_equal(a_tc, a_alu)
+        assert float(np.max(np.abs(a_tc - a_alu))) <= AMP_TOL["c64"]
+
+
+def test_dense4_tensor_cores_in_dynamic_programs(svmod, orc):
+    """Dense four-qubit gates beside measurement, reset and feed-forward (the
+    collapse is fused into the tile load that feeds the tensor-core stage)."""
+    n = 14
+    with svmod.State(n, "c64") as st:
+        for seed in range(4):
+            c = W.random_dynamic(700 + seed, n, n_ops=70, dense_k=4)
+            st.set_dense_pool(c.pool)
+            for shot in range(3):
+                compare_run(st, orc, c.ops, n, "c64", seed=seed, shot=shot, pool=c.pool)
+
+
 # --------------------------------------------------------------------------- dynamic circuits
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n", [2, 4, 6, 9, 13, 16])
