@@ -58,18 +58,27 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batching / VQE / serving measurements")
     ap.add_argument("--no-jit", action="store_true", help="use the generic pass kernels")
+    ap.add_argument("--circuit", default="layered", choices=["layered", "dense4"],
+                    help="layered: the plain dynamic-circuit workload; dense4: layers of dense 4-qubit unitaries")
+    ap.add_argument("--no-dense-tc", action="store_true", help="dense 4-qubit gates on the FP32 pipes")
     return ap.parse_args()
 
 
-def workload_name(n, dtype):
-    return (f"plain layered dynamic circuit, n={n}, {'complex64' if dtype == 'c64' else 'complex128'}: "
+def workload_name(n, dtype, kind="layered"):
+    cx = "complex64" if dtype == "c64" else "complex128"
+    if kind == "dense4":
+        return (f"dense-unitary circuit, n={n}, {cx}: 6 layers of Haar-random 4-qubit unitaries on a random "
+                f"partition of the qubits, RX/RY/RZ on the n mod 4 left over; 1 trajectory per step")
+    return (f"plain layered dynamic circuit, n={n}, {cx}: "
             f"20 layers (rotation on every qubit + CX perfect matching), measure+reset 2 qubits every 4 layers, "
             f"3-bit cond X/Z; 1 trajectory per step")
 
 
-def circuit(n, dtype):
+def circuit(n, dtype, kind="layered"):
     from paper_2604_11599_gb300 import workloads
 
+    if kind == "dense4":
+        return workloads.dense_layers(12, n, layers=6)
     return workloads.layered(GEN_SEED.get((n, dtype), 5), n, layers=20)
 
 
@@ -130,7 +139,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(n, dtype, seconds, gates_cap=None):
+def oracle_sample(n, dtype, seconds, gates_cap=None, kind="layered"):
     """The oracle over the longest gate-only prefix of the program that fits in
     `seconds`; returns (updates/s, sample description, threads)."""
     import numpy as np
@@ -138,22 +147,23 @@ def oracle_sample(n, dtype, seconds, gates_cap=None):
     import oracle
 
     oracle.build()
-    c = circuit(n, dtype)
+    c = circuit(n, dtype, kind)
     ops = c.ops
+    pool = c.pool if len(c.pool) else None
     gate_only = 0
-    while gate_only < len(ops) and ops[gate_only]["kind"] == 1:
+    while gate_only < len(ops) and ops[gate_only]["kind"] in (1, 2):
         gate_only += 1
     psi = np.empty(1 << n, dtype=np.complex128)
     # calibrate on 4 gates, then size the prefix to the time budget
     t0 = time.perf_counter()
-    oracle.run(ops[:4], n, out=psi)
+    oracle.run(ops[:4], n, pool=pool, out=psi)
     t_small = time.perf_counter() - t0
     per_gate = max(t_small / 4, 1e-6)
     k = int(max(4, min(gate_only, seconds / per_gate)))
     if gates_cap:
         k = min(k, gates_cap)
     t0 = time.perf_counter()
-    tr = oracle.run(ops[:k], n, out=psi)
+    tr = oracle.run(ops[:k], n, pool=pool, out=psi)
     dt = time.perf_counter() - t0
     assert tr.status == 0
     ups = k * float(1 << n) / dt
@@ -226,6 +236,43 @@ def measure_forms(sv, torch):
         vqe[dt] = {"parameter_sets": sets, "gradient_sets_per_s": sets / dts, "seconds": dts}
         h.close()
     out["vqe_adjoint"] = vqe
+    # dense four-qubit unitaries, n=30 complex64: tensor cores against the FP32 pipes
+    from paper_2604_11599_gb300.ir import Kind
+
+    c = W.dense_layers(12, 30, layers=6)
+    n_dense = int((c.ops["kind"] == int(Kind.DENSE)).sum())
+    dense = {"workload": "n=30 complex64, 6 layers of Haar-random dense 4-qubit unitaries on a random partition "
+                         "(7 per layer) + RX/RY/RZ on the 2 qubits left over; 1 trajectory per step",
+             "dense_gates_per_step": n_dense}
+    peaks, kind = measured_peaks()
+    with sv.State(30, "c64") as st:
+        st.set_jit(True)
+        st.set_dense_pool(c.pool)
+        prog = st.prepare(c.ops)
+        upd = float(prog.stats["gates"]) * float(1 << 30)
+        for tc in (True, False):
+            st.set_dense_tc(tc)
+            for _ in range(2):
+                st.launch(prog)
+            torch.cuda.synchronize()
+            st.profile(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                st.launch(prog)
+            e1.record()
+            e1.synchronize()
+            prof = st.profile_read()
+            st.profile(False)
+            ms = e0.elapsed_time(e1) / 3
+            gbs = prof["bytes"] / (prof["ms"] / 1000.0) / 1e9
+            useful = n_dense * float(1 << 30) * 128.0 * 3  # 128 flops / amplitude / dense gate, 3 steps
+            dense["tensor_cores" if tc else "fp32_pipes"] = {
+                "updates_per_s": upd / (ms / 1000.0), "ms_per_step": ms, "pass_kernels_gbs": gbs,
+                "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_kind": f"of {kind}",
+                "dense_tflops_useful": useful / (prof["ms"] / 1000.0) / 1e12}
+    out["dense4"] = dense
     # serving: a bounded slice of the Poisson request stream, server vs sequential plain path
     stream = W.serving_stream(seed=10, gen_seed=11, rate=200.0, duration=1.0, n_lo=10, n_hi=22, d_lo=10,
                               d_hi=40, max_shots=256)
@@ -250,7 +297,7 @@ def run_reference(args, rank, world):
     vals = []
     desc = threads = None
     for i in range(args.warmup + args.steps):
-        ups, desc, threads, dt = oracle_sample(args.n, args.dtype, per_step)
+        ups, desc, threads, dt = oracle_sample(args.n, args.dtype, per_step, kind=args.circuit)
         if i >= args.warmup:
             vals.append((ups, dt))
     ups = statistics.median(v for v, _ in vals)
@@ -259,7 +306,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * statistics.median(d for _, d in vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(args.n, args.dtype), "n": args.n},
+        "data": "synthetic", "config": {"workload": workload_name(args.n, args.dtype, args.circuit), "n": args.n},
         "cpu_baseline": {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -291,9 +338,12 @@ def main():
     from paper_2604_11599_gb300 import sv
 
     n, dtype = args.n, args.dtype
-    c = circuit(n, dtype)
+    c = circuit(n, dtype, args.circuit)
     st = sv.State(n, dtype)
     st.set_jit(not args.no_jit)
+    st.set_dense_tc(not args.no_dense_tc)
+    if len(c.pool):
+        st.set_dense_pool(c.pool)
     prog = st.prepare(c.ops)
     st.launch(prog, seed=0, shot=999)  # first launch compiles the specialised kernels (once per program)
     torch.cuda.synchronize()
@@ -366,7 +416,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        ups, desc, threads, dt = oracle_sample(n, dtype, args.cpu_seconds)
+        ups, desc, threads, dt = oracle_sample(n, dtype, args.cpu_seconds, kind=args.circuit)
         cpu = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                "seconds": dt}
 
@@ -375,7 +425,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(n, dtype), "n": n, "state": dtype,
+            "config": {"workload": workload_name(n, dtype, args.circuit), "n": n, "state": dtype,
                        "gates_per_step": stats["gates"], "draws_per_step": stats["draws"],
                        "passes_per_step": stats["passes"], "tile_bits": stats["tile_bits"],
                        "low_bits": stats["low_bits"], "l2": "inputs larger than L2 (state 2^n amplitudes)",

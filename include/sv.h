@@ -353,8 +353,10 @@ sv_status sv_set_dense_tc(sv_state* h, int enable);
 
 /*
  * Host-only check of the specialiser (no device touched): lowers the op list
- * and compiles its specialised module to a cubin.  On failure the first
- * log_len - 1 bytes of the compiler log are copied to log (nullable).
+ * and compiles its specialised module to a cubin.  The first log_len - 1 bytes
+ * of the compiler log are copied to log (nullable): on failure the errors, on
+ * success the ptxas resource report (registers, spill bytes, stack) of every
+ * compiled chunk.
  */
 sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
                        size_t n_complex, char* log, size_t log_len);

@@ -14,7 +14,9 @@
 // the dropped Alo*Blo term and the truncation of the low parts are ~2^-21
 // relative), accumulated in FP32 in tensor memory.
 //
-// Operands live in shared memory in the no-swizzle K-major layout of
+// A (the amplitudes) goes to tensor memory: every thread writes its group's
+// row into its own lane with tcgen05.st, so no shared-memory staging is needed.
+// B (the gate) lives in shared memory in the no-swizzle K-major layout of
 // core matrices (8 rows x 16 bytes, 128 contiguous bytes): element (row, k)
 // of a 32-column matrix at byte (row / 8) * 1024 + (k / 4) * 128 +
 // (row % 8) * 16 + (k % 4) * 4, i.e. 128 bytes between core matrices along K
@@ -62,6 +64,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
+// the reverse: thread l writes 32 consecutive columns of lane (taddr lane field) + l
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -94,12 +109,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
 }
-// D (tensor memory) = A * B^T (+ D when acc != 0); issued by one thread.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+// D (tensor memory) = A * B^T (+ D when acc != 0), A in tensor memory (row i
+// in lane i, element k in column a_tmem + k), B in shared memory; issued by
+// one thread.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
           d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
 // arrive once on the mbarrier when every MMA issued so far by this thread has completed
@@ -120,12 +138,15 @@ __host__ __device__ constexpr uint32_t cm_off(uint32_t row, uint32_t k) {
   return (row >> 3) * 1024u + (k >> 2) * 128u + (row & 7u) * 16u + (k & 3u) * 4u;
 }
 
-constexpr uint32_t TC_TMEM_COLS = 64;        // two 128 x 32 FP32 accumulators
+// Tensor memory of one CTA: A of rows 0..127 (warps 0-3) in columns 0..63
+// (TF32 high parts 0..31, low parts 32..63), A of rows 128..255 (warps 4-7) in
+// 64..127, the two 128 x 32 FP32 accumulators in 128..159 and 160..191.
+constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_WAIT_POLLS = 1u << 20;  // bounded MMA completion wait
 
 // Shared state of the tensor-core path (part of the pass kernel's static shared memory).
 struct TcShared {
-  __align__(128) float bt[2][1024];  // Bt high / low parts, core-matrix layout (32 x 32)
+  __align__(128) float bt[2][1024];  // B high / low parts, core-matrix layout (32 x 32)
   uint64_t bar;                      // MMA completion
   uint32_t tmem;                     // tensor-memory base address
   uint32_t pad;

@@ -45,7 +45,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
   const svp::DPass& d = P.passes[pi];
   const int GB = P.m - svp::REG_BITS;
   o << "struct JS" << pi << " {\n"
-    << "  template <typename T, int M>\n"
+    << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
     << "                                             TcCtx& tc) {\n"
@@ -76,7 +76,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (!fn) continue;
       std::ostringstream call;
       call << fn;
-      if (gt.op == svp::OP_D16) call << "<T, M>(a, smat + " << gt.mat << ", tb, tc)";
+      if (gt.op == svp::OP_D16) call << "<T, M, TC>(a, smat + " << gt.mat << ", tb, tc)";
       else if (two_qubit(gt.op)) call << "<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ")";
       else call << "<" << int(gt.p0) << ">(a, smat + " << gt.mat << ")";
       if (gt.flag >= 0) o << "      if (sgk[" << g << "] & 0x100u) " << call.str() << ";\n";
@@ -140,6 +140,14 @@ std::string cu_err(CUresult r) {
 
 // Source of one module: the stage programs of passes [p0, p1) and one kernel
 // that selects among them by pass index (a uniform branch per CTA).
+// passes [p0, p1) hold a dense gate that the tensor cores can take
+bool chunk_has_tc(const svp::Plan& P, size_t p0, size_t p1) {
+  if (P.dtype != SV_C64 || P.m != 12) return false;
+  for (size_t pi = p0; pi < p1; ++pi)
+    if (P.passes[pi].dense) return true;
+  return false;
+}
+
 std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   std::ostringstream o;
   const bool c64 = P.dtype == SV_C64;
@@ -152,20 +160,25 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   for (size_t pi = p0; pi < p1; ++pi)
     if (P.passes[pi].ns) emit_stages(o, P, pi);
   o << "struct JitStages {\n"
-    << "  template <typename T, int M>\n"
+    << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
     << "                                             TcCtx& tc) {\n"
     << "    switch (A.pass) {\n";
   for (size_t pi = p0; pi < p1; ++pi)
-    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M>(A, sp, sgk, smat, tb, tc); break;\n";
+    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc); break;\n";
   o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
   const char* T = c64 ? "float" : "double";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1)
-    << ") sv_jit_passes(const svk::PassArgs A) {\n"
-    << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
-    << "  __shared__ svk::PassShared<" << T << "> sh;\n"
-    << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages>(A, A.pass, sh, smem_raw);\n}\n";
+  // the tensor-core variant only where a pass of the chunk holds a dense gate
+  // (kernels without tcgen05 instructions sweep faster)
+  const bool tc = chunk_has_tc(P, p0, p1);
+  for (int v = 0; v < (tc ? 2 : 1); ++v)
+    o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1) << ") "
+      << (v ? "sv_jit_passes_tc" : "sv_jit_passes") << "(const svk::PassArgs A) {\n"
+      << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
+      << "  __shared__ svk::PassShared<" << T << "> sh;\n"
+      << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages, " << (v ? "true" : "false")
+      << ">(A, A.pass, sh, smem_raw);\n}\n";
   return o.str();
 }
 
@@ -178,15 +191,24 @@ std::string generate_source(const svp::Plan& P) { return generate_chunk(P, 0, P.
 
 namespace {
 
-sv_status compile_source(const std::string& src, std::vector<char>& cubin, std::string& err) {
+// verbose: ptxas resource usage (registers, spills, stack) into *info
+sv_status compile_source(const std::string& src, std::vector<char>& cubin, std::string& err,
+                         std::string* info = nullptr) {
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "sv_jit_passes.cu", kJitHeaderCount, kJitHeaderSources,
                          kJitHeaderNames) != NVRTC_SUCCESS) {
     err = "nvrtcCreateProgram failed";
     return SV_ERR_CUDA;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17"};
-  const nvrtcResult rc = nvrtcCompileProgram(prog, 2, opts);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--ptxas-options=-v"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, info ? 3 : 2, opts);
+  if (rc == NVRTC_SUCCESS && info) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &log[0]);
+    *info += log.c_str();
+  }
   if (rc != NVRTC_SUCCESS) {
     size_t n = 0;
     nvrtcGetProgramLogSize(prog, &n);
@@ -206,7 +228,7 @@ sv_status compile_source(const std::string& src, std::vector<char>& cubin, std::
 
 // Compiles the module chunks in parallel (NVRTC programs are independent).
 sv_status compile_chunks(const svp::Plan& P, std::vector<std::vector<char>>& cubins, std::vector<size_t>& first,
-                         std::string& err) {
+                         std::string& err, std::vector<std::string>* infos = nullptr) {
   const size_t passes = P.passes.size(), k = chunk_count(P);
   first.assign(k + 1, 0);
   for (size_t c = 0; c <= k; ++c) first[c] = passes * c / k;
@@ -215,7 +237,10 @@ sv_status compile_chunks(const svp::Plan& P, std::vector<std::vector<char>>& cub
   std::vector<std::string> errs(k);
   std::vector<std::thread> th;
   for (size_t c = 0; c < k; ++c)
-    th.emplace_back([&, c] { st[c] = compile_source(generate_chunk(P, first[c], first[c + 1]), cubins[c], errs[c]); });
+    th.emplace_back([&, c] {
+      st[c] = compile_source(generate_chunk(P, first[c], first[c + 1]), cubins[c], errs[c],
+                             infos ? &(*infos)[c] : nullptr);
+    });
   for (auto& t : th) t.join();
   for (size_t c = 0; c < k; ++c)
     if (st[c] != SV_OK) {
@@ -227,11 +252,14 @@ sv_status compile_chunks(const svp::Plan& P, std::vector<std::vector<char>>& cub
 
 }  // namespace
 
-sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err) {
+sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err, std::string* info) {
   std::vector<std::vector<char>> cubins;
   std::vector<size_t> first;
-  sv_status st = compile_chunks(P, cubins, first, err);
+  std::vector<std::string> infos(chunk_count(P));
+  sv_status st = compile_chunks(P, cubins, first, err, info ? &infos : nullptr);
   if (st == SV_OK && !cubins.empty()) cubin = cubins[0];
+  if (info)
+    for (const std::string& s : infos) *info += s;
   return st;
 }
 
@@ -272,6 +300,7 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
   const size_t one = (size_t(1) << P.m) * amp;
   J->smem = 2 * one <= size_t(128) * 1024 ? 2 * one : one;
   J->functions.assign(P.passes.size(), nullptr);
+  J->functions_tc.assign(P.passes.size(), nullptr);
   for (size_t c = 0; c < cubins.size(); ++c) {
     CUmodule mod;
     CUresult r = D.moduleLoadData(&mod, cubins[c].data());
@@ -280,14 +309,22 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
       return SV_ERR_CUDA;
     }
     J->modules.push_back(mod);
-    CUfunction f;
+    CUfunction f = nullptr, ftc = nullptr;
     r = D.moduleGetFunction(&f, mod, "sv_jit_passes");
     if (r == CUDA_SUCCESS) r = D.funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
+    if (r == CUDA_SUCCESS && chunk_has_tc(P, first[c], first[c + 1])) {
+      r = D.moduleGetFunction(&ftc, mod, "sv_jit_passes_tc");
+      if (r == CUDA_SUCCESS)
+        r = D.funcSetAttribute(ftc, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
+    }
     if (r != CUDA_SUCCESS) {
       err = "loading a specialised module: " + cu_err(r);
       return SV_ERR_CUDA;
     }
-    for (size_t pi = first[c]; pi < first[c + 1]; ++pi) J->functions[pi] = f;
+    for (size_t pi = first[c]; pi < first[c + 1]; ++pi) {
+      J->functions[pi] = f;
+      J->functions_tc[pi] = P.passes[pi].dense ? ftc : nullptr;
+    }
   }
   J->compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out = std::shared_ptr<JitModule>(std::move(J));
@@ -301,7 +338,8 @@ sv_status launch(const JitModule& J, int pass, const svk::PassArgs& a, int grid,
   svk::PassArgs b = a;
   b.pass = pass;
   void* args[] = {&b};
-  const CUresult r = driver().launchKernel(static_cast<CUfunction>(J.functions[size_t(pass)]), unsigned(grid), 1, 1,
+  void* fn = (a.dense_tc && J.functions_tc[size_t(pass)]) ? J.functions_tc[size_t(pass)] : J.functions[size_t(pass)];
+  const CUresult r = driver().launchKernel(static_cast<CUfunction>(fn), unsigned(grid), 1, 1,
                                     svp::PASS_THREADS, 1, 1, unsigned(J.smem), reinterpret_cast<CUstream>(s), args,
                                     nullptr);
   if (r != CUDA_SUCCESS) {

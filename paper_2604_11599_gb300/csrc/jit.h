@@ -23,6 +23,7 @@ namespace svj {
 struct JitModule {
   std::vector<void*> modules;      // CUmodule per chunk of passes
   std::vector<void*> functions;    // CUfunction of each pass
+  std::vector<void*> functions_tc; // its tensor-core variant (passes with a dense gate), else null
   size_t smem = 0;                 // dynamic shared memory per launch
   double compile_seconds = 0;
   ~JitModule();
@@ -31,8 +32,10 @@ struct JitModule {
 // Source text of the specialised module (for tests and inspection of the generator).
 std::string generate_source(const svp::Plan& P);
 
-// NVRTC only (no device needed): the module's cubin.
-sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err);
+// NVRTC only (no device needed): the module's cubin; with info, the ptxas
+// resource report (registers, spills, stack) of every chunk is appended to it.
+sv_status compile_cubin(const svp::Plan& P, std::vector<char>& cubin, std::string& err,
+                        std::string* info = nullptr);
 
 // compile_cubin + load into the current context.  Modules are cached for the
 // process by device and generated source, so a program lowered again reuses

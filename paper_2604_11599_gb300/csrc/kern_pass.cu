@@ -2,6 +2,8 @@
 
 #include <cstdio>
 
+#include <algorithm>
+
 #include "pass_body.cuh"
 
 namespace svk {
@@ -111,11 +113,12 @@ __global__ void k_init_state(void* state, uint64_t n_amp) {
     s[i] = (i == 0) ? mkc(T(1), T(0)) : mkc(T(0), T(0));
 }
 
-template <typename T, int M>
+// TC: the variant for passes holding a dense four-qubit gate (tensor cores)
+template <typename T, int M, bool TC>
 __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_pass(const PassArgs A, const int pi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassShared<T> sh;
-  pass_body<T, M, false>(A, pi, sh, smem_raw);
+  pass_body<T, M, false, GenericStages, TC>(A, pi, sh, smem_raw);
 }
 
 // ============================================================ host launchers
@@ -127,37 +130,75 @@ static size_t pass_smem() {
   return 2 * one <= size_t(128) * 1024 ? 2 * one : one;
 }
 
-template <typename T, int M>
-static cudaError_t launch_pass_tm(const PassArgs& a, int pi, int grid, cudaStream_t s) {
+template <typename T, int M, bool TC>
+static cudaError_t launch_pass_v(const PassArgs& a, int pi, int grid, cudaStream_t s) {
   const size_t smem = pass_smem<T, M>();
-  k_pass<T, M><<<grid, PASS_THREADS, smem, s>>>(a, pi);
+  static bool attr = false;  // dynamic shared memory above 48 KiB, once per variant
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_pass<T, M, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_pass<T, M, TC><<<grid, PASS_THREADS, smem, s>>>(a, pi);
   return cudaGetLastError();
+}
+
+template <typename T, int M>
+static cudaError_t launch_pass_tm(const PassArgs& a, int pi, int grid, cudaStream_t s, bool dense) {
+  if constexpr (sizeof(T) == 4 && M == 12)
+    if (dense && a.dense_tc) return launch_pass_v<T, M, true>(a, pi, grid, s);
+  return launch_pass_v<T, M, false>(a, pi, grid, s);
+}
+
+// Resident CTAs per SM from the kernel's own resource counts.  The runtime's
+// occupancy query answers 1 for any kernel that holds tcgen05 instructions
+// (measured on GB300), although CTAs that each allocate a slice of tensor
+// memory run side by side; the pass kernels take 64 of the 512 columns.
+static int blocks_per_sm(const cudaFuncAttributes& fa, size_t dyn_smem, int threads) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int regs_sm = 65536, smem_sm = 233472, smem_rsv = 1024, thr_sm = 2048, blk_sm = 32;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+  int n = blk_sm;
+  if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+  n = std::min(n, int(size_t(smem_sm) / (fa.sharedSizeBytes + dyn_smem + size_t(smem_rsv))));
+  n = std::min(n, thr_sm / threads);
+  n = std::min(n, int(512 / TC_TMEM_COLS));
+  return n;
 }
 
 template <typename T, int M>
 static cudaError_t pass_attr_tm(int* per_sm) {
   const size_t smem = pass_smem<T, M>();
-  cudaError_t e = cudaFuncSetAttribute(k_pass<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pass<T, M>, PASS_THREADS, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_pass<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaFuncAttributes fa{};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, M, false>);
+  if (e == cudaSuccess) *per_sm = blocks_per_sm(fa, smem, PASS_THREADS);
   return e;
 }
 
-cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s) {
+cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s, bool dense) {
   if (dtype == SV_C64) {
     switch (m) {
-      case 10: return launch_pass_tm<float, 10>(a, pi, grid, s);
-      case 11: return launch_pass_tm<float, 11>(a, pi, grid, s);
-      case 12: return launch_pass_tm<float, 12>(a, pi, grid, s);
-      case 13: return launch_pass_tm<float, 13>(a, pi, grid, s);
-      case 14: return launch_pass_tm<float, 14>(a, pi, grid, s);
+      case 10: return launch_pass_tm<float, 10>(a, pi, grid, s, dense);
+      case 11: return launch_pass_tm<float, 11>(a, pi, grid, s, dense);
+      case 12: return launch_pass_tm<float, 12>(a, pi, grid, s, dense);
+      case 13: return launch_pass_tm<float, 13>(a, pi, grid, s, dense);
+      case 14: return launch_pass_tm<float, 14>(a, pi, grid, s, dense);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (m) {
-    case 10: return launch_pass_tm<double, 10>(a, pi, grid, s);
-    case 11: return launch_pass_tm<double, 11>(a, pi, grid, s);
-    case 12: return launch_pass_tm<double, 12>(a, pi, grid, s);
-    case 13: return launch_pass_tm<double, 13>(a, pi, grid, s);
+    case 10: return launch_pass_tm<double, 10>(a, pi, grid, s, dense);
+    case 11: return launch_pass_tm<double, 11>(a, pi, grid, s, dense);
+    case 12: return launch_pass_tm<double, 12>(a, pi, grid, s, dense);
+    case 13: return launch_pass_tm<double, 13>(a, pi, grid, s, dense);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -171,21 +171,35 @@ __device__ __forceinline__ void g_d16(V* a, const V* m) {
 // Dense 16 x 16 unitary on the register qubits of every group of a
 // 2^12-amplitude complex64 tile, on the tensor cores (dev_tc.cuh).  Collective:
 // all 256 threads call it together, each holding its group (= its thread
-// index) in a[].  Once every thread has read its group the tile buffer tb is
-// free, so it holds the A operand, 128 rows at a time: the TF32 high parts in
-// its first 16 KiB, the low parts in the next 16 KiB.  Rows 0..127 (warps 0-3)
-// go to accumulator columns 0..31, rows 128..255 (warps 4-7) to 32..63; warp w
-// reads its rows back from tensor-memory lanes 32 (w mod 4) ... + 31.
+// index) in a[].  Warp w writes its 32 rows (TF32 high and low parts) into
+// tensor-memory lanes 32 (w mod 4) ... + 31, columns 64 (w / 4) ...; one
+// thread then issues both 128-row products back to back (rows 0..127 into the
+// accumulator at column 128, rows 128..255 into the one at 160) and every
+// thread reads its output row from its own lane once they complete.
 template <typename V>
-__device__ __forceinline__ void d16_tc(V* a, const V* m, V* tb, TcCtx& tc) {
+__device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   const int tid = threadIdx.x, warp = tid >> 5;
   TcShared& s = *tc.s;
-  unsigned char* stage = reinterpret_cast<unsigned char*>(tb);
   unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[0]);
   unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[1]);
-  tc_fence_before();
-  __syncthreads();  // every group read from the tile; previous results read from tensor memory
-  {  // Bt entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]
+  const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
+  const uint32_t half = uint32_t(warp >> 2);
+  {  // this thread's row: high parts, then (same registers) low parts
+    uint32_t w[32];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      w[2 * j] = __float_as_uint(tf32_hi(a[j].x));
+      w[2 * j + 1] = __float_as_uint(tf32_hi(a[j].y));
+    }
+    tmem_st32(tc.tmem + lane_base + 64u * half, w);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      w[2 * j] = __float_as_uint(a[j].x - tf32_hi(a[j].x));
+      w[2 * j + 1] = __float_as_uint(a[j].y - tf32_hi(a[j].y));
+    }
+    tmem_st32(tc.tmem + lane_base + 64u * half + 32u, w);
+  }
+  {  // B entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]; the previous products have completed
     const int r = tid >> 4, c = tid & 15;
     const V u = m[r * 16 + c];
     const float e[4] = {u.x, -u.y, u.y, u.x};
@@ -197,45 +211,34 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, V* tb, TcCtx& tc) {
       *reinterpret_cast<float*>(bt1 + off) = e[q] - hi;
     }
   }
-  constexpr uint32_t IDESC = idesc_tf32(128, 32);
-#pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    if ((tid >> 7) == h) {
-      const uint32_t row = uint32_t(tid & 127);
+  tmem_wait_st();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();  // all rows in tensor memory, B in shared memory, previous results read
+  if (tid == 0 && tc.ok) {
+    tc_fence_after();
+    constexpr uint32_t IDESC = idesc_tf32(128, 32);
+    const uint32_t b0 = smem_u32(bt0), b1 = smem_u32(bt1);
 #pragma unroll
-      for (int kc = 0; kc < 8; ++kc) {  // K elements 4kc..4kc+3: amplitudes 2kc, 2kc+1 (re, im)
-        const V x0 = a[2 * kc], x1 = a[2 * kc + 1];
-        const float4 hi = make_float4(tf32_hi(x0.x), tf32_hi(x0.y), tf32_hi(x1.x), tf32_hi(x1.y));
-        const float4 lo = make_float4(x0.x - hi.x, x0.y - hi.y, x1.x - hi.z, x1.y - hi.w);
-        const uint32_t off = cm_off(row, uint32_t(4 * kc));
-        *reinterpret_cast<float4*>(stage + off) = hi;
-        *reinterpret_cast<float4*>(stage + 16384 + off) = lo;
-      }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && tc.ok) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(stage), b0 = smem_u32(bt0), b1 = smem_u32(bt1);
-      const uint32_t d = tc.tmem + uint32_t(32 * h);
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t d = tc.tmem + 128u + 32u * uint32_t(h), ah = tc.tmem + 64u * uint32_t(h);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {  // K = 8 per MMA; three products per k-step
-        const uint32_t ko = uint32_t(k) * 256u;
-        mma_tf32(d, smem_desc(a0 + ko, 128, 1024), smem_desc(b0 + ko, 128, 1024), IDESC, k > 0 ? 1u : 0u);
-        mma_tf32(d, smem_desc(a0 + ko, 128, 1024), smem_desc(b1 + ko, 128, 1024), IDESC, 1u);
-        mma_tf32(d, smem_desc(a0 + 16384 + ko, 128, 1024), smem_desc(b0 + ko, 128, 1024), IDESC, 1u);
+        const uint32_t ko = uint32_t(k) * 256u, kc = uint32_t(k) * 8u;
+        mma_tf32_ts(d, ah + kc, smem_desc(b0 + ko, 128, 1024), IDESC, k > 0 ? 1u : 0u);
+        mma_tf32_ts(d, ah + kc, smem_desc(b1 + ko, 128, 1024), IDESC, 1u);
+        mma_tf32_ts(d, ah + 32u + kc, smem_desc(b0 + ko, 128, 1024), IDESC, 1u);
       }
-      mma_commit(&s.bar);
     }
-    // after a wait ran out, no further MMAs or waits (the barriers stay): the
-    // pass ends quickly and the run reports SV_ERR_TIMEOUT
-    if (tc.ok && !mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS)) tc.ok = false;
-    ++tc.phase;
-    tc_fence_after();
+    mma_commit(&s.bar);
   }
+  // after a wait ran out, no further MMAs or waits (the barriers stay): the
+  // pass ends quickly and the run reports SV_ERR_TIMEOUT
+  if (tc.ok && !mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS)) tc.ok = false;
+  ++tc.phase;
+  tc_fence_after();
   uint32_t r[32];
-  tmem_ld32(tc.tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(32 * (warp >> 2)), r);
+  tmem_ld32(tc.tmem + lane_base + 128u + 32u * half, r);
   tmem_wait_ld();
 #pragma unroll
   for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
@@ -243,11 +246,11 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, V* tb, TcCtx& tc) {
 
 // A dense four-qubit unitary: on the tensor cores where the pass enabled them
 // (complex64, 2^12-amplitude tiles), else on the FP32 / FP64 pipes.
-template <typename T, int M, typename V>
+template <typename T, int M, bool TC, typename V>
 __device__ __forceinline__ void d16_apply(V* a, const V* m, V* tb, TcCtx& tc) {
-  if constexpr (sizeof(T) == 4 && M == 12) {
+  if constexpr (TC && sizeof(T) == 4 && M == 12) {
     if (tc.on) {
-      d16_tc(a, m, tb, tc);
+      d16_tc(a, m, tc);
       return;
     }
   }
@@ -606,7 +609,7 @@ struct PassShared {
 // Data-driven register stages: every stage reads its register / group bit
 // addresses and gate records from the plan at run time.
 struct GenericStages {
-  template <typename T, int M>
+  template <typename T, int M, bool TC>
   static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,
                                              const typename CxT<T>::V* smat, typename CxT<T>::V* tb, TcCtx& tc) {
     using V = typename CxT<T>::V;
@@ -625,7 +628,7 @@ struct GenericStages {
         for (int g = st.g0; g < st.g0 + st.ng; ++g) {
           const uint32_t w = sgk[g];
           if (!(w & 0x100u)) continue;
-          if ((w & 0xFFu) == OP_D16 * 16u) d16_apply<T, M>(a, smat + (w >> 16), tb, tc);
+          if ((w & 0xFFu) == OP_D16 * 16u) d16_apply<T, M, TC>(a, smat + (w >> 16), tb, tc);
           else apply_gate(a, w & 0xFFu, smat + (w >> 16));
         }
 #pragma unroll
@@ -637,7 +640,10 @@ struct GenericStages {
   }
 };
 
-template <typename T, int M, bool CTA, typename Stages = GenericStages>
+// TC: the kernel variant that may send dense four-qubit gates to the tensor
+// cores (launched only for passes that hold one: the mere presence of tcgen05
+// instructions in a kernel measured ~20% slower sweeps on GB300).
+template <typename T, int M, bool CTA, typename Stages = GenericStages, bool TC = false>
 __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T>& sh, void* smem_tiles) {
   using V = typename CxT<T>::V;
   using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
@@ -705,7 +711,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     // Dense four-qubit gates on the tensor cores: this CTA takes 64 columns of
     // tensor memory (two 128 x 32 FP32 accumulators) and an mbarrier for the
     // MMA completions, and gives both back after the tile loop.
-    if constexpr (sizeof(T) == 4 && M == 12 && !CTA) tc.on = A.dense_tc != 0 && sp.dense != 0 && any_gate;
+    if constexpr (TC && sizeof(T) == 4 && M == 12 && !CTA) tc.on = A.dense_tc != 0 && sp.dense != 0 && any_gate;
     if (tc.on) {
       if (warp == 0) {
         tmem_alloc(&sh.tc.tmem, TC_TMEM_COLS);
@@ -866,7 +872,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         }
 
         // ---- gate stages
-        if (any_gate) Stages::template run<T, M>(A, sp, sgk, smat, tb, tc);
+        if (any_gate) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc);
 
         // ---- measurement-group table
         if (needed) {

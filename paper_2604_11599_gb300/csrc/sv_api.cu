@@ -225,7 +225,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
         const sv_status st = svj::launch(*jm, int(i), a, grid, s, err);
         if (st != SV_OK) return fail(st, err);
       } else {
-        SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s));
+        SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s, P.passes[i].dense != 0));
       }
       if (h->profiling) {
         SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));
@@ -454,7 +454,7 @@ sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, co
   sv_status st = svp::build_plan(n, dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, svp::Tuning{}, P, err);
   if (st == SV_OK) {
     std::vector<char> cubin;
-    st = svj::compile_cubin(P, cubin, err);
+    st = svj::compile_cubin(P, cubin, err, &err);
   }
   if (log && log_len) {
     const size_t k = std::min(err.size(), log_len - 1);
