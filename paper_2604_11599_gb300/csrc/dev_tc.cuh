@@ -9,10 +9,10 @@
 // Bt[2r+1][2c] = Im U_rc, Bt[2r+1][2c+1] = Re U_rc.  That is a dense
 // contraction of 8 flops per amplitude and row of U (128 flops per complex64
 // amplitude), so it goes to the tensor pipe as kind::tf32 MMAs.  TF32 keeps
-// 10 mantissa bits; FP32 accuracy comes from the three-product split
-// A*B ~= Ahi*Bhi + Ahi*Blo + Alo*Bhi (Ahi = A rounded to TF32, Alo = A - Ahi;
-// the dropped Alo*Blo term and the truncation of the low parts are ~2^-21
-// relative), accumulated in FP32 in tensor memory.
+// 10 mantissa bits; FP32-level accuracy comes from the three-product split
+// A*B ~= Ahi*Bhi + Ahi*Blo + Alo*Bhi (Ahi = A truncated to TF32, Alo = A - Ahi
+// exactly; the dropped Alo*Blo term and the truncation of the low parts are
+// ~2^-20 relative), accumulated in FP32 in tensor memory.
 //
 // A (the amplitudes) goes to tensor memory: every thread writes its group's
 // row into its own lane with tcgen05.st, so no shared-memory staging is needed.
@@ -126,12 +126,10 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// x rounded to TF32 (10 mantissa bits, nearest, ties away), as an FP32 value
-__device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
+// x truncated to TF32 (its top 19 bits: sign, exponent, 10 mantissa bits);
+// x - tf32_hi(x) is exact in FP32 and below 2^-10 |x|, so the MMA's own
+// truncation of that low part leaves ~2^-20 |x| of error
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 // byte offset of element (row, k) in the 32-column core-matrix layout
 __host__ __device__ constexpr uint32_t cm_off(uint32_t row, uint32_t k) {
@@ -145,16 +143,19 @@ constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_WAIT_POLLS = 1u << 20;  // bounded MMA completion wait
 
 // Shared state of the tensor-core path (part of the pass kernel's static shared memory).
+constexpr int TC_SLOTS = 2;  // dense gates per pass (MAX_PASS_MAT holds two 16 x 16 matrices)
+
 struct TcShared {
-  __align__(128) float bt[2][1024];  // B high / low parts, core-matrix layout (32 x 32)
-  uint64_t bar;                      // MMA completion
-  uint32_t tmem;                     // tensor-memory base address
-  uint32_t pad;
+  __align__(128) float bt[TC_SLOTS][2][1024];  // B high / low parts per dense gate, core-matrix layout
+  uint64_t bar;                                // MMA completion
+  uint32_t tmem;                               // tensor-memory base address
+  uint32_t slot_mat[TC_SLOTS];                 // matrix offset (in the pass's matrix block) of each slot
 };
 
 // Per-thread view of it, passed to the stages.
 struct TcCtx {
   TcShared* s;
+  const void* smat;  // the pass's matrix block in shared memory
   uint32_t tmem;   // tensor-memory base address
   uint32_t phase;  // completed MMA batches (parity of the next wait)
   bool on;         // dense gates of this pass go to the tensor cores

@@ -176,12 +176,34 @@ __device__ __forceinline__ void g_d16(V* a, const V* m) {
 // thread then issues both 128-row products back to back (rows 0..127 into the
 // accumulator at column 128, rows 128..255 into the one at 160) and every
 // thread reads its output row from its own lane once they complete.
+// B of a dense gate (its 32 x 32 real form, TF32 high and low parts) into a
+// slot; once per pass, by all threads.
+template <typename V>
+__device__ __forceinline__ void d16_build_b(const V* m, TcShared& s, int slot) {
+  unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[slot][0]);
+  unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
+  for (int e = threadIdx.x; e < 256; e += PASS_THREADS) {  // entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]
+    const int r = e >> 4, c = e & 15;
+    const V u = m[e];
+    const float v[4] = {u.x, -u.y, u.y, u.x};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t off = cm_off(uint32_t(2 * r + (q >> 1)), uint32_t(2 * c + (q & 1)));
+      const float hi = tf32_hi(v[q]);
+      *reinterpret_cast<float*>(bt0 + off) = hi;
+      *reinterpret_cast<float*>(bt1 + off) = v[q] - hi;
+    }
+  }
+}
+
 template <typename V>
 __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   const int tid = threadIdx.x, warp = tid >> 5;
   TcShared& s = *tc.s;
-  unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[0]);
-  unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[1]);
+  const uint32_t mo = uint32_t(m - static_cast<const V*>(tc.smat));
+  const int slot = s.slot_mat[0] == mo ? 0 : 1;
+  unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[slot][0]);
+  unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
   const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
   const uint32_t half = uint32_t(warp >> 2);
   {  // this thread's row: high parts, then (same registers) low parts
@@ -199,22 +221,9 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
     }
     tmem_st32(tc.tmem + lane_base + 64u * half + 32u, w);
   }
-  {  // B entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]; the previous products have completed
-    const int r = tid >> 4, c = tid & 15;
-    const V u = m[r * 16 + c];
-    const float e[4] = {u.x, -u.y, u.y, u.x};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t off = cm_off(uint32_t(2 * r + (q >> 1)), uint32_t(2 * c + (q & 1)));
-      const float hi = tf32_hi(e[q]);
-      *reinterpret_cast<float*>(bt0 + off) = hi;
-      *reinterpret_cast<float*>(bt1 + off) = e[q] - hi;
-    }
-  }
   tmem_wait_st();
-  fence_async_smem();
   tc_fence_before();
-  __syncthreads();  // all rows in tensor memory, B in shared memory, previous results read
+  __syncthreads();  // all rows in tensor memory, previous results read
   if (tid == 0 && tc.ok) {
     tc_fence_after();
     constexpr uint32_t IDESC = idesc_tf32(128, 32);
@@ -697,7 +706,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const bool do_work = do_store || needed;
   const bool need_ticket = sp.nc > 0 || (do_store && !ident);
 
-  TcCtx tc{&sh.tc, 0u, 0u, false, true};
+  TcCtx tc{&sh.tc, nullptr, 0u, 0u, false, true};
   if (do_work) {
     if (any_gate)
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
@@ -727,6 +736,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     if (tc.on) {
       tc_fence_after();
       tc.tmem = sh.tc.tmem;
+      tc.smat = smat;
+      // B of the pass's dense gates, once: slot k <- the k-th dense record
+      int k = 0;
+      for (int g = 0; g < int(sp.ng) && k < TC_SLOTS; ++g)
+        if ((sgk[g] & 0xFFu) == OP_D16 * 16u) {
+          const uint32_t mo = sgk[g] >> 16;
+          d16_build_b(smat + mo, sh.tc, k);
+          if (tid == 0) sh.tc.slot_mat[k] = mo;
+          ++k;
+        }
+      fence_async_smem();
+      __syncthreads();
     }
 
     uint64_t tmask = 0;
