@@ -22,6 +22,9 @@ const char* op_template(int op) {
     case svp::OP_U: return "g_u";
     case svp::OP_R: return "g_r";
     case svp::OP_RX: return "g_rx";
+    case svp::OP_RXF: return "g_rxf";
+    case svp::OP_RYF: return "g_ryf";
+    case svp::OP_DZ: return "g_dz";
     case svp::OP_D: return "g_d";
     case svp::OP_X: return "g_x";
     case svp::OP_CU: return "g_cu";
@@ -79,7 +82,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (gt.op == svp::OP_D16) call << "<T, M, TC>(a, smat + " << gt.mat << ", tb, tc)";
       else if (two_qubit(gt.op)) call << "<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ")";
       else call << "<" << int(gt.p0) << ">(a, smat + " << gt.mat << ")";
-      if (gt.flag >= 0) o << "      if (sgk[" << g << "] & 0x100u) " << call.str() << ";\n";
+      if (gt.flag >= 0) o << "      if (sgk[" << g << "] & SGK_ON) " << call.str() << ";\n";
       else o << "      " << call.str() << ";\n";
     }
     if (pairs) {
@@ -176,7 +179,7 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
     o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1) << ") "
       << (v ? "sv_jit_passes_tc" : "sv_jit_passes") << "(const svk::PassArgs A) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
-      << "  __shared__ svk::PassShared<" << T << "> sh;\n"
+      << "  __shared__ svk::PassShared<" << T << ", " << (v ? "true" : "false") << "> sh;\n"
       << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages, " << (v ? "true" : "false")
       << ">(A, A.pass, sh, smem_raw);\n}\n";
   return o.str();

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
       uint32_t ndots = 0;
       for (int g = tid; g < int(sp.ng); g += PASS_THREADS) {
         const DGate d = J.b_gates[sp.g0 + g];
-        sh.sgk[g] = uint32_t(d.key) | (1u << 8) | (d.mat << 16);
+        sh.sgk[g] = uint32_t(d.key) | SGK_ON | (d.mat << 16);
         sdslot[g] = d.dslot;
         if (d.op == OP_DOT || d.op == OP_CDOT) sdotg[d.dslot] = d.gidx;
       }
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
       }
       __syncthreads();
       for (int g = 0; g < int(sp.ng); ++g) {
-        const uint32_t op = (sh.sgk[g] & 0xFFu) >> 4;
+        const uint32_t op = (sh.sgk[g] & SGK_KEY) >> 4;
         if (op == OP_DOT || op == OP_CDOT) ndots = max(ndots, uint32_t(sdslot[g]) + 1);
       }
       uint64_t tmask = 0;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
             }
             for (int g = st.g0; g < st.g0 + st.ng; ++g) {
               const uint32_t w = sh.sgk[g];
-              const uint32_t key = w & 0xFFu;
+              const uint32_t key = w & SGK_KEY;
               const uint32_t op = key >> 4;
               const V* mt = sh.smat + (w >> 16);
               if (op == OP_DOT || op == OP_CDOT) {

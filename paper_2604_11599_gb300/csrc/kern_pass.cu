@@ -78,6 +78,21 @@ __global__ void k_prep(PrepArgs P) {
             mats[j.out] = mkc(T(m[0].x), T(m[0].y));
             mats[j.out + 1] = mkc(T(m[3].x), T(m[3].y));
             break;
+          case OP_RXF: case OP_RYF: {
+            // RX: m00 = c, m01 = -i s; RY: m00 = c, m10 = s.  Factor the larger of
+            // |c|, |s| out so that the remaining coefficient has magnitude <= 1.
+            const double c = m[0].x, sn = j.op == OP_RXF ? -m[1].y : m[2].x;
+            const bool form1 = fabs(sn) > fabs(c);
+            mats[j.out] = mkc(T(form1 ? c / sn : sn / c), T(form1 ? 1 : 0));
+            mats[j.out + 1] = mkc(T(form1 ? sn : c), T(0));
+            break;
+          }
+          case OP_DZ: {  // diag(d0, d1) = d0 diag(1, d1 / d0), |d0| = 1
+            const double2 d0 = m[0], d1 = m[3];
+            mats[j.out] = mkc(T(d1.x * d0.x + d1.y * d0.y), T(d1.y * d0.x - d1.x * d0.y));
+            mats[j.out + 1] = mkc(T(d0.x), T(d0.y));
+            break;
+          }
           default: break;
         }
       }
@@ -117,7 +132,7 @@ __global__ void k_init_state(void* state, uint64_t n_amp) {
 template <typename T, int M, bool TC>
 __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_pass(const PassArgs A, const int pi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ PassShared<T> sh;
+  __shared__ PassShared<T, TC> sh;
   pass_body<T, M, false, GenericStages, TC>(A, pi, sh, smem_raw);
 }
 

@@ -68,6 +68,67 @@ __device__ __forceinline__ void g_rx(V* a, const V* m) {
   }
 }
 
+// Factored rotations (forward plans): the scalar factor m[1] is applied by the
+// pass, so each output is one fused multiply-add per component.
+// RX: form 0 [1 -it; -it 1] (t = m[0].x), form 1 [u -i; -i u] (u = m[0].x).
+template <int P, typename V>
+__device__ __forceinline__ void g_rxf(V* a, const V* m) {
+  const auto k = m[0].x;
+  if (m[0].y == 0) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << P)) continue;
+      const int h = j | (1 << P);
+      const V x = a[j], y = a[h];
+      a[j] = mkc(fma(k, y.y, x.x), fma(-k, y.x, x.y));
+      a[h] = mkc(fma(k, x.y, y.x), fma(-k, x.x, y.y));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << P)) continue;
+      const int h = j | (1 << P);
+      const V x = a[j], y = a[h];
+      a[j] = mkc(fma(k, x.x, y.y), fma(k, x.y, -y.x));
+      a[h] = mkc(fma(k, y.x, x.y), fma(k, y.y, -x.x));
+    }
+  }
+}
+
+// RY: form 0 [1 -t; t 1], form 1 [u -1; 1 u].
+template <int P, typename V>
+__device__ __forceinline__ void g_ryf(V* a, const V* m) {
+  const auto k = m[0].x;
+  if (m[0].y == 0) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << P)) continue;
+      const int h = j | (1 << P);
+      const V x = a[j], y = a[h];
+      a[j] = mkc(fma(-k, y.x, x.x), fma(-k, y.y, x.y));
+      a[h] = mkc(fma(k, x.x, y.x), fma(k, x.y, y.y));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j & (1 << P)) continue;
+      const int h = j | (1 << P);
+      const V x = a[j], y = a[h];
+      a[j] = mkc(fma(k, x.x, -y.x), fma(k, x.y, -y.y));
+      a[h] = mkc(fma(k, y.x, x.x), fma(k, y.y, x.y));
+    }
+  }
+}
+
+// diag(1, p) on bit P (the factor d0 of diag(d0, d1) is applied by the pass)
+template <int P, typename V>
+__device__ __forceinline__ void g_dz(V* a, const V* m) {
+  const V p = m[0];
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j & (1 << P)) a[j] = cmul(p, a[j]);
+}
+
 template <int P, typename V>
 __device__ __forceinline__ void g_d(V* a, const V* m) {
   const V d0 = m[0], d1 = m[1];
@@ -340,6 +401,9 @@ __device__ __forceinline__ void apply_gate(V* a, uint32_t key, const V* mt) {
     SVK_K1(OP_U, g_u)
     SVK_K1(OP_R, g_r)
     SVK_K1(OP_RX, g_rx)
+    SVK_K1(OP_RXF, g_rxf)
+    SVK_K1(OP_RYF, g_ryf)
+    SVK_K1(OP_DZ, g_dz)
     SVK_K1(OP_D, g_d)
     SVK_K1(OP_X, g_x)
     SVK_K2(OP_CU, g_cu)
@@ -596,9 +660,23 @@ __device__ __forceinline__ uint32_t group_base(const uint16_t* E, uint32_t g) {
   return b;
 }
 
-// Shared state of one pass (static shared memory of the kernel that runs it).
-template <typename T>
-struct PassShared {
+// The measurement table is accumulated from the tile before the pass's scalar
+// factor f is multiplied in: |amp|^2 sums scale by |f|^2.
+static __device__ __forceinline__ void scale_table(double* ctab, double2 f) {
+  const double m = f.x * f.x + f.y * f.y;
+  if (m != 1.0)
+    for (int i = 0; i < 16; ++i) ctab[i] *= m;
+}
+
+// Shared state of one pass (static shared memory of the kernel that runs it);
+// the tensor-core part exists only in the variant that may use it.
+template <bool TC> struct TcPart {};
+template <> struct TcPart<true> {
+  TcShared tc;  // tensor-core path of dense gates
+};
+
+template <typename T, bool TC = false>
+struct PassShared : TcPart<TC> {
   DPass sp;
   uint32_t sgk[MAX_PASS_GATES];  // key | active << 8 | matrix offset << 16
   __align__(16) typename CxT<T>::V smat[MAX_PASS_MAT];
@@ -606,9 +684,14 @@ struct PassShared {
   double ctab[16];               // measurement-group table of this CTA
   double wsum[PASS_THREADS / 32][16];
   double tile16[16];
+  double2 pfac;                  // product of the factors of the pass's active factored gates
   int s_last;
-  TcShared tc;                   // tensor-core path of dense gates
 };
+template <typename T, bool TC>
+__device__ __forceinline__ TcShared* tc_shared(PassShared<T, TC>& sh) {
+  if constexpr (TC) return &sh.tc;
+  else return nullptr;
+}
 
 // One pass over the state.  GRID mode (CTA = false): the tiles are shared by
 // all CTAs of the launch and the last CTA to finish reduces the group table
@@ -636,9 +719,9 @@ struct GenericStages {
         for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
         for (int g = st.g0; g < st.g0 + st.ng; ++g) {
           const uint32_t w = sgk[g];
-          if (!(w & 0x100u)) continue;
-          if ((w & 0xFFu) == OP_D16 * 16u) d16_apply<T, M, TC>(a, smat + (w >> 16), tb, tc);
-          else apply_gate(a, w & 0xFFu, smat + (w >> 16));
+          if (!(w & SGK_ON)) continue;
+          if ((w & SGK_KEY) == OP_D16 * 16u) d16_apply<T, M, TC>(a, smat + (w >> 16), tb, tc);
+          else apply_gate(a, w & SGK_KEY, smat + (w >> 16));
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
@@ -653,7 +736,7 @@ struct GenericStages {
 // cores (launched only for passes that hold one: the mere presence of tcgen05
 // instructions in a kernel measured ~20% slower sweeps on GB300).
 template <typename T, int M, bool CTA, typename Stages = GenericStages, bool TC = false>
-__device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T>& sh, void* smem_tiles) {
+__device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T, TC>& sh, void* smem_tiles) {
   using V = typename CxT<T>::V;
   using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
   constexpr int GB = M - REG_BITS;  // group-index bits of a stage
@@ -683,7 +766,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   for (int g = tid; g < int(sp.ng); g += PASS_THREADS) {
     const DGate d = A.gates[sp.g0 + g];
     const uint32_t on = d.flag < 0 ? 1u : (A.flags[d.flag] ? 1u : 0u);
-    sgk[g] = uint32_t(d.key) | (on << 8) | (d.mat << 16);
+    sgk[g] = uint32_t(d.key) | (on << SGK_ON_BIT) | (d.mat << 16);
     act_any |= int(on);
   }
   const bool any_gate = __syncthreads_or(act_any) != 0;
@@ -706,7 +789,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const bool do_work = do_store || needed;
   const bool need_ticket = sp.nc > 0 || (do_store && !ident);
 
-  TcCtx tc{&sh.tc, nullptr, 0u, 0u, false, true};
+  TcCtx tc{tc_shared(sh), nullptr, 0u, 0u, false, true};
   if (do_work) {
     if (any_gate)
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
@@ -723,27 +806,46 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     if constexpr (TC && sizeof(T) == 4 && M == 12 && !CTA) tc.on = A.dense_tc != 0 && sp.dense != 0 && any_gate;
     if (tc.on) {
       if (warp == 0) {
-        tmem_alloc(&sh.tc.tmem, TC_TMEM_COLS);
+        tmem_alloc(&tc.s->tmem, TC_TMEM_COLS);
         tmem_relinquish();
       }
       if (tid == 0) {
-        mbar_init(&sh.tc.bar, 1);
+        mbar_init(&tc.s->bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
       }
       tc_fence_before();
     }
     __syncthreads();
+    // the scalar factors of the factored rotations (OP_RXF / OP_RYF / OP_DZ) that
+    // are active in this pass, multiplied into the tile when it is stored
+    if (tid == 0) {
+      double fr = 1.0, fi = 0.0;
+      if (any_gate)
+        for (int g = 0; g < int(sp.ng); ++g) {
+          const uint32_t w = sgk[g], op = (w & SGK_KEY) >> 4;
+          if (!(w & SGK_ON) || (op != OP_RXF && op != OP_RYF && op != OP_DZ)) continue;
+          const V f = smat[(w >> 16) + 1];
+          const double r = fr * double(f.x) - fi * double(f.y);
+          fi = fr * double(f.y) + fi * double(f.x);
+          fr = r;
+        }
+      sh.pfac = make_double2(fr, fi);
+    }
+    __syncthreads();
+    const double2 pf = sh.pfac;
+    const bool fscale = !(pf.x == 1.0 && pf.y == 0.0);
+    const V fT = mkc(T(pf.x), T(pf.y));
     if (tc.on) {
       tc_fence_after();
-      tc.tmem = sh.tc.tmem;
+      tc.tmem = tc.s->tmem;
       tc.smat = smat;
       // B of the pass's dense gates, once: slot k <- the k-th dense record
       int k = 0;
       for (int g = 0; g < int(sp.ng) && k < TC_SLOTS; ++g)
-        if ((sgk[g] & 0xFFu) == OP_D16 * 16u) {
+        if ((sgk[g] & SGK_KEY) == OP_D16 * 16u) {
           const uint32_t mo = sgk[g] >> 16;
-          d16_build_b(smat + mo, sh.tc, k);
-          if (tid == 0) sh.tc.slot_mat[k] = mo;
+          d16_build_b(smat + mo, *tc.s, k);
+          if (tid == 0) tc.s->slot_mat[k] = mo;
           ++k;
         }
       fence_async_smem();
@@ -936,10 +1038,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
             const uint64_t gi = base | schunk[ch] | woff;
             const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
-            if constexpr (sizeof(T) == 4)
-              __stcg(reinterpret_cast<float4*>(A.state) + (gi >> 1), *reinterpret_cast<const float4*>(tb + p));
-            else
-              __stcg(reinterpret_cast<double2*>(A.state) + gi, tb[p]);
+            if constexpr (sizeof(T) == 4) {
+              float4 q = *reinterpret_cast<const float4*>(tb + p);
+              if (fscale) {
+                const float2 a0 = cmul(fT, make_float2(q.x, q.y)), a1 = cmul(fT, make_float2(q.z, q.w));
+                q = make_float4(a0.x, a0.y, a1.x, a1.y);
+              }
+              __stcg(reinterpret_cast<float4*>(A.state) + (gi >> 1), q);
+            } else {
+              const V x = tb[p];
+              __stcg(reinterpret_cast<double2*>(A.state) + gi, fscale ? cmul(fT, x) : x);
+            }
           }
         }
         if (pipe) {
@@ -967,7 +1076,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   if constexpr (CTA) {
     if (need_ticket) {
       __syncthreads();
-      if (tid == 0) scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
+      if (tid == 0) {
+        scale_table(ctab, sh.pfac);
+        scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
+      }
     }
     __syncthreads();
   } else {
@@ -989,6 +1101,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     }
     __syncthreads();
     if (tid != 0) return;
+    scale_table(ctab, sh.pfac);
     scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
   }
 }

@@ -265,10 +265,20 @@ struct Builder {
     return d;
   }
 
-  void emit_job_gate(const Item& it, uint32_t out) {
+  // The op a gate item runs as: forward plans take the factored rotations
+  // (RX, RY and one-qubit diagonal gates), backward plans the plain ones.
+  uint8_t op_of(const Item& it) const {
+    if (adjoint || it.gate < 0 || it.nq != 1) return it.op;
+    if (it.gate == SV_RX) return OP_RXF;
+    if (it.gate == SV_RY) return OP_RYF;
+    if (it.op == OP_D) return OP_DZ;
+    return it.op;
+  }
+
+  void emit_job_gate(const Item& it, uint32_t out, uint8_t op) {
     DJob j{};
     j.kind = J_GATE;
-    j.op = it.op;
+    j.op = op;
     j.adj = adjoint ? 1 : 0;
     j.gate = uint8_t(it.gate);
     for (int k = 0; k < 3; ++k) {
@@ -290,7 +300,7 @@ struct Builder {
   }
 
   // matrix entries of an item (with its derivative items in backward plans)
-  int mat_len(const Item& it) const { return op_mat_len(it.op) + 4 * n_dots(it); }
+  int mat_len(const Item& it) const { return op_mat_len(op_of(it)) + 4 * n_dots(it); }
 
   // conjugate transpose of a row-major K x K complex matrix (re, im pairs)
   static std::vector<double> dagger(const double* m, int K) {
@@ -473,7 +483,7 @@ struct Builder {
           d.flag = -1;
           d.p0 = uint8_t(rpos[loc[it.q[0]]]);
           d.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;
-          d.key = uint8_t(d.op * 16 + d.p0 * 4 + d.p1);
+          d.key = uint16_t(d.op * 16 + d.p0 * 4 + d.p1);
           d.mat = mat;
           d.dslot = uint16_t(dots++);
           d.gidx = uint32_t(it.pidx[k]);
@@ -482,16 +492,16 @@ struct Builder {
           P.gates.push_back(d);
         }
         DGate g{};
-        g.op = it.op;
+        g.op = op_of(it);
         if (it.op == OP_D16) ps.dense = 1;
         g.flag = it.flag;
         g.p0 = uint8_t(rpos[loc[it.q[0]]]);
         g.p1 = it.nq > 1 ? uint8_t(rpos[loc[it.q[1]]]) : 0;
-        g.key = uint8_t(it.op == OP_D16 ? OP_D16 * 16 : it.op * 16 + g.p0 * 4 + g.p1);
+        g.key = uint16_t(g.op == OP_D16 ? OP_D16 * 16 : g.op * 16 + g.p0 * 4 + g.p1);
         g.mat = mat;
         const uint32_t out = P.n_mat + mat;
         if (it.gate >= 0) {
-          emit_job_gate(it, out);
+          emit_job_gate(it, out, g.op);
         } else if (it.op == OP_U || it.op == OP_U4) {
           const int K = it.op == OP_U ? 2 : 4;
           std::vector<double> v = adjoint ? dagger(it.dense, K) : std::vector<double>(it.dense, it.dense + 2 * K * K);
@@ -525,7 +535,7 @@ struct Builder {
             }
           emit_job_const(OP_D16, v, out);
         }
-        mat += uint32_t(op_mat_len(it.op));
+        mat += uint32_t(op_mat_len(g.op));
         P.gates.push_back(g);
       }
       st.ng = uint16_t(P.gates.size() - ps.g0 - st.g0);  // gate records, derivative items included

@@ -39,6 +39,13 @@ enum OpCode : uint8_t {
   // lambda in registers 8..15, accumulated for one gradient entry; M = dU/da * U^dagger
   OP_DOT,   // M (4 complex) on p0
   OP_CDOT,  // M on target p1 where control p0 is 1
+  // forward plans only: one-qubit rotations with a scalar factor taken out, so
+  // that one matrix entry per row is 1 (two FP operations per amplitude
+  // instead of four); the pass multiplies the product of the factors of its
+  // active gates into the state once, when it stores the tile
+  OP_RXF,   // RX = f [1 -it; -it 1] (form 0) or f [u -i; -i u] (form 1): (k, form), (f)
+  OP_RYF,   // RY = f [1 -t; t 1] (form 0) or f [u -1; 1 u] (form 1): (k, form), (f)
+  OP_DZ,    // diag(d0, d1) = d0 diag(1, p): (p), (d0)
   OP_COUNT
 };
 
@@ -47,7 +54,7 @@ enum OpCode : uint8_t {
 static inline int op_mat_len(int op) {
   switch (op) {
     case OP_U: case OP_R: case OP_CU: case OP_DOT: case OP_CDOT: return 4;
-    case OP_RX: case OP_D: case OP_CD: return 2;
+    case OP_RX: case OP_D: case OP_CD: case OP_RXF: case OP_RYF: case OP_DZ: return 2;
     case OP_U4: return 16;
     case OP_D16: return 256;
     default: return 0;
@@ -77,15 +84,18 @@ constexpr int MAX_ADJ_PARAMS = 1024;
 
 // gate as the kernel sees it: positions are register-bit indices (0..3) of its stage
 struct DGate {
-  uint8_t key;    // op * 16 + p0 * 4 + p1: one switch selects op and positions
-  uint8_t op, p0, p1;
+  uint16_t key;   // op * 16 + p0 * 4 + p1 (9 bits): one switch selects op and positions
+  uint8_t op, p0, p1, pad0;
+  uint16_t dslot; // OP_DOT / OP_CDOT: accumulator slot within the pass
   int32_t flag;   // -1: unconditional; else index into the flag array
   uint32_t mat;   // offset (complex entries) from the pass's matrix base
-  uint16_t dslot; // OP_DOT / OP_CDOT: accumulator slot within the pass
-  uint16_t pad2;
   uint32_t gidx;  // OP_DOT / OP_CDOT: gradient entry (parameter index)
   uint32_t pad3;
 };
+// a gate record in a kernel's shared list: key | active << SGK_ON_BIT | matrix offset << 16
+constexpr uint32_t SGK_KEY = 0x1FFu;
+constexpr int SGK_ON_BIT = 9;
+constexpr uint32_t SGK_ON = 1u << SGK_ON_BIT;
 
 // Register stage.  The tile is stored XOR-swizzled in shared memory (see
 // tile_swizzle); because the swizzle is linear over GF(2), the address of a

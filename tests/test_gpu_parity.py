@@ -80,6 +80,38 @@ def test_specialised_kernels_parity(svmod, orc, dtype):
             assert prog.stats["specialised"] == 1
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_factored_rotations_edge_angles(svmod, orc, dtype):
+    """RX / RY / RZ / phase gates run with their scalar factor taken out (form
+    chosen by |cos| vs |sin|; the pass applies the product of the factors when it
+    stores and scales its measurement table by its squared modulus).  Angles at
+    and around the form switch and the zeros of cos and sin, with measurements
+    and resets inside the same passes."""
+    n = 13
+    edge = [0.0, math.pi / 2, math.pi, 3 * math.pi / 2, 2 * math.pi, 3 * math.pi, -math.pi,
+            math.pi - 1e-7, math.pi + 1e-7, 1e-7, math.pi / 2 + 1e-9, 7.5]
+    rng = np.random.default_rng(17)
+    for trial in range(3):
+        c = Circuit(n)
+        for q in range(n):
+            c.h(q)
+        for layer in range(4):
+            for q in range(n):
+                th = float(edge[rng.integers(len(edge))])
+                [c.rx, c.ry, c.rz, c.p][int(rng.integers(4))](q, th)
+            for q in range(0, n - 1, 2):
+                c.cx(q, q + 1)
+            c.measure(int(rng.integers(n)), layer)
+            c.reset(int(rng.integers(n)))
+            c.s(int(rng.integers(n)))
+            c.t(int(rng.integers(n)))
+        with svmod.State(n, dtype) as st:
+            for jit in (False, True):
+                st.set_jit(jit)
+                for shot in range(3):
+                    compare_run(st, orc, c.ops, n, dtype, seed=trial, shot=shot)
+
+
 @pytest.mark.parametrize("jit", [False, True])
 def test_dense4_tensor_cores_parity(svmod, orc, jit):
     """Dense four-qubit unitaries on the tensor cores (complex64, 2^12-amplitude
