@@ -267,20 +267,19 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
   const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
   const uint32_t half = uint32_t(warp >> 2);
-  {  // this thread's row: high parts, then (same registers) low parts
-    uint32_t w[32];
+  {  // this thread's row, 16 columns at a time: high parts (columns 0..31), low parts (32..63)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      w[2 * j] = __float_as_uint(tf32_hi(a[j].x));
-      w[2 * j + 1] = __float_as_uint(tf32_hi(a[j].y));
-    }
-    tmem_st32(tc.tmem + lane_base + 64u * half, w);
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      w[2 * j] = __float_as_uint(a[j].x - tf32_hi(a[j].x));
-      w[2 * j + 1] = __float_as_uint(a[j].y - tf32_hi(a[j].y));
+      for (int j = 0; j < 8; ++j) {
+        const V x = a[8 * (q & 1) + j];
+        const float h0 = tf32_hi(x.x), h1 = tf32_hi(x.y);
+        w[2 * j] = __float_as_uint(q < 2 ? h0 : x.x - h0);
+        w[2 * j + 1] = __float_as_uint(q < 2 ? h1 : x.y - h1);
+      }
+      tmem_st16(tc.tmem + lane_base + 64u * half + 16u * uint32_t(q), w);
     }
-    tmem_st32(tc.tmem + lane_base + 64u * half + 32u, w);
   }
   tmem_wait_st();
   tc_fence_before();
@@ -316,15 +315,17 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
 
 // A dense four-qubit unitary: on the tensor cores where the pass enabled them
 // (complex64, 2^12-amplitude tiles), else on the FP32 / FP64 pipes.
+// The tensor-core variant of a pass kernel runs only with the tensor-core path
+// on (sv_set_dense_tc), so it carries no FP32 fallback (its registers would
+// spill); the status records it if that is ever violated.
 template <typename T, int M, bool TC, typename V>
 __device__ __forceinline__ void d16_apply(V* a, const V* m, V* tb, TcCtx& tc) {
   if constexpr (TC && sizeof(T) == 4 && M == 12) {
-    if (tc.on) {
-      d16_tc(a, m, tc);
-      return;
-    }
+    if (tc.on) d16_tc(a, m, tc);
+    else if (threadIdx.x == 0) tc.ok = false;
+  } else {
+    g_d16(a, m);
   }
-  g_d16(a, m);
 }
 
 #define SVK_K1(OP, FN)                          \
@@ -1062,8 +1063,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       bcur = spread_add(bcur, sstep, omask);
     }
     if (pipe) cp_async_wait<0>();
+    if (!tc.ok)  // a completion wait ran out, or a dense gate reached this variant with the path off
+      atomicCAS(&A.ctrl->status, 0, int32_t(tc.on ? SV_ERR_TIMEOUT : SV_ERR_UNSUPPORTED));
     if (tc.on) {
-      if (!tc.ok) atomicCAS(&A.ctrl->status, 0, int32_t(SV_ERR_TIMEOUT));
       tc_fence_before();
       __syncthreads();  // every tensor-memory read of this CTA is complete
       if (warp == 0) {
