@@ -902,6 +902,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       }
     }
 
+    double tacc = 0.0;  // this lane's measurement-table slot over the tiles (all group qubits in the tile)
     for (uint64_t u = ustart; u < nunits; u += ustep) {
       uint64_t tl[2] = {u, 0};
       int cnt = 1;
@@ -1014,21 +1015,28 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             }
           }
           const Acc r = warp_transpose_reduce16(acc, lane);
-          if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = double(r);
-          __syncthreads();
-          if (tid < 16) {
-            double s2 = 0;
-            for (int w = 0; w < PASS_THREADS / 32; ++w) s2 += sh.wsum[w][tid];
-            tile16[tid] = s2;
-          }
-          __syncthreads();
-          if (tid < (1 << sp.kin)) {
-            uint32_t ob = 0;
-            for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
-            double s2 = 0;
-            for (int j = 0; j < 16; ++j)
-              if ((uint32_t(j) & kmask) == uint32_t(tid)) s2 += tile16[j];
-            ctab[tid | (ob << sp.kin)] += s2;
+          if (sp.kin == sp.gk) {
+            // every measured qubit is a tile qubit, so a lane's table slot is the
+            // same in every tile: lanes accumulate across tiles in FP64 (tile
+            // order) and the warps are combined once, after the tile loop
+            if ((lane & 1) == 0) tacc += double(r);
+          } else {
+            if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = double(r);
+            __syncthreads();
+            if (tid < 16) {
+              double s2 = 0;
+              for (int w = 0; w < PASS_THREADS / 32; ++w) s2 += sh.wsum[w][tid];
+              tile16[tid] = s2;
+            }
+            __syncthreads();
+            if (tid < (1 << sp.kin)) {
+              uint32_t ob = 0;
+              for (int k = 0; k < sp.gk - sp.kin; ++k) ob |= uint32_t((base >> sp.outer_gq[k]) & 1) << k;
+              double s2 = 0;
+              for (int j = 0; j < 16; ++j)
+                if ((uint32_t(j) & kmask) == uint32_t(tid)) s2 += tile16[j];
+              ctab[tid | (ob << sp.kin)] += s2;
+            }
           }
         }
 
@@ -1063,6 +1071,22 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       bcur = spread_add(bcur, sstep, omask);
     }
     if (pipe) cp_async_wait<0>();
+    if (needed && sp.kin == sp.gk) {  // the lanes' table slots, combined over warps in a fixed order
+      if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = tacc;
+      __syncthreads();
+      if (tid < 16) {
+        double s2 = 0;
+        for (int w = 0; w < PASS_THREADS / 32; ++w) s2 += sh.wsum[w][tid];
+        tile16[tid] = s2;
+      }
+      __syncthreads();
+      if (tid < (1 << sp.kin)) {
+        double s2 = 0;
+        for (int j = 0; j < 16; ++j)
+          if ((uint32_t(j) & kmask) == uint32_t(tid)) s2 += tile16[j];
+        ctab[tid] += s2;
+      }
+    }
     if (!tc.ok)  // a completion wait ran out, or a dense gate reached this variant with the path off
       atomicCAS(&A.ctrl->status, 0, int32_t(tc.on ? SV_ERR_TIMEOUT : SV_ERR_UNSUPPORTED));
     if (tc.on) {
