@@ -143,11 +143,19 @@ std::string cu_err(CUresult r) {
 
 // Source of one module: the stage programs of passes [p0, p1) and one kernel
 // that selects among them by pass index (a uniform branch per CTA).
-// passes [p0, p1) hold a dense gate that the tensor cores can take
-bool chunk_has_tc(const svp::Plan& P, size_t p0, size_t p1) {
-  if (P.dtype != SV_C64 || P.m != 12) return false;
+// the pass may run on the tensor cores (dense gate, complex64, 2^12-amplitude tiles)
+bool pass_tc(const svp::Plan& P, size_t pi) { return P.dtype == SV_C64 && P.m == 12 && P.passes[pi].dense; }
+
+const char* variant_name(bool tc, bool proj) {
+  return tc ? (proj ? "sv_jit_passes_tc_p" : "sv_jit_passes_tc") : (proj ? "sv_jit_passes_p" : "sv_jit_passes");
+}
+
+// some pass of [p0, p1) launches variant (tc, proj): the plain-arithmetic
+// variant of every pass exists (sv_set_dense_tc(0) runs it), the tensor-core
+// one for passes with a dense gate
+bool chunk_has_variant(const svp::Plan& P, size_t p0, size_t p1, bool tc, bool proj) {
   for (size_t pi = p0; pi < p1; ++pi)
-    if (P.passes[pi].dense) return true;
+    if ((P.passes[pi].proj != 0) == proj && (!tc || pass_tc(P, pi))) return true;
   return false;
 }
 
@@ -172,16 +180,19 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
     if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc); break;\n";
   o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
   const char* T = c64 ? "float" : "double";
-  // the tensor-core variant only where a pass of the chunk holds a dense gate
-  // (kernels without tcgen05 instructions sweep faster)
-  const bool tc = chunk_has_tc(P, p0, p1);
-  for (int v = 0; v < (tc ? 2 : 1); ++v)
+  // kernel variants: tensor cores only where a pass of the chunk holds a dense
+  // gate (kernels without tcgen05 instructions sweep faster), the projector
+  // pipeline only where a pass may start with a measurement projector pending
+  for (int v = 0; v < 4; ++v) {
+    const bool vt = v & 1, vp = v & 2;
+    if (!chunk_has_variant(P, p0, p1, vt, vp)) continue;
     o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1) << ") "
-      << (v ? "sv_jit_passes_tc" : "sv_jit_passes") << "(const svk::PassArgs A) {\n"
+      << variant_name(vt, vp) << "(const svk::PassArgs A) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
-      << "  __shared__ svk::PassShared<" << T << ", " << (v ? "true" : "false") << "> sh;\n"
-      << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages, " << (v ? "true" : "false")
-      << ">(A, A.pass, sh, smem_raw);\n}\n";
+      << "  __shared__ svk::PassShared<" << T << ", " << (vt ? "true" : "false") << "> sh;\n"
+      << "  svk::pass_body<" << T << ", " << P.m << ", false, svk::JitStages, " << (vt ? "true" : "false") << ", "
+      << (vp ? "true" : "false") << ">(A, A.pass, sh, smem_raw);\n}\n";
+  }
   return o.str();
 }
 
@@ -312,21 +323,21 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
       return SV_ERR_CUDA;
     }
     J->modules.push_back(mod);
-    CUfunction f = nullptr, ftc = nullptr;
-    r = D.moduleGetFunction(&f, mod, "sv_jit_passes");
-    if (r == CUDA_SUCCESS) r = D.funcSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
-    if (r == CUDA_SUCCESS && chunk_has_tc(P, first[c], first[c + 1])) {
-      r = D.moduleGetFunction(&ftc, mod, "sv_jit_passes_tc");
+    CUfunction fv[4] = {nullptr, nullptr, nullptr, nullptr};  // index: tc | proj << 1
+    for (int v = 0; v < 4 && r == CUDA_SUCCESS; ++v) {
+      if (!chunk_has_variant(P, first[c], first[c + 1], v & 1, v & 2)) continue;
+      r = D.moduleGetFunction(&fv[v], mod, variant_name(v & 1, v & 2));
       if (r == CUDA_SUCCESS)
-        r = D.funcSetAttribute(ftc, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
+        r = D.funcSetAttribute(fv[v], CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(J->smem));
     }
     if (r != CUDA_SUCCESS) {
       err = "loading a specialised module: " + cu_err(r);
       return SV_ERR_CUDA;
     }
     for (size_t pi = first[c]; pi < first[c + 1]; ++pi) {
-      J->functions[pi] = f;
-      J->functions_tc[pi] = P.passes[pi].dense ? ftc : nullptr;
+      const int pj = P.passes[pi].proj ? 2 : 0;
+      J->functions[pi] = fv[pj];
+      J->functions_tc[pi] = pass_tc(P, pi) ? fv[pj | 1] : nullptr;
     }
   }
   J->compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -128,12 +128,13 @@ __global__ void k_init_state(void* state, uint64_t n_amp) {
     s[i] = (i == 0) ? mkc(T(1), T(0)) : mkc(T(0), T(0));
 }
 
-// TC: the variant for passes holding a dense four-qubit gate (tensor cores)
-template <typename T, int M, bool TC>
+// TC: the variant for passes holding a dense four-qubit gate (tensor cores);
+// PROJ: the variant for passes that may start with a measurement projector pending
+template <typename T, int M, bool TC, bool PROJ>
 __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_pass(const PassArgs A, const int pi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassShared<T, TC> sh;
-  pass_body<T, M, false, GenericStages, TC>(A, pi, sh, smem_raw);
+  pass_body<T, M, false, GenericStages, TC, PROJ>(A, pi, sh, smem_raw);
 }
 
 // ============================================================ host launchers
@@ -145,24 +146,26 @@ static size_t pass_smem() {
   return 2 * one <= size_t(128) * 1024 ? 2 * one : one;
 }
 
-template <typename T, int M, bool TC>
+template <typename T, int M, bool TC, bool PROJ>
 static cudaError_t launch_pass_v(const PassArgs& a, int pi, int grid, cudaStream_t s) {
   const size_t smem = pass_smem<T, M>();
   static bool attr = false;  // dynamic shared memory above 48 KiB, once per variant
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_pass<T, M, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_pass<T, M, TC, PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_pass<T, M, TC><<<grid, PASS_THREADS, smem, s>>>(a, pi);
+  k_pass<T, M, TC, PROJ><<<grid, PASS_THREADS, smem, s>>>(a, pi);
   return cudaGetLastError();
 }
 
 template <typename T, int M>
-static cudaError_t launch_pass_tm(const PassArgs& a, int pi, int grid, cudaStream_t s, bool dense) {
+static cudaError_t launch_pass_tm(const PassArgs& a, int pi, int grid, cudaStream_t s, bool dense, bool proj) {
   if constexpr (sizeof(T) == 4 && M == 12)
-    if (dense && a.dense_tc) return launch_pass_v<T, M, true>(a, pi, grid, s);
-  return launch_pass_v<T, M, false>(a, pi, grid, s);
+    if (dense && a.dense_tc)
+      return proj ? launch_pass_v<T, M, true, true>(a, pi, grid, s) : launch_pass_v<T, M, true, false>(a, pi, grid, s);
+  return proj ? launch_pass_v<T, M, false, true>(a, pi, grid, s) : launch_pass_v<T, M, false, false>(a, pi, grid, s);
 }
 
 // Resident CTAs per SM from the kernel's own resource counts.  The runtime's
@@ -191,29 +194,30 @@ static int blocks_per_sm(const cudaFuncAttributes& fa, size_t dyn_smem, int thre
 template <typename T, int M>
 static cudaError_t pass_attr_tm(int* per_sm) {
   const size_t smem = pass_smem<T, M>();
-  cudaError_t e = cudaFuncSetAttribute(k_pass<T, M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = cudaFuncSetAttribute(k_pass<T, M, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   cudaFuncAttributes fa{};
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, M, false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, M, false, false>);
   if (e == cudaSuccess) *per_sm = blocks_per_sm(fa, smem, PASS_THREADS);
   return e;
 }
 
-cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s, bool dense) {
+cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s, bool dense,
+                        bool proj) {
   if (dtype == SV_C64) {
     switch (m) {
-      case 10: return launch_pass_tm<float, 10>(a, pi, grid, s, dense);
-      case 11: return launch_pass_tm<float, 11>(a, pi, grid, s, dense);
-      case 12: return launch_pass_tm<float, 12>(a, pi, grid, s, dense);
-      case 13: return launch_pass_tm<float, 13>(a, pi, grid, s, dense);
-      case 14: return launch_pass_tm<float, 14>(a, pi, grid, s, dense);
+      case 10: return launch_pass_tm<float, 10>(a, pi, grid, s, dense, proj);
+      case 11: return launch_pass_tm<float, 11>(a, pi, grid, s, dense, proj);
+      case 12: return launch_pass_tm<float, 12>(a, pi, grid, s, dense, proj);
+      case 13: return launch_pass_tm<float, 13>(a, pi, grid, s, dense, proj);
+      case 14: return launch_pass_tm<float, 14>(a, pi, grid, s, dense, proj);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (m) {
-    case 10: return launch_pass_tm<double, 10>(a, pi, grid, s, dense);
-    case 11: return launch_pass_tm<double, 11>(a, pi, grid, s, dense);
-    case 12: return launch_pass_tm<double, 12>(a, pi, grid, s, dense);
-    case 13: return launch_pass_tm<double, 13>(a, pi, grid, s, dense);
+    case 10: return launch_pass_tm<double, 10>(a, pi, grid, s, dense, proj);
+    case 11: return launch_pass_tm<double, 11>(a, pi, grid, s, dense, proj);
+    case 12: return launch_pass_tm<double, 12>(a, pi, grid, s, dense, proj);
+    case 13: return launch_pass_tm<double, 13>(a, pi, grid, s, dense, proj);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -51,7 +51,8 @@ cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, c
 #endif
 #ifndef __CUDACC_RTC__
 // dense: the pass holds a dense four-qubit gate (its tensor-core variant runs when a.dense_tc)
-cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s, bool dense);
+// proj: the pass may start with a measurement projector pending (its copy-pipelined variant runs)
+cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, cudaStream_t s, bool dense, bool proj);
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm);

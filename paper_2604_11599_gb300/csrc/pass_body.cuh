@@ -661,6 +661,33 @@ __device__ __forceinline__ uint32_t group_base(const uint16_t* E, uint32_t g) {
   return b;
 }
 
+// The tiles of one unit of a pipelined sweep with a pending projector (bases
+// are spread over the non-tile qubits): dst is swept and stored, reading its
+// amplitudes from src; with outer flips xo the partner tile dst ^ xo becomes
+// zero.  act = false: the projector zeroes dst as well (nothing is copied or
+// swept).
+struct Unit {
+  uint64_t dst, src;
+  bool act;
+};
+static __device__ __forceinline__ Unit unit_tiles(uint64_t ub, uint64_t xo, uint64_t px, uint64_t pm, uint64_t pv,
+                                                  uint64_t omask, bool ident) {
+  Unit t;
+  const uint64_t pmo = pm & omask, pvo = pv & omask;
+  const bool ca = ident || (((ub ^ px) & pmo) == pvo);
+  if (!xo) {
+    t.dst = t.src = ub;
+    t.act = ca;
+    return t;
+  }
+  const uint64_t b = ub ^ xo;
+  const bool cb = ((b ^ px) & pmo) == pvo;
+  t.act = ca || cb;
+  t.dst = ca ? ub : (cb ? b : ub);
+  t.src = t.dst ^ xo;
+  return t;
+}
+
 // The measurement table is accumulated from the tile before the pass's scalar
 // factor f is multiplied in: |amp|^2 sums scale by |f|^2.
 static __device__ __forceinline__ void scale_table(double* ctab, double2 f) {
@@ -736,7 +763,9 @@ struct GenericStages {
 // TC: the kernel variant that may send dense four-qubit gates to the tensor
 // cores (launched only for passes that hold one: the mere presence of tcgen05
 // instructions in a kernel measured ~20% slower sweeps on GB300).
-template <typename T, int M, bool CTA, typename Stages = GenericStages, bool TC = false>
+// PROJ: the variant for passes that may start with a measurement projector
+// pending (it keeps the copy pipeline for them; see the tile loop).
+template <typename T, int M, bool CTA, typename Stages = GenericStages, bool TC = false, bool PROJ = false>
 __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassShared<T, TC>& sh, void* smem_tiles) {
   using V = typename CxT<T>::V;
   using Acc = T;  // per-thread |amp|^2 accumulation: FP32 for complex64, FP64 for complex128
@@ -875,27 +904,47 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     const uint32_t c0 = uint32_t(tid) >> vl;
     const uint32_t q0 = swz<T>((c0 << L) | woff);
 
-    // Identity projector: raw 16-byte asynchronous copies keep the next tile in
-    // flight while the current one is processed (two shared-memory buffers).
-    // Otherwise the tile is loaded synchronously with the projector applied.
-    const bool pipe = DB && ident;
+    // Tiles stream in by 16-byte asynchronous copies, the next tile in flight
+    // while the current one is processed (two shared-memory buffers), when no
+    // measurement projector is pending.  Otherwise the plain variant loads the
+    // tile synchronously with the projector applied on the way in, while the
+    // PROJ variant (launched for passes that may follow a measurement) keeps
+    // the copy pipeline: the copy reads the source of the projector's flip
+    // (a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv), and each thread then
+    // zeroes, scales and (complex64, flip of bit 0) swaps the vectors it
+    // copied.  Flips of qubits outside the tile (xo) pair tile t with t ^ xo in
+    // one unit: the tile that satisfies the projector is copied from its
+    // partner, and the partner becomes zero.  Tiles that the projector zeroes
+    // are neither copied nor swept.
+    const bool pipe = PROJ ? (DB && ((xo & ~pm) == 0)) : (DB && ident);
+    const bool upair = PROJ && pipe && pair;  // units are tile pairs
+    const uint64_t umask = upair ? (omask & ~(xo & (~xo + 1))) : omask;  // unit index bits
+    const uint64_t pxi = PROJ ? (px & tmask & (sizeof(T) == 4 ? ~1ull : ~0ull)) : 0;  // inner flip, granule-aligned
     int cur = 0;
-    // Tile bases advance by masked addition instead of a bit-by-bit deposit per tile.
-    const uint64_t sstep = pdep64(ustep, omask);
-    const uint64_t sahead = pdep64(uint64_t(NBUF - 1) * ustep, omask);
-    uint64_t bcur = pdep64(ustart, omask);
+    // Unit bases advance by masked addition instead of a bit-by-bit deposit per unit.
+    const uint64_t sstep = pdep64(ustep, umask);
+    const uint64_t sahead = pdep64(uint64_t(NBUF - 1) * ustep, umask);
+    uint64_t bcur = pdep64(ustart, umask);
     auto buffer = [&](int k) { return tile + size_t(k) * (size_t(1) << M); };
-    if (pipe) {  // prologue: the first NBUF - 1 tiles of this CTA, one commit group each
+    if (pipe) {  // prologue: the first NBUF - 1 units of this CTA, one commit group each
       for (int k = 0; k < NBUF - 1; ++k) {
         const uint64_t uk = ustart + uint64_t(k) * ustep;
         if (uk < nunits) {
-          const uint64_t bk = pdep64(uk, omask);
-          V* dst = buffer(k);
+          uint64_t src = pdep64(uk, umask);
+          bool go = true;
+          if constexpr (PROJ) {
+            const Unit Uk = unit_tiles(src, xo, px, pm, pv, omask, ident);
+            src = Uk.src;
+            go = Uk.act;
+          }
+          if (go) {
+            V* dst = buffer(k);
 #pragma unroll
-          for (int v = 0; v < NVT; ++v) {
-            const uint32_t ch = c0 + (uint32_t(v) << (VB - L));
-            cp_async16(dst + (q0 ^ swz<T>(uint32_t(v) << VB)),
-                       reinterpret_cast<const V*>(A.state) + (bk | schunk[ch] | woff));
+            for (int v = 0; v < NVT; ++v) {
+              const uint32_t ch = c0 + (uint32_t(v) << (VB - L));
+              cp_async16(dst + (q0 ^ swz<T>(uint32_t(v) << VB)),
+                         reinterpret_cast<const V*>(A.state) + ((src | schunk[ch] | woff) ^ pxi));
+            }
           }
         }
         cp_async_commit();
@@ -906,7 +955,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     for (uint64_t u = ustart; u < nunits; u += ustep) {
       uint64_t tl[2] = {u, 0};
       int cnt = 1;
-      if (pair) {
+      if (pair && !upair) {
         const uint64_t lo = u & ((1ull << hbit) - 1);
         const uint64_t t0 = ((u >> hbit) << (hbit + 1)) | lo;
         const uint64_t t1 = t0 ^ xt;
@@ -919,10 +968,45 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       for (int k2 = 0; k2 < cnt; ++k2) {
         V* tb;
         uint64_t base;
+        bool act = true;  // false: the projector zeroes this tile (PROJ variant)
         if (pipe) {
           base = bcur;
           tb = buffer(cur);
-          cp_async_wait<NBUF - 2>();  // this tile's group; the NBUF - 2 newer ones may still fly
+          cp_async_wait<NBUF - 2>();  // this unit's group; the NBUF - 2 newer ones may still fly
+          if constexpr (PROJ) {
+            if (!ident) {  // the projector, on the vectors this thread copied
+              const Unit U = unit_tiles(bcur, xo, px, pm, pv, omask, false);
+              base = U.dst;
+              act = U.act;
+#pragma unroll
+              for (int k = 0; k < NVT; ++k) {
+                const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+                const uint64_t gi = base | schunk[ch] | woff;
+                const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+                const uint64_t s0 = gi ^ px;
+                if constexpr (sizeof(T) == 4) {
+                  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                  if (act) {
+                    const float4 r = *reinterpret_cast<const float4*>(tb + p);
+                    const bool ok0 = (s0 & pm) == pv, ok1 = ((s0 ^ 1ull) & pm) == pv;
+                    const float2 e0 = make_float2(r.x, r.y), e1 = make_float2(r.z, r.w);
+                    const float2 x0 = (px & 1) ? e1 : e0, x1 = (px & 1) ? e0 : e1;
+                    q = make_float4(ok0 ? x0.x * sc : 0.f, ok0 ? x0.y * sc : 0.f, ok1 ? x1.x * sc : 0.f,
+                                    ok1 ? x1.y * sc : 0.f);
+                  }
+                  *reinterpret_cast<float4*>(tb + p) = q;
+                } else {
+                  V x = make_double2(0, 0);
+                  if (act && (s0 & pm) == pv) {
+                    x = tb[p];
+                    x.x *= sc;
+                    x.y *= sc;
+                  }
+                  tb[p] = x;
+                }
+              }
+            }
+          }
         } else {
           tb = tile;
           base = pair ? pdep64(tl[k2], omask) : bcur;
@@ -979,28 +1063,38 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         // tile, so its buffer can be refilled.  When the first stage keeps the
         // copies' warp bits, each warp reads only what its own lanes copied and
         // refills only what its own lanes stored: a warp barrier suffices.
-        if (pipe && any_gate && !sp.bar_in) __syncwarp();
+        if (pipe && any_gate && act && !sp.bar_in) __syncwarp();
         else __syncthreads();
-        if (pipe) {  // refill the buffer processed one iteration ago with the tile NBUF - 1 ahead
+        if (pipe) {  // refill the buffer processed one iteration ago with the unit NBUF - 1 ahead
           const uint64_t un = u + uint64_t(NBUF - 1) * ustep;
           if (un < nunits) {
-            const uint64_t bn = spread_add(bcur, sahead, omask);
-            V* nb = buffer((cur + NBUF - 1) % NBUF);
+            uint64_t src = spread_add(bcur, sahead, umask);
+            bool go = true;
+            if constexpr (PROJ) {
+              if (!ident) {
+                const Unit Un = unit_tiles(src, xo, px, pm, pv, omask, false);
+                src = Un.src;
+                go = Un.act;
+              }
+            }
+            if (go) {
+              V* nb = buffer((cur + NBUF - 1) % NBUF);
 #pragma unroll
-            for (int k = 0; k < NVT; ++k) {
-              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
-              cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
-                         reinterpret_cast<const V*>(A.state) + (bn | schunk[ch] | woff));
+              for (int k = 0; k < NVT; ++k) {
+                const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+                cp_async16(nb + (q0 ^ swz<T>(uint32_t(k) << VB)),
+                           reinterpret_cast<const V*>(A.state) + ((src | schunk[ch] | woff) ^ pxi));
+              }
             }
           }
           cp_async_commit();
         }
 
         // ---- gate stages
-        if (any_gate) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc);
+        if (any_gate && act) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc);
 
-        // ---- measurement-group table
-        if (needed) {
+        // ---- measurement-group table (a zeroed tile adds nothing)
+        if (needed && act) {
           Acc acc[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
@@ -1059,6 +1153,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
               __stcg(reinterpret_cast<double2*>(A.state) + gi, fscale ? cmul(fT, x) : x);
             }
           }
+          if (upair) {  // the unit's partner tile becomes zero (its data was read above)
+#pragma unroll
+            for (int k = 0; k < NVT; ++k) {
+              const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
+              const uint64_t gi = (base ^ xo) | schunk[ch] | woff;
+              if constexpr (sizeof(T) == 4)
+                __stcg(reinterpret_cast<float4*>(A.state) + (gi >> 1), make_float4(0.f, 0.f, 0.f, 0.f));
+              else
+                __stcg(reinterpret_cast<double2*>(A.state) + gi, make_double2(0, 0));
+            }
+          }
         }
         if (pipe) {
           // no barrier: the next iteration's barrier orders these reads before
@@ -1068,7 +1173,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           __syncthreads();
         }
       }
-      bcur = spread_add(bcur, sstep, omask);
+      bcur = spread_add(bcur, sstep, umask);
     }
     if (pipe) cp_async_wait<0>();
     if (needed && sp.kin == sp.gk) {  // the lanes' table slots, combined over warps in a fixed order

@@ -861,6 +861,23 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     b.emit_pass({}, tq, nullptr, true);
   }
 
+  // Which passes can start with a measurement projector pending: one is left
+  // by every pass whose scalar phase draws, and applied by the next pass that
+  // stores the state (surely if it holds an unconditional gate, or flushes).
+  {
+    bool pending = false;
+    for (DPass& d : P.passes) {
+      d.proj = pending ? 1 : 0;
+      bool draws = false, stores = d.flush != 0;
+      for (uint32_t c = 0; c < d.nc; ++c) {
+        const uint8_t k = P.scalars[d.c0 + c].kind;
+        draws = draws || k == S_MEASURE || k == S_RESET;
+      }
+      for (uint32_t g = 0; g < d.ng && !stores; ++g) stores = P.gates[d.g0 + g].flag < 0;
+      pending = draws || (pending && !stores);
+    }
+  }
+
   P.stats.records = n_ops;
   P.stats.unrolled_ops = n_gates + n_draws;
   P.stats.gates = n_gates;

@@ -225,7 +225,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
         const sv_status st = svj::launch(*jm, int(i), a, grid, s, err);
         if (st != SV_OK) return fail(st, err);
       } else {
-        SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s, P.passes[i].dense != 0));
+        SV_CUDA(svk::launch_pass(h->dtype, a, int(i), grid, P.m, s, P.passes[i].dense != 0, P.passes[i].proj != 0));
       }
       if (h->profiling) {
         SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));

@@ -150,6 +150,8 @@ struct DPass {
   uint8_t flush;          // 1: final pass that only applies a pending projector
   uint8_t bar_in;         // 1: block barrier between the tile copy and the first stage
   uint8_t dense;          // 1: the pass holds a dense four-qubit gate (OP_D16)
+  uint8_t proj;           // 1: a measurement projector may be pending when the pass starts
+  uint8_t pad[3];
   uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
   uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
   uint16_t red_R[REG_BITS];       // reduction stage: register-bit addresses
