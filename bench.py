@@ -213,13 +213,21 @@ def measure_forms(sv, torch):
         t0 = time.perf_counter()
         st.sample(c.ops, 1000)
         tps = time.perf_counter() - t0
+        lat = []  # per-shot latency of the plain path: one sv_run (creg read back) per shot
+        for shot in range(300):
+            t1 = time.perf_counter()
+            st.run(c.ops, seed=0, shot=shot)
+            lat.append(time.perf_counter() - t1)
+        lat.sort()
     with sv.Batch("c128") as b:
         p = b.add_program(c.ops, 5)
         b.run([p] * 1000, np.zeros(1000), np.arange(1000))
         t0 = time.perf_counter()
         b.run([p] * 1000, np.zeros(1000), np.arange(1000))
         tbs = time.perf_counter() - t0
-    out["plain_small_1000_shots"] = {"plain_path_shots_per_s": 1000 / tps, "batched_shots_per_s": 1000 / tbs}
+    out["plain_small_1000_shots"] = {"plain_path_shots_per_s": 1000 / tps, "batched_shots_per_s": 1000 / tbs,
+                                     "plain_shot_latency_p50_ms": 1000 * lat[len(lat) // 2],
+                                     "plain_shot_latency_p99_ms": 1000 * lat[int(0.99 * len(lat))]}
     # VQE: n=20 hardware-efficient ansatz, 320 parameters, 200 Pauli terms
     c = W.hea(20, 8)
     terms = W.heisenberg_fields(9, 20, 200)
