@@ -82,6 +82,28 @@ def circuit(n, dtype, kind="layered"):
     return workloads.layered(GEN_SEED.get((n, dtype), 5), n, layers=20)
 
 
+# FP64 operations the sweep kernels execute per amplitude for each IR gate (complex128):
+# factored RX / RY one FMA per component (4), one-qubit diagonals a complex multiply on
+# half the amplitudes (3), CX / X / SWAP register renames (0), other one-qubit gates a
+# 2x2 complex product (14), controlled ones the same on half (7), plus 6 per storing
+# pass for the pass factor.  Nominal GB300 FP64 rate: 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_ops_per_step(ops, n_passes, n):
+    from paper_2604_11599_gb300.ir import Gate, Kind
+
+    per = {Gate.RX: 4, Gate.RY: 4, Gate.RZ: 3, Gate.P: 3, Gate.S: 3, Gate.SDG: 3, Gate.T: 3, Gate.TDG: 3,
+           Gate.Z: 3, Gate.CX: 0, Gate.X: 0, Gate.SWAP: 0, Gate.CZ: 0, Gate.I: 0}
+    total = 0
+    for r in ops:
+        if int(r["kind"]) != int(Kind.GATE):
+            continue
+        g = Gate(int(r["gate"]))
+        total += per.get(g, 7 if g >= Gate.CX else 14)
+    return float(total + 6 * n_passes) * float(1 << n)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -343,9 +365,10 @@ def main():
     from paper_2604_11599_gb300 import build
 
     build.build()
-    from paper_2604_11599_gb300 import sv
+    from paper_2604_11599_gb300 import replicas, sv
 
     n, dtype = args.n, args.dtype
+    stream_id = replicas.stream_of(rank)  # ranks simulate independent trajectories
     c = circuit(n, dtype, args.circuit)
     st = sv.State(n, dtype)
     st.set_jit(not args.no_jit)
@@ -360,7 +383,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
-        st.launch(prog, seed=0, shot=1000 + i)
+        st.launch(prog, seed=0, stream_id=stream_id, shot=1000 + i)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -371,7 +394,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(args.steps):
-        st.launch(prog, seed=0, shot=i)
+        st.launch(prog, seed=0, stream_id=stream_id, shot=i)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
@@ -380,12 +403,8 @@ def main():
     prof = st.profile_read()
     st.profile(False)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = upd * world / (ms / 1000.0)
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    value = replicas.whole_job_rate(upd, ms / 1000.0, world)
 
     # end to end through the public API with host buffers, plan lowered + copied each step
     e2e = None
@@ -397,14 +416,10 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         for i in range(args.steps):
-            st.run(c.ops, seed=0, shot=i)  # waits for the classical register
-        dt = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+            st.run(c.ops, seed=0, stream_id=stream_id, shot=i)  # waits for the classical register
+        dt = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, dist, "cuda")
         st.set_cache(True)
-        e2e = {"value": upd * world / dt, "unit": UNIT,
+        e2e = {"value": replicas.whole_job_rate(upd, dt, world), "unit": UNIT,
                "h2d_bytes_per_step": int(stats["plan_bytes"]), "d2h_bytes_per_step": 8,
                "ms_per_step": dt * 1000.0}
 
@@ -415,8 +430,14 @@ def main():
                 "kernel": "sv_jit_passes (k_pass specialised)" if stats["specialised"] else "k_pass",
                 "peak_kind": f"of {kind}", "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
                 "avg_launch_ms": prof["ms"] / max(1, prof["launches"])}
-    if dtype == "c128":
-        roofline["note"] = "complex128 sweeps are FP64-ALU-bound on GB300"
+    if dtype == "c128":  # FP64-bound: the arithmetic the kernels execute against the FP64 rate
+        flops = fp64_ops_per_step(c.ops, stats["passes"], n)
+        tf = flops / (prof["ms"] / 1000.0) / 1e12 if prof["ms"] > 0 else 0.0
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": None, "kernel": roofline["kernel"],
+                    "peak_kind": "of nominal (GB300 FP64 1.25 TFLOP/s; 0.60 TFMA/s measured by a probe)",
+                    "fp64_ops_per_step": flops, "hbm_achieved_gbs": achieved,
+                    "hbm_frac_of_measured": achieved / peaks["hbm_gbs"]}
 
     forms = None
     if rank == 0 and not args.no_forms:
