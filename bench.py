@@ -266,6 +266,33 @@ def measure_forms(sv, torch):
         vqe[dt] = {"parameter_sets": sets, "gradient_sets_per_s": sets / dts, "seconds": dts}
         h.close()
     out["vqe_adjoint"] = vqe
+    # terminal sampling and Pauli-sum expectation on an n=28 complex64 state (one read of the
+    # state per sampling call; one per group of terms that share an X mask)
+    peaks, kind = measured_peaks()
+    n_s = 28
+    c = W.layered(3, n_s, layers=2)
+    terms = W.heisenberg_fields(9, n_s, 10 * n_s)
+    groups = len(set(int(x) for x in terms["x_mask"]))
+    sbytes = float(1 << n_s) * 8
+    with sv.State(n_s, "c64") as st:
+        st.set_jit(True)
+        st.run(c.ops)
+        st.sample_state(1 << 16)
+        st.expval(terms)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.sample_state(1 << 20, seed=1)
+        ts = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        st.expval(terms)
+        te = time.perf_counter() - t0
+    out["sample_expval"] = {
+        "state": f"n={n_s} complex64 after 2 layered layers",
+        "sampling": {"shots": 1 << 20, "seconds": ts, "shots_per_s": (1 << 20) / ts,
+                     "state_reads_gbs": sbytes / ts / 1e9, "hbm_frac": sbytes / ts / 1e9 / peaks["hbm_gbs"]},
+        "expval": {"terms": int(len(terms)), "x_groups": groups, "seconds": te,
+                   "group_reads_gbs": groups * sbytes / te / 1e9,
+                   "hbm_frac": groups * sbytes / te / 1e9 / peaks["hbm_gbs"], "hbm_peak_kind": f"of {kind}"}}
     # dense four-qubit unitaries, n=30 complex64: tensor cores against the FP32 pipes
     from paper_2604_11599_gb300.ir import Kind
 
@@ -274,7 +301,6 @@ def measure_forms(sv, torch):
     dense = {"workload": "n=30 complex64, 6 layers of Haar-random dense 4-qubit unitaries on a random partition "
                          "(7 per layer) + RX/RY/RZ on the 2 qubits left over; 1 trajectory per step",
              "dense_gates_per_step": n_dense}
-    peaks, kind = measured_peaks()
     with sv.State(30, "c64") as st:
         st.set_jit(True)
         st.set_dense_pool(c.pool)

@@ -51,7 +51,8 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
-    << "                                             TcCtx& tc) {\n"
+    << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
+    << "                                             const bool fscale) {\n"
     << "    using V = typename CxT<T>::V;\n"
     << "    const int tid = threadIdx.x;\n";
   for (uint32_t si = 0; si < d.ns; ++si) {
@@ -85,7 +86,27 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (gt.flag >= 0) o << "      if (sgk[" << g << "] & SGK_ON) " << call.str() << ";\n";
       else o << "      " << call.str() << ";\n";
     }
-    if (pairs) {
+    if (d.direct && si + 1 == d.ns) {
+      // direct store: register j of group grp is state index base ^ G(grp) ^ goff[j],
+      // G and goff XORs of the qubits behind the group and register bits
+      uint64_t goff[16];
+      goff[0] = 0;
+      for (int j = 1; j < 16; ++j)
+        goff[j] = goff[j & (j - 1)] ^ (1ull << d.tq[st.Rb[__builtin_ctz(unsigned(j))]]);
+      o << "      uint64_t g = base;\n";
+      for (int k = 0; k < GB; ++k) o << "      if (grp & " << (1 << k) << ") g |= " << (1ull << d.tq[st.Eb[k]]) << "ull;\n";
+      o << "      if (fscale) {\n#pragma unroll\n        for (int j = 0; j < 16; ++j) a[j] = cmul(fT, a[j]);\n      }\n";
+      // the group's and the registers' qubits are distinct, so g ^ goff[j] = g + goff[j]:
+      // one base pointer and constant offsets
+      o << "      V* const gp = reinterpret_cast<V*>(A.state) + g;\n";
+      if (pairs) {
+        for (int j = 0; j < 16; j += 2)
+          o << "      __stcg(reinterpret_cast<float4*>(gp + " << goff[j] << "ll), make_float4(a[" << j << "].x, a[" << j
+            << "].y, a[" << j + 1 << "].x, a[" << j + 1 << "].y));\n";
+      } else {
+        for (int j = 0; j < 16; ++j) o << "      __stcg(gp + " << goff[j] << "ll, a[" << j << "]);\n";
+      }
+    } else if (pairs) {
       for (int j = 0; j < 16; j += 2)
         o << "      *reinterpret_cast<float4*>(tb + (b ^ " << off[j] << "u)) = make_float4(a[" << j << "].x, a[" << j
           << "].y, a[" << j + 1 << "].x, a[" << j + 1 << "].y);\n";
@@ -171,13 +192,15 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   for (size_t pi = p0; pi < p1; ++pi)
     if (P.passes[pi].ns) emit_stages(o, P, pi);
   o << "struct JitStages {\n"
+    << "  static constexpr bool kDirect = true;  // direct passes store from the last stage\n"
     << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
-    << "                                             TcCtx& tc) {\n"
+    << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
+    << "                                             const bool fscale) {\n"
     << "    switch (A.pass) {\n";
   for (size_t pi = p0; pi < p1; ++pi)
-    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc); break;\n";
+    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc, base, fT, fscale); break;\n";
   o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
   const char* T = c64 ? "float" : "double";
   // kernel variants: tensor cores only where a pass of the chunk holds a dense

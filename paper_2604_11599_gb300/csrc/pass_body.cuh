@@ -729,9 +729,11 @@ __device__ __forceinline__ TcShared* tc_shared(PassShared<T, TC>& sh) {
 // Data-driven register stages: every stage reads its register / group bit
 // addresses and gate records from the plan at run time.
 struct GenericStages {
+  static constexpr bool kDirect = false;  // the tile is always stored by the pass's store phase
   template <typename T, int M, bool TC>
   static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,
-                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb, TcCtx& tc) {
+                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb, TcCtx& tc,
+                                             const uint64_t, const typename CxT<T>::V, const bool) {
     using V = typename CxT<T>::V;
     constexpr int GB = M - REG_BITS;
     constexpr int NGRP = 1 << GB;
@@ -754,7 +756,9 @@ struct GenericStages {
 #pragma unroll
         for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
       }
-      if (st.bar) __syncthreads();
+      // a direct pass relaxes the barrier after its last stage for kernels that
+      // store from registers; this one stores from shared memory
+      if (st.bar || (sp.direct && si + 1 == sp.ns)) __syncthreads();
       else __syncwarp();
     }
   }
@@ -1091,7 +1095,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         }
 
         // ---- gate stages
-        if (any_gate && act) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc);
+        if (any_gate && act) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc, base, fT, fscale);
+        // the last stage stored the tile itself (specialised kernels, direct passes)
+        const bool stored = Stages::kDirect && sp.direct && any_gate && act;
 
         // ---- measurement-group table (a zeroed tile adds nothing)
         if (needed && act) {
@@ -1137,7 +1143,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         // ---- store
         if (do_store) {
 #pragma unroll
-          for (int k = 0; k < NVT; ++k) {
+          for (int k = 0; k < NVT && !stored; ++k) {
             const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
             const uint64_t gi = base | schunk[ch] | woff;
             const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);

@@ -409,9 +409,24 @@ struct Builder {
       const uint32_t fm = all & ~rm;
       const bool can_be_clean = lanes_ok(fm, pairs);
 
+      // Direct store (the last stage of a pass without a measurement table
+      // writes its registers to the state itself, specialised kernels): every
+      // store instruction must write whole 128-byte lines (scattered 32-byte
+      // sectors measured slower than the pass's own store phase).  The tile bits
+      // `dwant` below a line (bits 0..2 + B, less register bit 0 when it holds
+      // complex64 amplitude pairs) go to the first lanes; the warp bits avoid them.
+      const bool dlast = !adjoint && si == K - 1 && !(seg && seg->has_group);
+      std::vector<int> dwant;
+      if (dlast) {  // the first lanes cover a 128-byte line: tile bits below 3 + B, minus register bit 0
+        for (int b = (B == 1 && (rm & 1u)) ? 1 : 0; b < 3 + B; ++b) dwant.push_back(b);
+      }
+      bool dpossible = dlast;
+      for (int b : dwant) dpossible = dpossible && !((rm >> b) & 1u);
+      uint32_t dmask = 0;
+      for (int b : dwant) dmask |= 1u << b;
       int W[3] = {-1, -1, -1};
       if (warp_local) {
-        if (!(rm & wcm) && (!can_be_clean || lanes_ok(fm & ~wcm, pairs))) {
+        if (!(rm & wcm) && (!can_be_clean || lanes_ok(fm & ~wcm, pairs)) && !(dpossible && (wcm & dmask))) {
           for (int i = 0; i < 3; ++i) W[i] = Wcur[i];
           bar_before[size_t(si)] = 0;
         } else {
@@ -428,6 +443,7 @@ struct Builder {
               for (int c = b + 1; c < m; ++c) {
                 const uint32_t tm = (1u << a) | (1u << b) | (1u << c);
                 if ((tm & rm) || (B == 1 && (tm & 1u))) continue;
+                if (dpossible && (tm & dmask)) continue;
                 if (can_be_clean && !lanes_ok(fm & ~tm, pairs)) continue;
                 const int r = std::min(run[a], std::min(run[b], run[c]));
                 const int score = 8 * r + (si + 1 + r == K && tm == w0m ? 4 : 0) + popc(tm & w0m);
@@ -456,6 +472,7 @@ struct Builder {
       for (int j = 0; j < MAX_TILE_BITS; ++j) rpos[j] = -1;
       for (int r = 0; r < reg_bits; ++r) {
         st.R[r] = uint16_t(tile_swizzle(1u << reg[size_t(r)], B));
+        st.Rb[r] = uint8_t(reg[size_t(r)]);
         rpos[reg[size_t(r)]] = r;
       }
       std::vector<int> freeb;
@@ -471,7 +488,22 @@ struct Builder {
       } else {
         for (size_t k = 0; k < freeb.size(); ++k) ebits.push_back(thr[k]);
       }
-      for (int k = 0; k < m - reg_bits; ++k) st.E[k] = uint16_t(tile_swizzle(1u << ebits[size_t(k)], B));
+      if (dpossible) {
+        const auto lanes_end = ebits.begin() + std::min<long>(5, long(ebits.size()));
+        bool ok = true;
+        for (int b : dwant) ok = ok && std::find(ebits.begin(), lanes_end, b) != lanes_end;
+        if (ok) {  // those tile bits first, in order; the lane order is otherwise kept
+          for (size_t i = 0; i < dwant.size(); ++i) {
+            auto it = std::find(ebits.begin() + long(i), lanes_end, dwant[i]);
+            std::rotate(ebits.begin() + long(i), it, it + 1);
+          }
+          ps.direct = 1;
+        }
+      }
+      for (int k = 0; k < m - reg_bits; ++k) {
+        st.E[k] = uint16_t(tile_swizzle(1u << ebits[size_t(k)], B));
+        st.Eb[k] = uint8_t(ebits[size_t(k)]);
+      }
       const std::vector<int>& sg = stG[size_t(si)];
       for (int idx : sg) {
         const Item& it = items[idx];
@@ -544,11 +576,15 @@ struct Builder {
     }
     // barrier flags: a block barrier wherever the warp bits change; after the
     // last stage unless it ends on the copies' warp bits without a group table
-    const bool tail_local = warp_local && K > 0 && Wcur[0] == W0[0] && Wcur[1] == W0[1] && Wcur[2] == W0[2] &&
-                            !(seg && seg->has_group);
-    bar_before[size_t(K)] = tail_local ? 0 : 1;
+    const bool end_w0 = warp_local && K > 0 && Wcur[0] == W0[0] && Wcur[1] == W0[1] && Wcur[2] == W0[2];
+    const bool tail_local = end_w0 && !(seg && seg->has_group);
+    // a direct store leaves no shared-memory reader after the last stage; the
+    // next tile's refill of this buffer then needs the last stage's warps to
+    // own what they refill, or a block barrier when the tile lands
+    bar_before[size_t(K)] = (tail_local || (ps.direct && warp_local)) ? 0 : 1;
     for (int si = 0; si < K; ++si) P.stages[ps.s0 + size_t(si)].bar = bar_before[size_t(si) + 1];
     ps.bar_in = K > 0 ? bar_before[0] : 1;
+    if (ps.direct && !end_w0) ps.bar_in = 1;
     ps.ng = uint32_t(P.gates.size() - ps.g0);
     ps.ns = uint32_t(P.stages.size() - ps.s0);
     ps.nmat = mat;
@@ -743,6 +779,8 @@ int check_barriers(const Plan& P, uint64_t* warp_syncs, uint64_t* block_syncs) {
     else {
       ++*warp_syncs;
       bad += !same(copy_own, own[0]);
+      // direct store: the refill of the previous tile's buffer follows its last stage
+      if (ps.direct) bad += !same(own[ps.ns - 1], copy_own);
     }
     for (uint32_t si = 0; si < ps.ns; ++si) {
       const DStage& st = P.stages[ps.s0 + si];
@@ -752,7 +790,8 @@ int check_barriers(const Plan& P, uint64_t* warp_syncs, uint64_t* block_syncs) {
       }
       ++*warp_syncs;
       if (si + 1 < ps.ns) bad += !same(own[si], own[si + 1]);
-      else bad += !same(own[si], copy_own) || ps.gk != 0;
+      else if (!ps.direct) bad += !same(own[si], copy_own) || ps.gk != 0;
+      else bad += ps.gk != 0;
     }
   }
   return bad;

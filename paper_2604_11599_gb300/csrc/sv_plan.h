@@ -106,6 +106,8 @@ struct DStage {
   uint16_t R[REG_BITS];
   uint16_t E[MAX_TILE_BITS - REG_BITS];  // E[5..7] select the warp (tiles of >= 12 bits)
   uint16_t bar;                          // 1: block barrier after the stage, 0: warp barrier suffices
+  uint8_t Rb[REG_BITS];                  // the tile bits behind R and E (unswizzled)
+  uint8_t Eb[MAX_TILE_BITS - REG_BITS];
 };
 
 // Shared-memory layout of a tile, in 16-byte granules (one complex128 or two
@@ -151,7 +153,8 @@ struct DPass {
   uint8_t bar_in;         // 1: block barrier between the tile copy and the first stage
   uint8_t dense;          // 1: the pass holds a dense four-qubit gate (OP_D16)
   uint8_t proj;           // 1: a measurement projector may be pending when the pass starts
-  uint8_t pad[3];
+  uint8_t direct;         // 1: specialised kernels store the tile from the last stage's registers
+  uint8_t pad[2];
   uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
   uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
   uint16_t red_R[REG_BITS];       // reduction stage: register-bit addresses

@@ -144,12 +144,15 @@ def test_dense4_tensor_cores_in_dynamic_programs(svmod, orc):
 
 
 # --------------------------------------------------------------------------- dynamic circuits
+@pytest.mark.parametrize("jit", [False, True])
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n", [2, 4, 6, 9, 13, 16])
-def test_random_dynamic_programs(svmod, orc, dtype, n):
-    """Measures, resets, nested if/else on 1-3 bit predicates, loops, dense gates."""
+def test_random_dynamic_programs(svmod, orc, dtype, n, jit):
+    """Measures, resets, nested if/else on 1-3 bit predicates, loops, dense gates
+    (generic and per-program specialised kernels)."""
     stats = {}
     with svmod.State(n, dtype) as st:
+        st.set_jit(jit)
         for seed in range(6):
             c = W.random_dynamic(1000 * n + seed, n, n_ops=70, dense_k=min(n, 2))
             st.set_dense_pool(c.pool)
@@ -170,12 +173,15 @@ def test_plain_small_config_records(svmod, orc):
     assert stats.get("forced", 0) == 0
 
 
+@pytest.mark.parametrize("jit", [False, True])
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("n", [12, 18, 21])
-def test_layered_config_small_sizes(svmod, orc, dtype, n):
-    """The layered measure/reset/cond workload at sizes the oracle runs in seconds."""
+def test_layered_config_small_sizes(svmod, orc, dtype, n, jit):
+    """The layered measure/reset/cond workload at sizes the oracle runs in seconds
+    (generic and per-program specialised kernels)."""
     c = W.layered(2, n, layers=20 if n <= 18 else 8)
     with svmod.State(n, dtype) as st:
+        st.set_jit(jit)
         for shot in range(2):
             compare_run(st, orc, c.ops, n, dtype, seed=0, shot=shot)
 
