@@ -488,7 +488,7 @@ def main():
                        "compile_seconds": round(stats["compile_seconds"], 2),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (2 + stats["passes"]), "clocks": clk, "forms": forms,
+            "gpu_launches": args.steps * stats["kernels_per_run"], "clocks": clk, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     st.close()

@@ -128,6 +128,8 @@ typedef struct sv_program_stats {
                               copy and after each stage                      */
   uint64_t warp_barriers;  /* the same steps where a warp barrier suffices (every warp keeps
                               to its own amplitudes across the step; checked at lowering)  */
+  uint64_t kernels_per_run; /* kernel launches of one sv_launch: matrix preparation, a separate
+                               |0...0> sweep unless the first pass generates it, the passes */
 } sv_program_stats;
 
 #ifndef __CUDACC_RTC__ /* device code compiled at run time needs the types above only */

@@ -24,6 +24,7 @@ struct PassArgs {
   int n;             // simulated qubits
   int pass;          // pass index (specialised kernels select their stage program by it)
   int dense_tc;      // 1: dense four-qubit gates of complex64 2^12-amplitude tiles on the tensor cores
+  int gen_init;      // 1: this launch is the program's first pass and generates |0...0> instead of loading it
 };
 
 struct PrepArgs {

@@ -920,6 +920,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     // one unit: the tile that satisfies the projector is copied from its
     // partner, and the partner becomes zero.  Tiles that the projector zeroes
     // are neither copied nor swept.
+    const bool gen = PROJ && A.gen_init != 0;  // (no projector is pending at the first pass)
     const bool pipe = PROJ ? (DB && ((xo & ~pm) == 0)) : (DB && ident);
     const bool upair = PROJ && pipe && pair;  // units are tile pairs
     const uint64_t umask = upair ? (omask & ~(xo & (~xo + 1))) : omask;  // unit index bits
@@ -939,7 +940,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           if constexpr (PROJ) {
             const Unit Uk = unit_tiles(src, xo, px, pm, pv, omask, ident);
             src = Uk.src;
-            go = Uk.act;
+            go = Uk.act && !gen;
           }
           if (go) {
             V* dst = buffer(k);
@@ -978,7 +979,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           tb = buffer(cur);
           cp_async_wait<NBUF - 2>();  // this unit's group; the NBUF - 2 newer ones may still fly
           if constexpr (PROJ) {
-            if (!ident) {  // the projector, on the vectors this thread copied
+            if (gen) {  // the first pass: |0...0> in the tile holding index 0, zeros elsewhere
+              act = base == 0;
+#pragma unroll
+              for (int k = 0; k < NVT; ++k) {
+                const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
+                const bool one = act && tid == 0 && k == 0;  // local index 0: thread 0's first vector
+                if constexpr (sizeof(T) == 4)
+                  *reinterpret_cast<float4*>(tb + p) = make_float4(one ? 1.f : 0.f, 0.f, 0.f, 0.f);
+                else
+                  tb[p] = make_double2(one ? 1.0 : 0.0, 0.0);
+              }
+            } else if (!ident) {  // the projector, on the vectors this thread copied
               const Unit U = unit_tiles(bcur, xo, px, pm, pv, omask, false);
               base = U.dst;
               act = U.act;
@@ -1024,7 +1036,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             if constexpr (sizeof(T) == 4) {
               const float4* gs = reinterpret_cast<const float4*>(A.state);
               float2 x0, x1;
-              if (zero_tile) {
+              if (gen) {  // the first pass generates |0...0>
+                x0 = make_float2(gi == 0 ? 1.f : 0.f, 0.f);
+                x1 = make_float2(0.f, 0.f);
+              } else if (zero_tile) {
                 x0 = x1 = make_float2(0.f, 0.f);
               } else if (ident) {
                 const float4 q = __ldcg(gs + (gi >> 1));
@@ -1045,7 +1060,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             } else {
               const double2* gs = reinterpret_cast<const double2*>(A.state);
               double2 x;
-              if (zero_tile) {
+              if (gen) {
+                x = make_double2(gi == 0 ? 1.0 : 0.0, 0.0);
+              } else if (zero_tile) {
                 x = make_double2(0, 0);
               } else if (ident) {
                 x = __ldcg(gs + gi);
@@ -1075,7 +1092,9 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             uint64_t src = spread_add(bcur, sahead, umask);
             bool go = true;
             if constexpr (PROJ) {
-              if (!ident) {
+              if (gen) {
+                go = false;
+              } else if (!ident) {
                 const Unit Un = unit_tiles(src, xo, px, pm, pv, omask, false);
                 src = Un.src;
                 go = Un.act;

@@ -915,8 +915,22 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
       for (uint32_t g = 0; g < d.ng && !stores; ++g) stores = P.gates[d.g0 + g].flag < 0;
       pending = draws || (pending && !stores);
     }
+    // The first pass generates the initial state when it surely stores (an
+    // unconditional gate): the tile holding index 0 starts as |0...0>, every
+    // other tile is zero before and after the pass.  It runs as the variant
+    // that handles per-tile zeroing.
+    if (!P.passes.empty()) {
+      DPass& d = P.passes[0];
+      bool stores = false;
+      for (uint32_t g = 0; g < d.ng && !stores; ++g) stores = P.gates[d.g0 + g].flag < 0;
+      if (stores && d.ns > 0) {
+        P.gen_init = true;
+        d.proj = 1;
+      }
+    }
   }
 
+  P.stats.kernels_per_run = 1 + (P.gen_init ? 0 : 1) + P.passes.size();
   P.stats.records = n_ops;
   P.stats.unrolled_ops = n_gates + n_draws;
   P.stats.gates = n_gates;

@@ -186,7 +186,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
   pa.stream = stream_id;
   pa.shot = shot;
   SV_CUDA(svk::launch_prep(h->dtype, pa, s));
-  SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
+  if (!P.gen_init) SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
   if (h->use_jit && !p->jit_tried) {
     p->jit_tried = true;
     std::string err;
@@ -212,6 +212,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
     a.dense_tc = h->dense_tc ? 1 : 0;
     const double sbytes = double(1ull << h->n_int) * double(h->amp_bytes);
     for (size_t i = 0; i < P.passes.size(); ++i) {
+      a.gen_init = (P.gen_init && i == 0) ? 1 : 0;
       if (h->profiling) {
         while (h->events.size() < h->ev_used + 2) {
           cudaEvent_t e;
@@ -231,7 +232,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
         SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));
         h->ev_used += 2;
         const svp::DPass& d = P.passes[i];
-        h->prof_bytes += (d.ng > 0 || d.flush) ? 2 * sbytes : sbytes;
+        h->prof_bytes += a.gen_init ? sbytes : ((d.ng > 0 || d.flush) ? 2 * sbytes : sbytes);  // generated: write only
       }
     }
   }

@@ -41,7 +41,7 @@ class ProgramStats(C.Structure):
                 ("draws", C.c_uint64), ("passes", C.c_uint64), ("stages", C.c_uint64),
                 ("flags", C.c_uint64), ("tile_bits", C.c_int32), ("low_bits", C.c_int32),
                 ("plan_bytes", C.c_uint64), ("specialised", C.c_int32), ("compile_seconds", C.c_double),
-                ("block_barriers", C.c_uint64), ("warp_barriers", C.c_uint64)]
+                ("block_barriers", C.c_uint64), ("warp_barriers", C.c_uint64), ("kernels_per_run", C.c_uint64)]
 
 
 _lib = None
