@@ -52,7 +52,7 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
     << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
-    << "                                             const bool fscale) {\n"
+    << "                                             const bool fscale, const ProjFold& pj) {\n"
     << "    using V = typename CxT<T>::V;\n"
     << "    const int tid = threadIdx.x;\n";
   for (uint32_t si = 0; si < d.ns; ++si) {
@@ -73,6 +73,25 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
           << "] = make_float2(q.x, q.y); a[" << j + 1 << "] = make_float2(q.z, q.w); }\n";
     } else {
       for (int j = 0; j < 16; ++j) o << "      a[" << j << "] = tb[b ^ " << off[j] << "u];\n";
+    }
+    if (d.proj && si == 0) {
+      // the pending projector, on the loaded amplitudes: register j of group grp is
+      // tile index li(grp) ^ loff[j]; kept iff ((t ^ px) & pm) == pv, scaled by ps
+      uint32_t loff[16];
+      loff[0] = 0;
+      for (int j = 1; j < 16; ++j) loff[j] = loff[j & (j - 1)] ^ (1u << st.Rb[__builtin_ctz(unsigned(j))]);
+      o << "      if (pj.on) {\n        uint32_t li = 0;\n";
+      for (int k = 0; k < GB; ++k) o << "        if (grp & " << (1 << k) << ") li |= " << (1u << st.Eb[k]) << "u;\n";
+      if (P.dtype == SV_C64 && st.Rb[0] == 0) {  // amplitude pairs in registers: a flip of tile bit 0 swaps them
+        o << "        if (pj.swap0) {\n";
+        for (int j = 0; j < 16; j += 2) o << "          { const V t = a[" << j << "]; a[" << j << "] = a[" << j + 1 << "]; a[" << j + 1 << "] = t; }\n";
+        o << "        }\n";
+      }
+      o << "        const auto ps = decltype(a[0].x)(pj.ps);\n";
+      for (int j = 0; j < 16; ++j)
+        o << "        a[" << j << "] = (((li ^ " << loff[j] << "u ^ pj.px) & pj.pm) == pj.pv) ? mkc(a[" << j << "].x * ps, a["
+          << j << "].y * ps) : mkc(decltype(ps)(0), decltype(ps)(0));\n";
+      o << "      }\n";
     }
     for (uint32_t g = st.g0; g < uint32_t(st.g0) + st.ng; ++g) {
       const svp::DGate& gt = P.gates[d.g0 + g];
@@ -192,15 +211,16 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   for (size_t pi = p0; pi < p1; ++pi)
     if (P.passes[pi].ns) emit_stages(o, P, pi);
   o << "struct JitStages {\n"
-    << "  static constexpr bool kDirect = true;  // direct passes store from the last stage\n"
+    << "  static constexpr bool kDirect = true;    // direct passes store from the last stage\n"
+    << "  static constexpr bool kFoldProj = true;  // the first stage applies a pending projector\n"
     << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
     << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
-    << "                                             const bool fscale) {\n"
+    << "                                             const bool fscale, const ProjFold& pj) {\n"
     << "    switch (A.pass) {\n";
   for (size_t pi = p0; pi < p1; ++pi)
-    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc, base, fT, fscale); break;\n";
+    if (P.passes[pi].ns) o << "      case " << pi << ": JS" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc, base, fT, fscale, pj); break;\n";
   o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
   const char* T = c64 ? "float" : "double";
   // kernel variants: tensor cores only where a pass of the chunk holds a dense

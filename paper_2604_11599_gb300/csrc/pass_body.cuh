@@ -721,6 +721,18 @@ __device__ __forceinline__ TcShared* tc_shared(PassShared<T, TC>& sh) {
   else return nullptr;
 }
 
+// The pending projector in tile-local bits, for kernels whose first stage
+// applies it to the amplitudes it loads (instead of a separate in-place pass
+// over the copied tile).  The copy has already applied the flip's bits other
+// than tile bit 0; swap0: the flip includes tile bit 0 (complex64 amplitude
+// pairs swap in registers).
+struct ProjFold {
+  bool on;
+  uint32_t pm, pv, px;  // tile-local: bit b <-> qubit tq[b]
+  bool swap0;
+  double ps;
+};
+
 // One pass over the state.  GRID mode (CTA = false): the tiles are shared by
 // all CTAs of the launch and the last CTA to finish reduces the group table
 // and runs the scalar phase.  CTA mode (CTA = true): the calling CTA owns the
@@ -729,11 +741,13 @@ __device__ __forceinline__ TcShared* tc_shared(PassShared<T, TC>& sh) {
 // Data-driven register stages: every stage reads its register / group bit
 // addresses and gate records from the plan at run time.
 struct GenericStages {
-  static constexpr bool kDirect = false;  // the tile is always stored by the pass's store phase
+  static constexpr bool kDirect = false;    // the tile is always stored by the pass's store phase
+  static constexpr bool kFoldProj = false;  // a pending projector is applied to the copied tile
   template <typename T, int M, bool TC>
   static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,
                                              const typename CxT<T>::V* smat, typename CxT<T>::V* tb, TcCtx& tc,
-                                             const uint64_t, const typename CxT<T>::V, const bool) {
+                                             const uint64_t, const typename CxT<T>::V, const bool,
+                                             const ProjFold&) {
     using V = typename CxT<T>::V;
     constexpr int GB = M - REG_BITS;
     constexpr int NGRP = 1 << GB;
@@ -921,7 +935,22 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     // partner, and the partner becomes zero.  Tiles that the projector zeroes
     // are neither copied nor swept.
     const bool gen = PROJ && A.gen_init != 0;  // (no projector is pending at the first pass)
+    // specialised kernels fold the projector into the first stage when it runs
+    // (gates active, a first stage exists; a flip of tile bit 0 needs pairs in it)
+    ProjFold pjf{false, 0u, 0u, 0u, false, ps};
+    if constexpr (PROJ && Stages::kFoldProj) {
+      if (!ident && !gen && any_gate && sp.ns > 0) {
+        for (int b = 0; b < M; ++b) {
+          pjf.pm |= uint32_t((pm >> sp.tq[b]) & 1) << b;
+          pjf.pv |= uint32_t((pv >> sp.tq[b]) & 1) << b;
+          pjf.px |= uint32_t((px >> sp.tq[b]) & 1) << b;
+        }
+        pjf.swap0 = sizeof(T) == 4 && (pjf.px & 1u);
+        pjf.on = !pjf.swap0 || A.stages[sp.s0].R[0] == 1;
+      }
+    }
     const bool pipe = PROJ ? (DB && ((xo & ~pm) == 0)) : (DB && ident);
+    pjf.on = pjf.on && pipe;  // the synchronous load applies the projector itself
     const bool upair = PROJ && pipe && pair;  // units are tile pairs
     const uint64_t umask = upair ? (omask & ~(xo & (~xo + 1))) : omask;  // unit index bits
     const uint64_t pxi = PROJ ? (px & tmask & (sizeof(T) == 4 ? ~1ull : ~0ull)) : 0;  // inner flip, granule-aligned
@@ -995,7 +1024,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
               base = U.dst;
               act = U.act;
 #pragma unroll
-              for (int k = 0; k < NVT; ++k) {
+              for (int k = 0; k < NVT && !(pjf.on && act); ++k) {  // (a folding first stage applies it)
                 const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
                 const uint64_t gi = base | schunk[ch] | woff;
                 const uint32_t p = q0 ^ swz<T>(uint32_t(k) << VB);
@@ -1114,7 +1143,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         }
 
         // ---- gate stages
-        if (any_gate && act) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc, base, fT, fscale);
+        if (any_gate && act) Stages::template run<T, M, TC && !CTA>(A, sp, sgk, smat, tb, tc, base, fT, fscale, pjf);
         // the last stage stored the tile itself (specialised kernels, direct passes)
         const bool stored = Stages::kDirect && sp.direct && any_gate && act;
 
