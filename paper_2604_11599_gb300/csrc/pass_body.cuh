@@ -848,9 +848,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
         if ((c >> k) & 1) o |= 1ull << sp.tq[L + k];
       schunk[c] = o;
     }
-    // Dense four-qubit gates on the tensor cores: this CTA takes 64 columns of
-    // tensor memory (two 128 x 32 FP32 accumulators) and an mbarrier for the
-    // MMA completions, and gives both back after the tile loop.
+    // Dense four-qubit gates on the tensor cores: this CTA takes 256 columns of
+    // tensor memory (the A rows and two 128 x 32 FP32 accumulators, dev_tc.cuh)
+    // and an mbarrier for the MMA completions, and gives both back after the
+    // tile loop; the B operand of each dense gate is built once, here.
     if constexpr (TC && sizeof(T) == 4 && M == 12 && !CTA) tc.on = A.dense_tc != 0 && sp.dense != 0 && any_gate;
     if (tc.on) {
       if (warp == 0) {
