@@ -222,51 +222,6 @@ cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, c
   }
 }
 
-// The factors carried between passes: each thread multiplies the factors of
-// its passes' factored gates (all unconditional in deferring passes), then one
-// thread runs the prefix product in pass order.
-template <typename T>
-__global__ void k_factors(const DPass* passes, const DGate* gates, const void* mats, int np, double2* fac) {
-  using V = typename CxT<T>::V;
-  const V* m = reinterpret_cast<const V*>(mats);
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    const DPass d = passes[p];
-    double fr = 1.0, fi = 0.0;
-    for (uint32_t g = 0; g < d.ng; ++g) {
-      const DGate gt = gates[d.g0 + g];
-      if (gt.op != OP_RXF && gt.op != OP_RYF && gt.op != OP_DZ) continue;
-      const V f = m[d.mat0 + gt.mat + 1];
-      const double r = fr * double(f.x) - fi * double(f.y);
-      fi = fr * double(f.y) + fi * double(f.x);
-      fr = r;
-    }
-    fac[p] = make_double2(fr, fi);
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double Fr = 1.0, Fi = 0.0;
-  for (int p = 0; p < np; ++p) {
-    const double2 f = fac[p];
-    const uint8_t cls = passes[p].fclass;
-    fac[p] = make_double2(Fr, Fi);
-    if (cls == 1) {
-      const double r = Fr * f.x - Fi * f.y;
-      Fi = Fr * f.y + Fi * f.x;
-      Fr = r;
-    } else if (cls == 2) {
-      Fr = 1.0;
-      Fi = 0.0;
-    }
-  }
-}
-
-cudaError_t launch_factors(int dtype, const DPass* passes, const DGate* gates, const void* mats, int np,
-                           double2* fac, cudaStream_t s) {
-  if (dtype == SV_C64) k_factors<float><<<1, 256, 0, s>>>(passes, gates, mats, np, fac);
-  else k_factors<double><<<1, 256, 0, s>>>(passes, gates, mats, np, fac);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s) {
   const dim3 blocks(p.njobs > 0 ? (p.njobs + 255) / 256 : 1, p.nsets > 0 ? p.nsets : 1);
   if (dtype == SV_C64) k_prep<float><<<blocks, 256, 0, s>>>(p);

@@ -25,7 +25,6 @@ struct PassArgs {
   int pass;          // pass index (specialised kernels select their stage program by it)
   int dense_tc;      // 1: dense four-qubit gates of complex64 2^12-amplitude tiles on the tensor cores
   int gen_init;      // 1: this launch is the program's first pass and generates |0...0> instead of loading it
-  const double2* fac;  // per pass: the rotation factor carried into it (null: every pass applies its own)
 };
 
 struct PrepArgs {
@@ -47,10 +46,6 @@ struct PrepArgs {
 
 #ifndef __CUDACC_RTC__
 cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s);
-// fac[p] = product of the rotation factors of the deferring passes before pass p
-// (since the last pass that applied them); after the matrices are prepared
-cudaError_t launch_factors(int dtype, const svp::DPass* passes, const svp::DGate* gates, const void* mats, int np,
-                           double2* fac, cudaStream_t s);
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s);

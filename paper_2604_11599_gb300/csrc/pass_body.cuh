@@ -712,8 +712,7 @@ struct PassShared : TcPart<TC> {
   double ctab[16];               // measurement-group table of this CTA
   double wsum[PASS_THREADS / 32][16];
   double tile16[16];
-  double2 pfac;                  // the factor the pass multiplies into the tile when it stores it
-  double2 ptab;                  // the factor its measurement table is scaled by (squared modulus)
+  double2 pfac;                  // product of the factors of the pass's active factored gates
   int s_last;
 };
 template <typename T, bool TC>
@@ -806,10 +805,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const uint64_t ustep = CTA ? 1ull : uint64_t(gridDim.x);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    sp = A.passes[pi];
-    sh.pfac = sh.ptab = make_double2(1.0, 0.0);  // (set from the gates when the pass sweeps)
-  }
+  if (tid == 0) sp = A.passes[pi];
   if (tid < 16) ctab[tid] = 0.0;
   __syncthreads();
   const int L = sp.L, n = A.n;
@@ -882,15 +878,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           fi = fr * double(f.y) + fi * double(f.x);
           fr = r;
         }
-      // the factor carried into this pass (deferred by earlier passes): the
-      // state it reads is (carried) x (stored values); the pass multiplies in
-      // its own factor (class 0), nothing (class 1: it defers its own too), or
-      // both (class 2); its measurement table scales by |carried x own|^2
-      const double2 fc = A.fac ? A.fac[pi] : make_double2(1.0, 0.0);
-      const double2 tot = make_double2(fc.x * fr - fc.y * fi, fc.x * fi + fc.y * fr);
-      const uint8_t cls = A.fac ? sp.fclass : 0;
-      sh.pfac = cls == 1 ? make_double2(1.0, 0.0) : (cls == 2 ? tot : make_double2(fr, fi));
-      sh.ptab = tot;
+      sh.pfac = make_double2(fr, fi);
     }
     __syncthreads();
     const double2 pf = sh.pfac;
@@ -1275,7 +1263,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     if (need_ticket) {
       __syncthreads();
       if (tid == 0) {
-        scale_table(ctab, sh.ptab);
+        scale_table(ctab, sh.pfac);
         scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
       }
     }
@@ -1299,7 +1287,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     }
     __syncthreads();
     if (tid != 0) return;
-    scale_table(ctab, sh.ptab);
+    scale_table(ctab, sh.pfac);
     scalar_phase(A, sp, ctab, do_store, pm, pv, px, ps);
   }
 }

@@ -930,58 +930,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     }
   }
 
-  // Rotation factors (OP_RXF / OP_RYF / OP_DZ) of passes that surely store and
-  // hold no conditional factored gate depend on the parameters only, so they
-  // can be deferred: the pass stores the unscaled tile and a small kernel
-  // carries the product to the last surely storing pass, which multiplies it
-  // in.  Other passes multiply their own (run-time) factor in; measurement
-  // tables scale by the carried product times the pass's own factor.  Used for
-  // complex128, whose sweeps are FP64-bound (measured 3.8 % faster); complex64
-  // sweeps measured 2.4 % slower with it, so they multiply per pass.
-  if (P.dtype == SV_C128) {
-    auto factored = [](uint8_t op) { return op == OP_RXF || op == OP_RYF || op == OP_DZ; };
-    int last_sure = -1;
-    std::vector<char> sure(P.passes.size(), 0), flagged(P.passes.size(), 0);
-    for (size_t i = 0; i < P.passes.size(); ++i) {
-      const DPass& d = P.passes[i];
-      for (uint32_t g = 0; g < d.ng; ++g) {
-        const DGate& gt = P.gates[d.g0 + g];
-        sure[i] = sure[i] || gt.flag < 0;
-        flagged[i] = flagged[i] || (gt.flag >= 0 && factored(gt.op));
-      }
-      if (sure[i]) last_sure = int(i);
-    }
-    // RX / RY factors have modulus in [2^-1/2, 1], so stored values grow by up to
-    // 2^1/2 per deferred one: a chain applies after at most `limit` of them
-    // (growth <= 2^32 for complex64, far inside either format's range).
-    const int limit = P.dtype == SV_C64 ? 64 : 1024;
-    int chain = 0;
-    for (size_t i = 0; i < P.passes.size(); ++i) {
-      DPass& d = P.passes[i];
-      int nrot = 0;
-      for (uint32_t g = 0; g < d.ng; ++g) {
-        const uint8_t op = P.gates[d.g0 + g].op;
-        nrot += op == OP_RXF || op == OP_RYF;
-      }
-      if (int(i) == last_sure) {
-        d.fclass = 2;
-        chain = 0;
-      } else if (int(i) < last_sure && sure[i] && !flagged[i]) {
-        if (chain + nrot > limit) {
-          d.fclass = 2;
-          chain = 0;
-        } else {
-          d.fclass = 1;
-          chain += nrot;
-        }
-      } else {
-        d.fclass = 0;
-      }
-      P.defer_factors = P.defer_factors || d.fclass == 1;
-    }
-  }
-
-  P.stats.kernels_per_run = 1 + (P.gen_init ? 0 : 1) + (P.defer_factors ? 1 : 0) + P.passes.size();
+  P.stats.kernels_per_run = 1 + (P.gen_init ? 0 : 1) + P.passes.size();
   P.stats.records = n_ops;
   P.stats.unrolled_ops = n_gates + n_draws;
   P.stats.gates = n_gates;

@@ -38,7 +38,6 @@ struct Plan {
   uint32_t max_dots = 0;             // backward plans: derivative accumulators per pass
   bool needs_flush = false;
   bool gen_init = false;             // the first pass surely stores: it generates |0...0> itself (no init sweep)
-  bool defer_factors = false;        // some pass defers its rotation factor (the carried factors are computed)
   sv_program_stats stats{};
   uint64_t n_params_needed = 0;      // 1 + the largest parameter index referenced
 };

@@ -91,7 +91,6 @@ struct sv_program {
   DevBuf<double> consts;
   DevBuf<unsigned char> mats;
   DevBuf<uint8_t> flags;
-  DevBuf<double2> fac;  // rotation factors carried between passes
   bool cached = false;  // owned by the state's cache
   std::shared_ptr<svj::JitModule> jit;  // specialised pass kernels (sv_set_jit)
   bool jit_tried = false;
@@ -144,7 +143,6 @@ sv_status upload_plan(cudaStream_t s, size_t amp_bytes, sv_program* p) {
   SV_CUDA(p->consts.upload(P.consts, s));
   SV_CUDA(p->mats.reserve(size_t(std::max<uint32_t>(P.n_mat, 1)) * amp_bytes));
   SV_CUDA(p->flags.reserve(std::max<uint32_t>(P.n_flags, 1)));
-  SV_CUDA(p->fac.reserve(std::max<size_t>(P.passes.size(), 1)));
   SV_CUDA(cudaMemsetAsync(p->flags.p, 0, std::max<uint32_t>(P.n_flags, 1), s));
   // the host copies above read pageable vectors; finish them before the plan can change
   SV_CUDA(cudaStreamSynchronize(s));
@@ -189,8 +187,6 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
   pa.shot = shot;
   SV_CUDA(svk::launch_prep(h->dtype, pa, s));
   if (!P.gen_init) SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, s));
-  if (P.defer_factors)
-    SV_CUDA(svk::launch_factors(h->dtype, p->passes.p, p->gates.p, p->mats.p, int(P.passes.size()), p->fac.p, s));
   if (h->use_jit && !p->jit_tried) {
     p->jit_tried = true;
     std::string err;
@@ -214,7 +210,6 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
     a.partials = h->partials.p;
     a.n = h->n_int;
     a.dense_tc = h->dense_tc ? 1 : 0;
-    a.fac = P.defer_factors ? p->fac.p : nullptr;
     const double sbytes = double(1ull << h->n_int) * double(h->amp_bytes);
     for (size_t i = 0; i < P.passes.size(); ++i) {
       a.gen_init = (P.gen_init && i == 0) ? 1 : 0;

@@ -154,9 +154,7 @@ struct DPass {
   uint8_t dense;          // 1: the pass holds a dense four-qubit gate (OP_D16)
   uint8_t proj;           // 1: a measurement projector may be pending when the pass starts
   uint8_t direct;         // 1: specialised kernels store the tile from the last stage's registers
-  uint8_t fclass;         // its rotation factor: 0 multiplied in at store, 1 deferred (carried to a
-                          // later pass), 2 multiplied in together with everything carried so far
-  uint8_t pad;
+  uint8_t pad[2];
   uint8_t tq[MAX_TILE_BITS];      // qubit at tile-local bit j (ascending for j >= L)
   uint8_t outer_gq[MAX_GROUP_Q];  // table bit kin+i <- qubit outer_gq[i] (outside the tile)
   uint16_t red_R[REG_BITS];       // reduction stage: register-bit addresses

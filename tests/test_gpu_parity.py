@@ -112,25 +112,6 @@ def test_factored_rotations_edge_angles(svmod, orc, dtype):
                     compare_run(st, orc, c.ops, n, dtype, seed=trial, shot=shot)
 
 
-@pytest.mark.parametrize("dtype", DTYPES)
-def test_deferred_factor_chains_stay_in_range(svmod, orc, dtype):
-    """Rotation factors of surely storing passes are carried to a later pass
-    (the stored values grow by up to 2^1/2 per deferred RX / RY); chains are
-    cut before that can leave the format's range.  Worst case: every rotation at
-    theta = pi/2 (factor 2^-1/2), 720 of them, generic and specialised kernels."""
-    n = 12
-    c = Circuit(n)
-    for layer in range(60):
-        for q in range(n):
-            (c.rx if (q + layer) % 2 else c.ry)(q, math.pi / 2)
-        for q in range(layer % 2, n - 1, 2):
-            c.cx(q, q + 1)
-    with svmod.State(n, dtype) as st:
-        for jit in (False, True):
-            st.set_jit(jit)
-            compare_run(st, orc, c.ops, n, dtype)
-
-
 @pytest.mark.parametrize("jit", [False, True])
 def test_dense4_tensor_cores_parity(svmod, orc, jit):
     """Dense four-qubit unitaries on the tensor cores (complex64, 2^12-amplitude
