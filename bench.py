@@ -241,15 +241,31 @@ def measure_forms(sv, torch):
             st.run(c.ops, seed=0, shot=shot)
             lat.append(time.perf_counter() - t1)
         lat.sort()
+        st.sample_branched(c.ops, 50)
+        t0 = time.perf_counter()
+        _, pst = st.sample_branched(c.ops, 1000)
+        tpb = time.perf_counter() - t0
     with sv.Batch("c128") as b:
         p = b.add_program(c.ops, 5)
         b.run([p] * 1000, np.zeros(1000), np.arange(1000))
         t0 = time.perf_counter()
         b.run([p] * 1000, np.zeros(1000), np.arange(1000))
         tbs = time.perf_counter() - t0
+        b.sample_branched([p], [0], [1000])
+        t0 = time.perf_counter()
+        _, bst = b.sample_branched([p], [0], [1000])
+        tbb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, bst5 = b.sample_branched([p], [0], [100_000])
+        tbb5 = time.perf_counter() - t0
     out["plain_small_1000_shots"] = {"plain_path_shots_per_s": 1000 / tps, "batched_shots_per_s": 1000 / tbs,
                                      "plain_shot_latency_p50_ms": 1000 * lat[len(lat) // 2],
-                                     "plain_shot_latency_p99_ms": 1000 * lat[int(0.99 * len(lat))]}
+                                     "plain_shot_latency_p99_ms": 1000 * lat[int(0.99 * len(lat))],
+                                     "branched_plain_path_shots_per_s": 1000 / tpb,
+                                     "branched_batched_shots_per_s": 1000 / tbb,
+                                     "branched_paths": pst["paths"], "branched_levels": bst["levels"],
+                                     "branched_batched_100k_shots_per_s": 100_000 / tbb5,
+                                     "branched_100k_paths": bst5["paths"]}
     # VQE: n=20 hardware-efficient ansatz, 320 parameters, 200 Pauli terms
     c = W.hea(20, 8)
     terms = W.heisenberg_fields(9, 20, 200)
@@ -338,10 +354,16 @@ def measure_forms(sv, torch):
     srv.serve(reqs[:4])
     _, st_srv = srv.serve(reqs)
     srv.close()
+    be1 = serve.GpuBackend("c64", seed=0, branching=False)
+    srv = serve.Server(be1)
+    srv.serve(reqs[:4])
+    _, st_srv1 = srv.serve(reqs)
+    srv.close()
     _, st_seq = serve.serve_sequential(be, reqs)
     out["serving"] = {"workload": f"{len(reqs)} requests (Poisson 200/s for 1 s), n log-uniform 10-22, depth "
                                   "10-40 layers, 1-8 measures with cond/loop feed-forward, shots log-uniform 1-256",
-                      "server": st_srv, "sequential_plain_path": st_seq}
+                      "server": st_srv, "server_one_trajectory_per_shot": st_srv1,
+                      "sequential_plain_path": st_seq}
     return out
 
 

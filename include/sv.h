@@ -132,6 +132,14 @@ typedef struct sv_program_stats {
                                |0...0> sweep unless the first pass generates it, the passes */
 } sv_program_stats;
 
+/* Shot branching (sv_sample_branched, sv_batch_sample_branched). */
+typedef struct sv_branch_stats {
+  uint64_t shots;       /* shots sampled                                           */
+  uint64_t paths;       /* trajectories simulated: one per distinct outcome path   */
+  uint64_t levels;      /* walk rounds (each finds the paths of the next depth)    */
+  uint64_t max_draws;   /* most draws on one path                                  */
+} sv_branch_stats;
+
 #ifndef __CUDACC_RTC__ /* device code compiled at run time needs the types above only */
 
 /*
@@ -199,6 +207,23 @@ sv_status sv_get_trace(sv_state* h, sv_draw* out, size_t max, size_t* n_out);
 sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
                     uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
                     uint64_t* bits_out);
+
+/*
+ * Shot branching: creg_out[s] (s < shots) receives exactly the register that
+ * sv_sample on this state gives shot s, but only one trajectory runs per
+ * distinct outcome path among the shots.  Shots that agree on their first k
+ * outcomes hold the same state, so each of their next draws compares its own
+ * Philox number with the same (p0, p1); a representative trajectory records
+ * those masses and a device walk routes every shot down the tree of paths
+ * (Sec. III-C: outcomes are still decided per shot at run time).  stats
+ * (nullable) reports shots, paths, walk rounds and the longest path.
+ * SV_ERR_UNSUPPORTED when a trajectory executes more than 4096 draws or
+ * shots >= 2^32 - 1; SV_ERR_NUMERIC as for sv_run.  The state holds the last
+ * representative's final state afterwards.  Waits for the output.
+ */
+sv_status sv_sample_branched(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
+                             uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
+                             sv_branch_stats* stats);
 
 /* Terminal samples of the current state: out[s] for counter (shot0 + s, 2^32). */
 sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
@@ -272,6 +297,20 @@ sv_status sv_batch_results(sv_batch* b, uint64_t* creg_out);
 sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
                        size_t n_items, uint64_t seed, uint64_t* creg_out);
 sv_status sv_batch_destroy(sv_batch* b);
+
+/*
+ * Shot branching on the batched engine: n_requests requests, request r
+ * running program prog_ids[r] with Philox stream stream_ids[r] for
+ * n_shots[r] shots (counters 0 .. n_shots[r]-1).  creg_out receives the
+ * records request after request (sum of n_shots entries), each equal to
+ * the record sv_batch_run gives that (program, stream, shot).  The
+ * representatives of each walk round run together in one persistent
+ * launch.  Replaces the batch's current items.  Errors as for
+ * sv_sample_branched and sv_batch_run.
+ */
+sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids,
+                                   const uint64_t* n_shots, size_t n_requests, uint64_t seed, uint64_t* creg_out,
+                                   sv_branch_stats* stats);
 
 /*
  * Energies and adjoint gradients of <H> = sum_t coeff_t <psi(theta)|P_t|psi(theta)>

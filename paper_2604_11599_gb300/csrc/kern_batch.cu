@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_batc
       C->ps = 1.0;
       C->ticket = 0;
       C->status = 0;
-      C->n_trace = MAX_TRACE;  // no draw records in batched runs
+      C->n_trace = B.trace_out ? 0 : MAX_TRACE;  // draw records only for shot branching
       for (uint32_t k = 0; k < P.ninit; ++k) {  // COND evaluations before the first measurement
         const DScalar s = P.init[k];
         const bool par = s.flag < 0 || flags[s.flag];
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_batc
     A.mats = P.mats;
     A.flags = flags;
     A.ctrl = C;
-    A.trace = nullptr;
+    A.trace = B.trace_out ? B.trace_slots + size_t(blockIdx.x) * MAX_TRACE : nullptr;
     A.partials = nullptr;
     A.n = int(w.n_int);
     A.pass = 0;
@@ -74,6 +74,20 @@ __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_batc
     if (tid == 0) {
       B.creg_out[w.out] = C->creg;
       if (C->status) atomicCAS(B.status_out, 0, C->status);
+      if (B.trace_out) B.m_out[w.out] = C->m;
+    }
+    if (B.trace_out) {  // the trajectory's draws, in the compact form the shot walk reads
+      const uint64_t m = C->m, lim = B.trace_cap < uint32_t(MAX_TRACE) ? B.trace_cap : uint32_t(MAX_TRACE);
+      const uint32_t k = uint32_t(m < lim ? m : lim);
+      for (uint32_t d = tid; d < k; d += PASS_THREADS) {
+        const DTrace t = A.trace[d];
+        BrDraw o;
+        o.p0 = t.p0;
+        o.p1 = t.p1;
+        o.outcome = t.outcome;
+        o.child = -1;
+        B.trace_out[size_t(w.out) * B.trace_cap + d] = o;
+      }
     }
     __syncthreads();
   }

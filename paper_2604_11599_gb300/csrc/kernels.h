@@ -59,6 +59,18 @@ cudaError_t launch_pass(int dtype, const PassArgs& a, int pi, int grid, int m, c
 cudaError_t pass_occupancy(int dtype, int m, int* blocks_per_sm);
 #endif
 
+// shot branching: the draws of one representative trajectory per outcome path,
+// and the walk that routes every shot of a request down the tree of paths
+struct BrDraw {
+  double p0, p1;    // unnormalised outcome masses the draw compared against
+  int32_t outcome;  // the representative's outcome
+  int32_t child;    // path whose representative took the other outcome here (-1: none yet)
+};
+struct BrPath {
+  uint32_t off, len;  // its draws: draws[off .. off + len)
+  uint64_t creg;      // classical register at the end of the path
+};
+
 // persistent batched execution: one CTA runs one trajectory at a time
 struct BatchProg {
   const svp::DPass* passes;
@@ -92,6 +104,11 @@ struct BatchArgs {
   uint64_t seed;
   uint64_t* creg_out;   // [n_items], indexed by BatchItem::out
   int* status_out;      // first nonzero trajectory status
+  // draw records (shot branching; trace_out == nullptr: none are kept)
+  svp::DTrace* trace_slots;  // [grid][MAX_TRACE] per-CTA scratch
+  BrDraw* trace_out;         // [n_items][trace_cap]
+  uint32_t trace_cap;
+  uint64_t* m_out;           // [n_items] draws executed
 };
 constexpr int BATCH_TILE_BITS = 12;
 #ifndef __CUDACC_RTC__
@@ -99,6 +116,28 @@ cudaError_t launch_batch(int dtype, const BatchArgs& a, int grid, cudaStream_t s
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t batch_occupancy(int dtype, int* blocks_per_sm);
+#endif
+
+// the walk over the shots of one or more requests (kern_branch.cu)
+struct BranchArgs {
+  const BrDraw* draws;
+  const BrPath* paths;
+  const uint64_t* req_begin;   // [nreq + 1] first shot (global index) of each request
+  const uint64_t* req_stream;  // [nreq] Philox stream of each request
+  const uint32_t* req_root;    // [nreq] first path of each request
+  uint32_t nreq;
+  uint64_t seed;
+  uint64_t nshots;
+  uint64_t* walk;      // [nshots] (path << 32) | depth, bit 31 set once the shot reached its path's end
+  uint32_t* claim;     // [ndraws] smallest shot that left the tree at this draw (0xFFFFFFFF: none)
+  uint32_t* fresh;     // [ndraws] draws claimed for the first time by this walk
+  uint32_t* nfresh;
+  uint64_t* creg_out;  // [nshots] (gather)
+};
+#ifndef __CUDACC_RTC__
+cudaError_t launch_branch_init(const BranchArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_branch_walk(const BranchArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_branch_gather(const BranchArgs& a, int sms, cudaStream_t s);
 #endif
 
 // batched adjoint gradients: one CTA per parameter set (persistent)

@@ -13,6 +13,7 @@
 
 #include "../../include/sv.h"
 #include "jit.h"
+#include "branch.h"
 #include "kernels.h"
 #include "planner.h"
 
@@ -128,6 +129,7 @@ struct sv_state {
   bool use_cache = true;
   bool use_jit = false;
   bool dense_tc = true;  // dense four-qubit gates on the tensor cores where the kernel supports it
+  std::unique_ptr<svb::Work, void (*)(svb::Work*)> branch{nullptr, svb::work_free};  // shot-branching scratch
 };
 
 namespace {
@@ -566,6 +568,64 @@ sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* p
   return check_status(h);
 }
 
+sv_status sv_sample_branched(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
+                             uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
+                             sv_branch_stats* stats) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (shots && !creg_out) return fail(SV_ERR_ARG, "creg_out is NULL");
+  if (n_ops && !ops) return fail(SV_ERR_ARG, "ops is NULL");
+  if (n_params && !params) return fail(SV_ERR_ARG, "params is NULL");
+  if (stats) *stats = sv_branch_stats{shots, 0, 0, 0};
+  if (!shots) return SV_OK;
+  sv_program* p = nullptr;
+  sv_status st = get_program(h, ops, n_ops, &p);
+  if (st != SV_OK) return st;
+  if (n_params) {
+    SV_CUDA(h->params.reserve(n_params));
+    SV_CUDA(cudaMemcpyAsync(h->params.p, params, n_params * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  const double* dp = n_params ? h->params.p : nullptr;
+  if (!h->branch) h->branch.reset(svb::work_new());
+  size_t cap = 0;
+  for (const svp::DScalar& x : p->plan.scalars) cap += (x.kind == svp::S_MEASURE || x.kind == svp::S_RESET) ? 1 : 0;
+  cap = std::min<size_t>(cap, svp::MAX_TRACE);
+  std::vector<DTrace> tr;
+  // representatives run one after another on this state, each a full sv_launch
+  svb::Runner run = [&](const std::vector<svb::RepReq>& reps, std::vector<svb::RepOut>& outs,
+                        std::string& err) -> sv_status {
+    outs.assign(reps.size(), svb::RepOut());
+    for (size_t k = 0; k < reps.size(); ++k) {
+      sv_status rs = launch_program(h, p, dp, n_params, seed, stream_id, reps[k].shot);
+      if (rs != SV_OK) {
+        err = g_err;
+        return rs;
+      }
+      Ctrl c;
+      cudaError_t e = cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream);
+      tr.resize(cap);  // the program's draw items bound the draws a trajectory executes
+      if (e == cudaSuccess && cap)
+        e = cudaMemcpyAsync(tr.data(), h->trace, cap * sizeof(DTrace), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      const size_t nk = std::min<uint64_t>(c.m, cap);
+      if (e != cudaSuccess) {
+        err = std::string("representative record: ") + cudaGetErrorString(e);
+        return SV_ERR_CUDA;
+      }
+      svb::RepOut& o = outs[k];
+      o.creg = c.creg;
+      o.status = c.status;
+      o.m = c.m;
+      o.draws.resize(nk);
+      for (size_t d = 0; d < nk; ++d) o.draws[d] = svk::BrDraw{tr[d].p0, tr[d].p1, tr[d].outcome, -1};
+    }
+    return SV_OK;
+  };
+  std::string err;
+  st = svb::sample(h->branch.get(), h->stream, h->sms, {stream_id}, {shots}, seed, 0, run, creg_out, stats, err);
+  if (st != SV_OK) return fail(st, err);
+  return SV_OK;
+}
+
 sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* total, double* per_term) {
   if (!h) return fail(SV_ERR_ARG, "null handle");
   if (n_terms && !terms) return fail(SV_ERR_ARG, "terms is NULL");
@@ -654,6 +714,13 @@ struct sv_batch {
   uint32_t slot_flags = 0;
   cudaGraphExec_t gexec = nullptr;
   uint64_t gkey = 0;
+  // shot branching
+  std::vector<uint32_t> prog_draws;  // draw items of each program (a bound on the draws a trajectory executes)
+  std::vector<svk::BatchItem> items_host;  // staging of the last quick item upload
+  DevBuf<DTrace> tslots;
+  DevBuf<svk::BrDraw> tout;
+  DevBuf<uint64_t> mout;
+  std::unique_ptr<svb::Work, void (*)(svb::Work*)> branch{nullptr, svb::work_free};
   ~sv_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (prep_ctrl) cudaFree(prep_ctrl);
@@ -739,14 +806,31 @@ sv_status sv_batch_add_program(sv_batch* b, int n, const sv_op* ops, size_t n_op
   b->hprogs.push_back(bp);
   b->prog_nint.push_back(uint32_t(P.n_int));
   b->prog_flags.push_back(std::max<uint32_t>(P.n_flags, 1));
+  uint32_t nd = 0;
+  for (const svp::DScalar& x : P.scalars) nd += (x.kind == svp::S_MEASURE || x.kind == svp::S_RESET) ? 1u : 0u;
+  b->prog_draws.push_back(nd);
   b->progs.push_back(std::move(p));
   SV_CUDA(b->d_progs.upload(b->hprogs, b->own));
   SV_CUDA(cudaStreamSynchronize(b->own));
   return SV_OK;
 }
 
+namespace {
+// quick: no wait for the upload and no device-memory query while the slots already fit
+sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                      size_t n_items, bool quick);
+}  // namespace
+
 sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
                              size_t n_items) {
+  return batch_items(b, prog_ids, stream_ids, shots, n_items, false);
+}
+
+}  // extern "C"
+
+namespace {
+sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                      size_t n_items, bool quick) {
   if (!b) return fail(SV_ERR_ARG, "null handle");
   if (n_items && (!prog_ids || !stream_ids || !shots)) return fail(SV_ERR_ARG, "null item arrays");
   if (n_items >= (size_t(1) << 32)) return fail(SV_ERR_ARG, "too many items");
@@ -769,22 +853,33 @@ sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64
                    [](const svk::BatchItem& x, const svk::BatchItem& y) { return x.n_int > y.n_int; });
   const uint64_t slot_amps = n_items ? (1ull << max_nint) : 1;
   const size_t need = size_t(b->grid) * slot_amps * b->amp_bytes;
-  size_t free_b = 0, total_b = 0;
-  SV_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  if (need > b->slots.n && need - b->slots.n > free_b) return fail(SV_ERR_OOM, "batch work space exceeds free device memory");
+  if (!(quick && need <= b->slots.n)) {
+    size_t free_b = 0, total_b = 0;
+    SV_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (need > b->slots.n && need - b->slots.n > free_b)
+      return fail(SV_ERR_OOM, "batch work space exceeds free device memory");
+  }
   if (cudaSuccess != b->slots.reserve(need)) return fail(SV_ERR_OOM, "batch state slots");
   SV_CUDA(b->fslots.reserve(size_t(b->grid) * max_flags));
   SV_CUDA(b->ctrls.reserve(size_t(b->grid)));
   SV_CUDA(b->queue.reserve(1));
   SV_CUDA(b->status.reserve(1));
   SV_CUDA(b->cregs.reserve(std::max<size_t>(n_items, 1)));
-  SV_CUDA(b->d_items.upload(items, b->own));
-  SV_CUDA(cudaStreamSynchronize(b->own));
+  if (quick) {  // the staging vector must outlive the copy: keep it in the handle
+    b->items_host.swap(items);
+    SV_CUDA(b->d_items.upload(b->items_host, b->own));
+  } else {
+    SV_CUDA(b->d_items.upload(items, b->own));
+    SV_CUDA(cudaStreamSynchronize(b->own));
+  }
   b->n_items = n_items;
   b->slot_amps = slot_amps;
   b->slot_flags = max_flags;
   return SV_OK;
 }
+}  // namespace
+
+extern "C" {
 
 sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   if (!b) return fail(SV_ERR_ARG, "null handle");
@@ -850,6 +945,104 @@ sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* st
   st = sv_batch_launch(b, seed);
   if (st != SV_OK) return st;
   return sv_batch_results(b, creg_out);
+}
+
+sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids,
+                                   const uint64_t* n_shots, size_t n_requests, uint64_t seed, uint64_t* creg_out,
+                                   sv_branch_stats* stats) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  if (n_requests && (!prog_ids || !stream_ids || !n_shots)) return fail(SV_ERR_ARG, "null request arrays");
+  if (n_requests >= (size_t(1) << 32)) return fail(SV_ERR_ARG, "too many requests");
+  uint64_t total = 0;
+  uint32_t cap = 1;
+  for (size_t r = 0; r < n_requests; ++r) {
+    if (prog_ids[r] >= b->progs.size()) return fail(SV_ERR_ARG, "unknown program id");
+    total += n_shots[r];
+    cap = std::max(cap, std::min<uint32_t>(b->prog_draws[prog_ids[r]], svp::MAX_TRACE));
+  }
+  if (stats) *stats = sv_branch_stats{total, 0, 0, 0};
+  if (total && !creg_out) return fail(SV_ERR_ARG, "creg_out is NULL");
+  if (!total) return SV_OK;
+  if (!b->branch) b->branch.reset(svb::work_new());
+  SV_CUDA(b->tslots.reserve(size_t(b->grid) * svp::MAX_TRACE));
+  std::vector<uint32_t> ip;
+  std::vector<uint64_t> is, ish, ic, im;
+  std::vector<svk::BrDraw> itr;
+  // the representatives of one round run together in one persistent launch
+  svb::Runner run = [&](const std::vector<svb::RepReq>& reps, std::vector<svb::RepOut>& outs,
+                        std::string& err) -> sv_status {
+    const size_t k = reps.size();
+    ip.resize(k);
+    is.resize(k);
+    ish.resize(k);
+    for (size_t i = 0; i < k; ++i) {
+      ip[i] = prog_ids[reps[i].req];
+      is[i] = stream_ids[reps[i].req];
+      ish[i] = reps[i].shot;
+    }
+    sv_status rs = batch_items(b, ip.data(), is.data(), ish.data(), k, true);
+    if (rs != SV_OK) {
+      err = g_err;
+      return rs;
+    }
+    cudaError_t e = b->tout.reserve(k * size_t(cap));
+    if (e == cudaSuccess) e = b->mout.reserve(k);
+    svk::BatchArgs a{};
+    a.items = b->d_items.p;
+    a.n_items = uint32_t(k);
+    a.progs = b->d_progs.p;
+    a.state_slots = b->slots.p;
+    a.slot_amps = b->slot_amps;
+    a.flag_slots = b->fslots.p;
+    a.slot_flags = b->slot_flags;
+    a.ctrls = b->ctrls.p;
+    a.queue = b->queue.p;
+    a.seed = seed;
+    a.creg_out = b->cregs.p;
+    a.status_out = b->status.p;
+    a.trace_slots = b->tslots.p;
+    a.trace_out = b->tout.p;
+    a.trace_cap = cap;
+    a.m_out = b->mout.p;
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in, b->user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->own, b->ev_in, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned), b->own);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status.p, 0, sizeof(int), b->own);
+    if (e == cudaSuccess) e = svk::launch_batch(b->dtype, a, b->grid, b->own);
+    ic.resize(k);
+    im.resize(k);
+    itr.resize(k * size_t(cap));
+    int bst = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ic.data(), b->cregs.p, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, b->own);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(im.data(), b->mout.p, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, b->own);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(itr.data(), b->tout.p, itr.size() * sizeof(svk::BrDraw), cudaMemcpyDeviceToHost, b->own);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bst, b->status.p, sizeof(int), cudaMemcpyDeviceToHost, b->own);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->own);
+    if (e != cudaSuccess) {
+      err = std::string("batched representatives: ") + cudaGetErrorString(e);
+      return SV_ERR_CUDA;
+    }
+    outs.assign(k, svb::RepOut());
+    for (size_t i = 0; i < k; ++i) {
+      svb::RepOut& o = outs[i];
+      o.creg = ic[i];
+      o.status = bst;  // the launch reports its first failing trajectory
+      o.m = im[i];
+      const size_t nk = std::min<uint64_t>(im[i], cap);
+      o.draws.assign(itr.begin() + i * size_t(cap), itr.begin() + i * size_t(cap) + nk);
+    }
+    return SV_OK;
+  };
+  std::vector<uint64_t> rstream(stream_ids, stream_ids + n_requests), rshots(n_shots, n_shots + n_requests);
+  std::string err;
+  // one resident wave of the batched kernel seeds the first round
+  sv_status st = svb::sample(b->branch.get(), b->own, b->sms, rstream, rshots, seed, uint64_t(b->grid), run, creg_out,
+                             stats, err);
+  if (st != SV_OK) return fail(st, err);
+  return SV_OK;
 }
 
 sv_status sv_batch_destroy(sv_batch* b) {

@@ -66,15 +66,19 @@ def footprint_bytes(n: int, dtype: str, batch_max_n: int = 18) -> int:
 
 
 class GpuBackend:
-    """Executes work on the GPU through the C-ABI binding."""
+    """Executes work on the GPU through the C-ABI binding.
 
-    def __init__(self, dtype: str = "c64", seed: int = 0):
+    With ``branching`` (default) the shots of a request run by shot
+    branching: one trajectory per distinct outcome path, every record equal
+    to the one the shot's own trajectory gives on the same engine."""
+
+    def __init__(self, dtype: str = "c64", seed: int = 0, branching: bool = True):
         import torch
 
         from . import sv
 
         self.sv, self.torch = sv, torch
-        self.dtype, self.seed = dtype, seed
+        self.dtype, self.seed, self.branching = dtype, seed, branching
         self.batch_stream = torch.cuda.Stream()
         with torch.cuda.stream(self.batch_stream):
             self.batch = sv.Batch(dtype, stream=self.batch_stream.cuda_stream)
@@ -85,11 +89,21 @@ class GpuBackend:
         return int(free)
 
     def run_batch(self, reqs: list[Req]) -> dict[int, np.ndarray]:
-        """All shots of these small requests in one persistent launch."""
+        """All shots of these small requests in one persistent launch (one
+        launch per walk round with branching)."""
         progs, streams, shots = [], [], []
         for r in reqs:
             if r.rid not in self.prog_ids:
                 self.prog_ids[r.rid] = self.batch.add_program(r.ops, r.n)
+        if self.branching:
+            out, _ = self.batch.sample_branched([self.prog_ids[r.rid] for r in reqs], [r.rid for r in reqs],
+                                                [r.shots for r in reqs], seed=self.seed)
+            res, k = {}, 0
+            for r in reqs:
+                res[r.rid] = out[k: k + r.shots]
+                k += r.shots
+            return res
+        for r in reqs:
             progs.append(np.full(r.shots, self.prog_ids[r.rid], dtype=np.uint32))
             streams.append(np.full(r.shots, r.rid, dtype=np.uint64))
             shots.append(np.arange(r.shots, dtype=np.uint64))
@@ -105,7 +119,16 @@ class GpuBackend:
         s = self.torch.cuda.Stream()
         with self.torch.cuda.stream(s):
             with self.sv.State(r.n, self.dtype, stream=s.cuda_stream) as st:
-                cregs, _ = st.sample(r.ops, r.shots, seed=self.seed, stream_id=r.rid)
+                if self.branching:
+                    cregs, _ = st.sample_branched(r.ops, r.shots, seed=self.seed, stream_id=r.rid)
+                else:
+                    cregs, _ = st.sample(r.ops, r.shots, seed=self.seed, stream_id=r.rid)
+        return cregs
+
+    def run_plain(self, r: Req) -> np.ndarray:
+        """The plain path: one trajectory per shot on one resident state."""
+        with self.sv.State(r.n, self.dtype) as st:
+            cregs, _ = st.sample(r.ops, r.shots, seed=self.seed, stream_id=r.rid)
         return cregs
 
 
@@ -204,7 +227,9 @@ class Server:
 
 
 def serve_sequential(backend, requests: list[Req], clock: Callable[[], float] = time.perf_counter):
-    """Baseline: one request at a time in arrival order, all on the plain path."""
+    """Baseline: one request at a time in arrival order, all on the plain path
+    (one trajectory per shot)."""
+    run = getattr(backend, "run_plain", backend.run_large)
     reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
     t0 = clock()
     results = []
@@ -212,7 +237,7 @@ def serve_sequential(backend, requests: list[Req], clock: Callable[[], float] = 
         while clock() - t0 < r.arrival:
             time.sleep(1e-4)
         ta = clock() - t0
-        cregs = backend.run_large(r)
+        cregs = run(r)
         results.append(Result(r.rid, cregs, r.arrival, ta, clock() - t0, "plain"))
     wall = clock() - t0
     lat = np.array([r.latency for r in results])

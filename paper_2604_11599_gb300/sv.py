@@ -44,6 +44,13 @@ class ProgramStats(C.Structure):
                 ("block_barriers", C.c_uint64), ("warp_barriers", C.c_uint64), ("kernels_per_run", C.c_uint64)]
 
 
+class BranchStats(C.Structure):
+    _fields_ = [("shots", C.c_uint64), ("paths", C.c_uint64), ("levels", C.c_uint64), ("max_draws", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -70,6 +77,8 @@ def lib():
         "sv_get_trace": ([vp, vp, sz, C.POINTER(sz)], st),
         "sv_sample": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, vp], st),
         "sv_sample_state": ([vp, u64, u64, u64, u64, vp], st),
+        "sv_sample_branched": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, C.POINTER(BranchStats)], st),
+        "sv_batch_sample_branched": ([vp, vp, vp, vp, sz, u64, vp, C.POINTER(BranchStats)], st),
         "sv_expval": ([vp, vp, sz, vp, vp], st),
         "sv_expval_static": ([vp, i32, i32, vp, sz, vp, vp], st),
         "sv_get_amplitudes": ([vp, vp, sz, sz], st),
@@ -273,6 +282,17 @@ class State:
                                stream_id, _ptr(cregs), _ptr(bits)))
         return cregs, bits
 
+    def sample_branched(self, ops: np.ndarray, shots: int, params=None, seed: int = 0, stream_id: int = 0):
+        """The registers sample() gives, one trajectory per distinct outcome path
+        (``sv_sample_branched``); returns (cregs, stats)."""
+        ops = _ops(ops)
+        p = _f64(params)
+        cregs = np.zeros(shots, dtype=np.uint64)
+        st = BranchStats()
+        _check(lib().sv_sample_branched(self._h, _ptr(ops), len(ops), _ptr(p), 0 if p is None else p.size, shots,
+                                        seed, stream_id, _ptr(cregs), C.byref(st)))
+        return cregs, st.as_dict()
+
     def sample_state(self, shots: int, seed: int = 0, stream_id: int = 0, shot0: int = 0) -> np.ndarray:
         out = np.zeros(shots, dtype=np.uint64)
         _check(lib().sv_sample_state(self._h, shots, seed, stream_id, shot0, _ptr(out)))
@@ -370,6 +390,22 @@ class Batch:
         self.set_items(prog_ids, stream_ids, shots)
         self.launch(seed)
         return self.results()
+
+    def sample_branched(self, prog_ids, stream_ids, n_shots, seed: int = 0):
+        """Request r: n_shots[r] shots (counters 0..) of program prog_ids[r] on
+        stream stream_ids[r], one trajectory per distinct outcome path
+        (``sv_batch_sample_branched``); returns (cregs request after request, stats)."""
+        pr = np.ascontiguousarray(prog_ids, dtype=np.uint32)
+        sid = np.ascontiguousarray(stream_ids, dtype=np.uint64)
+        ns = np.ascontiguousarray(n_shots, dtype=np.uint64)
+        if not (pr.size == sid.size == ns.size):
+            raise ValueError("request arrays differ in length")
+        cregs = np.zeros(int(ns.sum()), dtype=np.uint64)
+        st = BranchStats()
+        _check(lib().sv_batch_sample_branched(self._h, _ptr(pr), _ptr(sid), _ptr(ns), pr.size, seed, _ptr(cregs),
+                                              C.byref(st)))
+        self.n_items = 0
+        return cregs, st.as_dict()
 
     def close(self):
         if getattr(self, "_h", None):

@@ -25,6 +25,14 @@ def test_alone_vs_mix_and_plain_path():
         q0 = serve.Req(q.rid, 0.0, q.n, q.ops, q.shots)
         alone, _ = srv.serve([q0])
         assert np.array_equal(alone[0].cregs, mix[q.rid].cregs), q.rid
-    for q in reqs[:6]:
+    for q in reqs[:6]:  # branched large path and one trajectory per shot give the same records
         assert np.array_equal(be.run_large(q), mix[q.rid].cregs), q.rid
+        assert np.array_equal(be.run_plain(q), mix[q.rid].cregs), q.rid
     srv.close()
+    # the per-shot engines (branching off) agree as well
+    be2 = serve.GpuBackend("c64", seed=5, branching=False)
+    srv2 = serve.Server(be2, batch_max_n=21, large_workers=3)
+    mix2, _ = srv2.serve(reqs[:24])
+    for q in reqs[:24]:
+        assert np.array_equal(mix2[q.rid].cregs, mix[q.rid].cregs), q.rid
+    srv2.close()
