@@ -386,6 +386,96 @@ def random_clifford(seed: int, n: int, depth: int) -> Circuit:
     return c
 
 
+def random_clifford_dynamic(seed: int, n: int, n_ops: int = 80, max_depth: int = 3) -> Circuit:
+    """Random dynamic Clifford program: gates over {H, S, SDG, X, Y, Z, SX, CX,
+    CY, CZ, SWAP}, measures into 6 classical bits, resets, nested if/else on
+    1-3 bit predicates and bounded loops (the static suite's gate set, Sec.
+    IV-A.2, with the feed-forward patterns of the Abstract)."""
+    r = rng(seed)
+    c = Circuit(n)
+    one = ("h", "s", "sdg", "x", "y", "z", "sx")
+    two = ("cx", "cy", "cz", "swap")
+    state = {"left": n_ops}
+
+    def gate():
+        if n >= 2 and r.random() < 0.4:
+            a, b = (int(v) for v in r.choice(n, size=2, replace=False))
+            getattr(c, two[int(r.integers(len(two)))])(a, b)
+        else:
+            getattr(c, one[int(r.integers(len(one)))])(int(r.integers(n)))
+
+    def block(depth: int, budget: int):
+        for _ in range(budget):
+            if state["left"] <= 0:
+                return
+            state["left"] -= 1
+            u = r.random()
+            if u < 0.6:
+                gate()
+            elif u < 0.75:
+                c.measure(int(r.integers(n)), int(r.integers(6)))
+            elif u < 0.82:
+                c.reset(int(r.integers(n)))
+            elif u < 0.94 and depth < max_depth:
+                k = int(r.integers(1, 4))
+                bits = [int(v) for v in r.choice(6, size=k, replace=False)]
+                mask = _deposit(bits, (1 << k) - 1)
+                value = _deposit(bits, int(r.integers(1 << k)))
+                t = int(r.integers(1, 5))
+                e = int(r.integers(0, 4))
+                c.cond(mask, value, lambda: block(depth + 1, t),
+                       (lambda: block(depth + 1, e)) if e else None)
+            elif depth < max_depth:
+                k = int(r.integers(1, 4))
+                b = int(r.integers(1, 5))
+                c.loop(k, lambda: block(depth + 1, b))
+
+    while state["left"] > 0:
+        block(0, state["left"])
+    return c
+
+
+def repetition_code(d: int, rounds: int, flip_every: int = 0, ghz: bool = False) -> Circuit:
+    """Bit-flip repetition code of distance d (3 <= d <= 32): data qubits
+    0..d-1, ancillas d..2d-2.  Each round measures the d-1 neighbour parities
+    Z_j Z_{j+1} through an ancilla (CX, CX, measure into bit 32 + j, reset)
+    and corrects a single flipped data qubit by feed-forward: qubit i (inner)
+    when parities i-1 and i are set, qubit 0 when parity 0 alone is set among
+    parities 0, 1, qubit d-1 when parity d-2 alone is set among d-3, d-2.
+    flip_every > 0 applies X to data qubit (t mod d) before every
+    flip_every-th round t.  ghz: the data starts in (|0...0> + |1...1>)/sqrt 2
+    (H, CX chain), which every parity check leaves unchanged.  At the end the
+    data qubits are read into bits 0..d-1: all zero (ghz=False) or all equal,
+    each value with probability 1/2 (ghz=True), and a round's syndrome bits
+    depend only on the flips."""
+    if not 3 <= d <= 32:
+        raise ValueError("distance out of range")
+    c = Circuit(2 * d - 1)
+    if ghz:
+        c.h(0)
+        for i in range(d - 1):
+            c.cx(i, i + 1)
+    for t in range(rounds):
+        if flip_every and t % flip_every == 0:
+            c.x(t % d)
+        for j in range(d - 1):
+            a = d + j
+            c.cx(j, a).cx(j + 1, a)
+            c.measure(a, 32 + j)
+            c.reset(a)
+        for i in range(d):
+            if i == 0:
+                mask, value = (1 << 32) | (1 << 33), 1 << 32
+            elif i == d - 1:
+                mask, value = (1 << (32 + d - 3)) | (1 << (32 + d - 2)), 1 << (32 + d - 2)
+            else:
+                mask = value = (1 << (32 + i - 1)) | (1 << (32 + i))
+            c.cond(mask, value, lambda i=i: c.x(i))
+    for i in range(d):
+        c.measure(i, i)
+    return c
+
+
 _ALL_1Q = ("H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "SX")
 _ALL_1Q_ANG = ("RX", "RY", "RZ", "P")
 _ALL_2Q = ("CX", "CY", "CZ", "SWAP", "CH")
