@@ -266,6 +266,37 @@ def measure_forms(sv, torch):
                                      "branched_paths": pst["paths"], "branched_levels": bst["levels"],
                                      "branched_batched_100k_shots_per_s": 100_000 / tbb5,
                                      "branched_100k_paths": bst5["paths"]}
+    # Clifford programs: stabilizer tableaux (one warp per shot) against the state-vector engines
+    cl = {}
+    rep = W.repetition_code(32, 10, flip_every=1, ghz=True)
+    rnd = W.random_clifford_dynamic(21, 64, n_ops=150)
+    for name, circ, nq in (("repetition_d32_10_rounds_63q", rep, 63), ("random_dynamic_64q_150_ops", rnd, 64)):
+        with sv.Clifford(nq, circ.ops) as h:
+            h.sample(1000)
+            t0 = time.perf_counter()
+            h.sample(1_000_000, seed=1)
+            cl[name] = {"tableau_shots_per_s": 1e6 / (time.perf_counter() - t0), "shots": 1_000_000}
+    rep10 = W.repetition_code(10, 10, flip_every=1, ghz=True)
+    with sv.Clifford(19, rep10.ops) as h:
+        h.sample(1000)
+        t0 = time.perf_counter()
+        h.sample(100_000, seed=1)
+        t_tab = time.perf_counter() - t0
+    with sv.Batch("c64") as b:
+        p = b.add_program(rep10.ops, 19)
+        b.run([p] * 8, np.zeros(8), np.arange(8))
+        t0 = time.perf_counter()
+        b.run([p] * 1000, np.zeros(1000), np.arange(1000))
+        t_sv = time.perf_counter() - t0
+        b.sample_branched([p], [0], [1000])
+        t0 = time.perf_counter()
+        _, bst = b.sample_branched([p], [0], [100_000])
+        t_br = time.perf_counter() - t0
+    cl["repetition_d10_10_rounds_19q"] = {"tableau_shots_per_s": 1e5 / t_tab,
+                                          "sv_batched_per_shot_shots_per_s": 1000 / t_sv,
+                                          "sv_batched_branched_shots_per_s": 1e5 / t_br,
+                                          "branched_paths": bst["paths"]}
+    out["clifford"] = cl
     # VQE: n=20 hardware-efficient ansatz, 320 parameters, 200 Pauli terms
     c = W.hea(20, 8)
     terms = W.heisenberg_fields(9, 20, 200)

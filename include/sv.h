@@ -299,6 +299,32 @@ sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* st
 sv_status sv_batch_destroy(sv_batch* b);
 
 /*
+ * Clifford fast path: programs whose gates are all Clifford (I, H, X, Y, Z,
+ * S, SDG, SX, CX, CY, CZ, SWAP) with MEASURE, RESET, COND and LOOP records,
+ * on 1 <= n <= 64 qubits, sampled by stabilizer tableaux (Aaronson and
+ * Gottesman 2004) instead of state vectors: one warp per shot, 2n Pauli rows
+ * in registers.  The paper's static suite is random Clifford circuits (Sec.
+ * IV-A.2), run there on a stabilizer backend (Fig. 1c).
+ *   sv_clifford_create   lowers the op list (COND to jumps, LOOP unrolled, at
+ *                        most 2^24 instructions) and uploads it; work is
+ *                        enqueued on cuda_stream (NULL: legacy default stream).
+ *                        SV_ERR_UNSUPPORTED for a non-Clifford gate or a DENSE
+ *                        record, SV_ERR_ARG for bad qubits, bits or lengths.
+ *   sv_clifford_sample   creg_out[s] (host, `shots` entries) = the register of
+ *                        shot shot0 + s; draw m of a shot uses Philox counter
+ *                        (shot, m) as in sv_run, and a random outcome is 1 iff
+ *                        u >= 1/2, so records equal sv_sample's except where the
+ *                        state vector's rounded p0/(p0+p1) and 1/2 straddle u.
+ *                        Waits for the output.
+ *   sv_clifford_destroy  frees the handle.
+ */
+typedef struct sv_clifford sv_clifford;
+sv_status sv_clifford_create(int n, const sv_op* ops, size_t n_ops, void* cuda_stream, sv_clifford** out);
+sv_status sv_clifford_sample(sv_clifford* c, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                             uint64_t* creg_out);
+sv_status sv_clifford_destroy(sv_clifford* c);
+
+/*
  * Shot branching on the batched engine: n_requests requests, request r
  * running program prog_ids[r] with Philox stream stream_ids[r] for
  * n_shots[r] shots (counters 0 .. n_shots[r]-1).  creg_out receives the

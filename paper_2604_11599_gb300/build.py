@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libsv.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["kern_pass.cu", "kern_measure.cu", "kern_batch.cu", "kern_adjoint.cu", "sv_api.cu", "planner.cpp",
-           "expval_static.cu", "jit.cpp", "kern_branch.cu"]
+           "expval_static.cu", "jit.cpp", "kern_branch.cu", "kern_clifford.cu"]
 # headers compiled again at run time by the pass specialiser (jit.cpp); embedded as strings
 JIT_HEADERS = [("pass_body.cuh", "csrc/pass_body.cuh"), ("dev_common.cuh", "csrc/dev_common.cuh"),
                ("dev_tc.cuh", "csrc/dev_tc.cuh"),

@@ -79,6 +79,9 @@ def lib():
         "sv_sample_state": ([vp, u64, u64, u64, u64, vp], st),
         "sv_sample_branched": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, C.POINTER(BranchStats)], st),
         "sv_batch_sample_branched": ([vp, vp, vp, vp, sz, u64, vp, C.POINTER(BranchStats)], st),
+        "sv_clifford_create": ([i32, vp, sz, vp, C.POINTER(vp)], st),
+        "sv_clifford_sample": ([vp, u64, u64, u64, u64, vp], st),
+        "sv_clifford_destroy": ([vp], st),
         "sv_expval": ([vp, vp, sz, vp, vp], st),
         "sv_expval_static": ([vp, i32, i32, vp, sz, vp, vp], st),
         "sv_get_amplitudes": ([vp, vp, sz, sz], st),
@@ -410,6 +413,43 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().sv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Clifford:
+    """Clifford programs on up to 64 qubits by stabilizer tableaux, one warp per
+    shot (``sv_clifford_*``)."""
+
+    def __init__(self, n: int, ops: np.ndarray, stream=None):
+        ops = _ops(ops)
+        torch = _torch()
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        _check(lib().sv_clifford_create(n, _ptr(ops), len(ops), stream, C.byref(h)))
+        self._h = h.value
+        self.n = n
+
+    def sample(self, shots: int, seed: int = 0, stream_id: int = 0, shot0: int = 0) -> np.ndarray:
+        out = np.zeros(shots, dtype=np.uint64)
+        _check(lib().sv_clifford_sample(self._h, shots, seed, stream_id, shot0, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_clifford_destroy(self._h)
             self._h = None
 
     def __del__(self):
