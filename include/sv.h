@@ -299,6 +299,14 @@ sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* st
 sv_status sv_batch_destroy(sv_batch* b);
 
 /*
+ * Planner tuning of the programs added to the batch after this call: the
+ * tile is fixed at 2^12 amplitudes by the batched kernel; low_bits (3..12,
+ * contiguous low qubits of a tile) and max_pass_gates (0..128, gates fused
+ * into one pass) as in sv_set_tuning; 0 = default.  SV_ERR_ARG out of range.
+ */
+sv_status sv_batch_set_tuning(sv_batch* b, int low_bits, int max_pass_gates);
+
+/*
  * Clifford fast path: programs whose gates are all Clifford (I, H, X, Y, Z,
  * S, SDG, SX, CX, CY, CZ, SWAP) with MEASURE, RESET, COND and LOOP records,
  * on 1 <= n <= 64 qubits, sampled by stabilizer tableaux (Aaronson and

@@ -717,6 +717,7 @@ struct sv_batch {
   // shot branching
   std::vector<uint32_t> prog_draws;  // draw items of each program (a bound on the draws a trajectory executes)
   std::vector<svk::BatchItem> items_host;  // staging of the last quick item upload
+  int tune_low = 0, tune_gates = 0;           // planner tuning of programs added from now on (0: default)
   DevBuf<DTrace> tslots;
   DevBuf<svk::BrDraw> tout;
   DevBuf<uint64_t> mout;
@@ -765,6 +766,8 @@ sv_status sv_batch_add_program(sv_batch* b, int n, const sv_op* ops, size_t n_op
   svp::Tuning t;
   t.tile_bits = svk::BATCH_TILE_BITS;
   t.min_qubits = svk::BATCH_TILE_BITS;
+  if (b->tune_low) t.low_bits = b->tune_low;
+  t.max_pass_gates = b->tune_gates;
   std::string err;
   sv_status st = svp::build_plan(n, b->dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, t, p->plan, err);
   if (st != SV_OK) return fail(st, err);
@@ -945,6 +948,16 @@ sv_status sv_batch_run(sv_batch* b, const uint32_t* prog_ids, const uint64_t* st
   st = sv_batch_launch(b, seed);
   if (st != SV_OK) return st;
   return sv_batch_results(b, creg_out);
+}
+
+sv_status sv_batch_set_tuning(sv_batch* b, int low_bits, int max_pass_gates) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  if (low_bits && (low_bits < 3 || low_bits > svk::BATCH_TILE_BITS))
+    return fail(SV_ERR_ARG, "low_bits in 3..12 (tile_bits - low_bits <= 9)");
+  if (max_pass_gates < 0 || max_pass_gates > svp::MAX_PASS_GATES) return fail(SV_ERR_ARG, "max_pass_gates in 0..128");
+  b->tune_low = low_bits;
+  b->tune_gates = max_pass_gates;
+  return SV_OK;
 }
 
 sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids,

@@ -103,6 +103,7 @@ def lib():
         "sv_batch_results": ([vp, vp], st),
         "sv_batch_run": ([vp, vp, vp, vp, sz, u64, vp], st),
         "sv_batch_destroy": ([vp], st),
+        "sv_batch_set_tuning": ([vp, i32, i32], st),
         "sv_grad_create": ([i32, i32, vp, sz, vp, sz, vp, sz, vp, C.POINTER(vp)], st),
         "sv_grad_run": ([vp, vp, sz, sz, vp, vp], st),
         "sv_grad_destroy": ([vp], st),
@@ -371,6 +372,10 @@ class Batch:
         _check(lib().sv_batch_add_program(self._h, n, _ptr(ops), len(ops), _ptr(p), 0 if p is None else p.size,
                                           _ptr(pl), 0 if pl is None else pl.size, C.byref(pid)))
         return int(pid.value)
+
+    def set_tuning(self, low_bits: int = 0, max_pass_gates: int = 0) -> None:
+        """Planner tuning of programs added from now on (``sv_batch_set_tuning``)."""
+        _check(lib().sv_batch_set_tuning(self._h, low_bits, max_pass_gates))
 
     def set_items(self, prog_ids, stream_ids, shots) -> None:
         pr = np.ascontiguousarray(prog_ids, dtype=np.uint32)
