@@ -803,15 +803,23 @@ def _main(argv: Optional[Sequence[str]] = None) -> int:
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--param", type=float, action="append", default=[], help="input values, in declaration order")
+    ap.add_argument("--engine", default="branched", choices=["branched", "per-shot", "clifford"],
+                    help="branched: one trajectory per distinct outcome path (the same records as per-shot); "
+                         "clifford: stabilizer tableaux (Clifford gates only, up to 64 qubits)")
     a = ap.parse_args(argv)
     with open(a.file) as f:
         prog = lower(f.read())
     from . import sv
 
-    with sv.State(prog.n_qubits, a.dtype) as st:
-        if len(prog.pool):
-            st.set_dense_pool(prog.pool)
-        cregs, _ = st.sample(prog.ops, a.shots, params=a.param or None, seed=a.seed)
+    if a.engine == "clifford":
+        with sv.Clifford(prog.n_qubits, prog.ops) as cl:
+            cregs = cl.sample(a.shots, seed=a.seed)
+    else:
+        with sv.State(prog.n_qubits, a.dtype) as st:
+            if len(prog.pool):
+                st.set_dense_pool(prog.pool)
+            run = st.sample_branched if a.engine == "branched" else st.sample
+            cregs, _ = run(prog.ops, a.shots, params=a.param or None, seed=a.seed)
     counts: Dict[str, int] = {}
     for v in cregs:
         key = format(int(v), f"0{max(1, prog.n_bits)}b")
