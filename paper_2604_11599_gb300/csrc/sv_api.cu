@@ -818,20 +818,10 @@ sv_status sv_batch_add_program(sv_batch* b, int n, const sv_op* ops, size_t n_op
   return SV_OK;
 }
 
-namespace {
-// quick: no wait for the upload and no device-memory query while the slots already fit
-sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
-                      size_t n_items, bool quick);
-}  // namespace
-
-sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
-                             size_t n_items) {
-  return batch_items(b, prog_ids, stream_ids, shots, n_items, false);
-}
-
 }  // extern "C"
 
 namespace {
+// quick: no wait for the upload and no device-memory query while the slots already fit
 sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
                       size_t n_items, bool quick) {
   if (!b) return fail(SV_ERR_ARG, "null handle");
@@ -883,6 +873,11 @@ sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* str
 }  // namespace
 
 extern "C" {
+
+sv_status sv_batch_set_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids, const uint64_t* shots,
+                             size_t n_items) {
+  return batch_items(b, prog_ids, stream_ids, shots, n_items, false);
+}
 
 sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   if (!b) return fail(SV_ERR_ARG, "null handle");
