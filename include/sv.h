@@ -219,7 +219,9 @@ sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* p
  * (nullable) reports shots, paths, walk rounds and the longest path.
  * SV_ERR_UNSUPPORTED when a trajectory executes more than 4096 draws or
  * shots >= 2^32 - 1; SV_ERR_NUMERIC as for sv_run.  The state holds the last
- * representative's final state afterwards.  Waits for the output.
+ * representative's final state afterwards.  Device scratch (8 bytes per shot
+ * plus 24 bytes per recorded draw) is allocated on first use, grows as needed
+ * and is kept with the handle.  Waits for the output.
  */
 sv_status sv_sample_branched(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
                              uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
@@ -339,8 +341,10 @@ sv_status sv_clifford_destroy(sv_clifford* c);
  * records request after request (sum of n_shots entries), each equal to
  * the record sv_batch_run gives that (program, stream, shot).  The
  * representatives of each walk round run together in one persistent
- * launch.  Replaces the batch's current items.  Errors as for
- * sv_sample_branched and sv_batch_run.
+ * launch.  Replaces the batch's current items.  Besides the walk's scratch,
+ * the first call allocates 4,096 draw records per resident CTA (128 KiB each)
+ * and keeps them with the handle.  Errors as for sv_sample_branched and
+ * sv_batch_run.
  */
 sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const uint64_t* stream_ids,
                                    const uint64_t* n_shots, size_t n_requests, uint64_t seed, uint64_t* creg_out,
