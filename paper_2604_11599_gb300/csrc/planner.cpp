@@ -738,59 +738,74 @@ int check_barriers(const Plan& P, uint64_t* warp_syncs, uint64_t* block_syncs) {
   const int B = P.dtype == SV_C64 ? 1 : 0;
   int bad = 0;
   *warp_syncs = *block_syncs = 0;
+  // warp that touches each tile address: in the tile copy (per tile geometry) and in each stage
+  std::vector<int8_t> copy_own, first, prev, cur;
+  std::vector<uint8_t> cnt;
+  std::vector<uint32_t> base;
+  int cm = -1, cL = -1;
+  auto stage_own = [&](const DStage& st, int m, std::vector<int8_t>& own) {
+    const uint32_t T = 1u << m;
+    own.assign(T, int8_t(-1));
+    cnt.assign(T, 0);
+    uint32_t off[1 << REG_BITS];  // register offsets: XOR of R over the set bits of j
+    off[0] = 0;
+    for (int j = 1; j < (1 << REG_BITS); ++j) off[j] = off[j & (j - 1)] ^ st.R[__builtin_ctz(unsigned(j))];
+    const int G = int(T >> REG_BITS);
+    base.assign(size_t(G), 0);  // group bases: XOR of E over the set bits of g
+    for (int g = 1; g < G; ++g) base[size_t(g)] = base[size_t(g & (g - 1))] ^ st.E[__builtin_ctz(unsigned(g))];
+    for (int g = 0; g < G; ++g) {
+      const int8_t w = int8_t((g % PASS_THREADS) >> 5);
+      for (int j = 0; j < (1 << REG_BITS); ++j) {
+        const uint32_t a = base[size_t(g)] ^ off[j];
+        if (a >= T) {
+          ++bad;
+          continue;
+        }
+        if (cnt[a] < 255) ++cnt[a];
+        own[a] = w;
+      }
+    }
+    for (uint32_t a = 0; a < T; ++a) bad += cnt[a] != 1;
+  };
   for (const DPass& ps : P.passes) {
     if (ps.ns == 0) continue;
     const int m = ps.m, L = ps.L, T = 1 << m;
-    std::vector<int8_t> copy_own(size_t(T), -1);
-    const int VB = B ? 9 : 8, NVT = 1 << (m - VB), vl = B ? L - 1 : L;
-    for (int t = 0; t < PASS_THREADS; ++t) {
-      const uint32_t wv = uint32_t(t) & ((1u << vl) - 1u);
-      const uint32_t woff = B ? (wv << 1) : wv;
-      for (int k = 0; k < NVT; ++k) {
-        const uint32_t ch = (uint32_t(t) >> vl) + (uint32_t(k) << (VB - L));
-        const uint32_t a = tile_swizzle((ch << L) | woff, B);
-        for (int e = 0; e <= B; ++e) copy_own[a ^ uint32_t(e)] = int8_t(t >> 5);
-      }
-    }
-    std::vector<std::vector<int8_t>> own(ps.ns, std::vector<int8_t>(size_t(T), -1));
-    for (uint32_t si = 0; si < ps.ns; ++si) {
-      const DStage& st = P.stages[ps.s0 + si];
-      std::vector<int> cnt(size_t(T), 0);
-      for (int g = 0; g < (T >> REG_BITS); ++g) {
-        uint32_t b = 0;
-        for (int k = 0; k < m - REG_BITS; ++k)
-          if ((g >> k) & 1) b ^= st.E[k];
-        for (int j = 0; j < (1 << REG_BITS); ++j) {
-          uint32_t a = b;
-          for (int r = 0; r < REG_BITS; ++r)
-            if ((j >> r) & 1) a ^= st.R[r];
-          if (a >= uint32_t(T)) {
-            ++bad;
-            continue;
-          }
-          ++cnt[a];
-          own[si][a] = int8_t((g % PASS_THREADS) >> 5);
+    if (m != cm || L != cL) {
+      copy_own.assign(size_t(T), int8_t(-1));
+      const int VB = B ? 9 : 8, NVT = 1 << (m - VB), vl = B ? L - 1 : L;
+      for (int t = 0; t < PASS_THREADS; ++t) {
+        const uint32_t wv = uint32_t(t) & ((1u << vl) - 1u);
+        const uint32_t woff = B ? (wv << 1) : wv;
+        for (int k = 0; k < NVT; ++k) {
+          const uint32_t ch = (uint32_t(t) >> vl) + (uint32_t(k) << (VB - L));
+          const uint32_t a = tile_swizzle((ch << L) | woff, B);
+          for (int e = 0; e <= B; ++e) copy_own[a ^ uint32_t(e)] = int8_t(t >> 5);
         }
       }
-      for (int a = 0; a < T; ++a) bad += cnt[size_t(a)] != 1;
+      cm = m;
+      cL = L;
     }
-    auto same = [&](const std::vector<int8_t>& x, const std::vector<int8_t>& y) { return x == y; };
+    // every stage's map is checked; consecutive maps are compared where no block barrier separates them
+    for (uint32_t si = 0; si < ps.ns; ++si) {
+      stage_own(P.stages[ps.s0 + si], m, cur);
+      if (si == 0) first = cur;
+      else if (!P.stages[ps.s0 + si - 1].bar) bad += prev != cur;
+      std::swap(prev, cur);
+    }
+    // prev: the last stage's map
     if (ps.bar_in) ++*block_syncs;
     else {
       ++*warp_syncs;
-      bad += !same(copy_own, own[0]);
+      bad += first != copy_own;
       // direct store: the refill of the previous tile's buffer follows its last stage
-      if (ps.direct) bad += !same(own[ps.ns - 1], copy_own);
+      if (ps.direct) bad += prev != copy_own;
     }
     for (uint32_t si = 0; si < ps.ns; ++si) {
-      const DStage& st = P.stages[ps.s0 + si];
-      if (st.bar) {
-        ++*block_syncs;
-        continue;
-      }
-      ++*warp_syncs;
-      if (si + 1 < ps.ns) bad += !same(own[si], own[si + 1]);
-      else if (!ps.direct) bad += !same(own[si], copy_own) || ps.gk != 0;
+      if (P.stages[ps.s0 + si].bar) ++*block_syncs;
+      else ++*warp_syncs;
+    }
+    if (!P.stages[ps.s0 + ps.ns - 1].bar) {
+      if (!ps.direct) bad += (prev != copy_own) || ps.gk != 0;
       else bad += ps.gk != 0;
     }
   }

@@ -130,6 +130,7 @@ class Circuit:
         self.dense_pool: list[np.ndarray] = []
         self._dense_len = 0
         self.n_params = 0
+        self._ops_cache = None  # (record list, its length, concatenated array)
 
     # -- low level -----------------------------------------------------------------
     def _rec(self, kind: Kind) -> np.ndarray:
@@ -206,6 +207,7 @@ class Circuit:
         n2 = len(self._recs)
         self._recs[at]["then_len"] = n1 - n0
         self._recs[at]["else_len"] = n2 - n1
+        self._ops_cache = None
         return self
 
     def loop(self, k: int, body: Callable[[], object]) -> "Circuit":
@@ -215,6 +217,7 @@ class Circuit:
         n0 = len(self._recs)
         body()
         self._recs[at]["body_len"] = len(self._recs) - n0
+        self._ops_cache = None
         return self
 
     # -- standard gates ------------------------------------------------------------
@@ -246,9 +249,16 @@ class Circuit:
     # -- output --------------------------------------------------------------------
     @property
     def ops(self) -> np.ndarray:
+        """The flat record array (a copy; built once per change of the program:
+        appends and header edits invalidate it, and so does replacing the record
+        list)."""
         if not self._recs:
             return np.zeros(0, dtype=OP_DTYPE)
-        return np.concatenate(self._recs)
+        c = self._ops_cache
+        if c is None or c[0] is not self._recs or c[1] != len(self._recs):
+            c = (self._recs, len(self._recs), np.concatenate(self._recs))
+            self._ops_cache = c
+        return c[2].copy()
 
     @property
     def pool(self) -> np.ndarray:
