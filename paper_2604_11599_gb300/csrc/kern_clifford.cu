@@ -324,6 +324,31 @@ struct Lowering {
     }
   }
 
+  // Instructions the records [i0, i1) unroll to, saturating above the limit
+  // (so that an oversized program is refused before anything is emitted).
+  uint64_t count(size_t i0, size_t i1) const {
+    uint64_t c = 0;
+    for (size_t i = i0; i < i1 && c <= CL_MAX_INSTR;) {
+      const sv_op& o = ops[i];
+      if (o.kind == SV_COND) {
+        const size_t t1 = i + 1 + o.then_len, e1 = t1 + o.else_len;
+        if (e1 > i1) return c + 1;  // malformed: block() reports it
+        c += 2 + count(i + 1, t1) + count(t1, e1);
+        i = e1;
+      } else if (o.kind == SV_LOOP) {
+        const size_t b1 = i + 1 + o.body_len;
+        if (b1 > i1) return c + 1;
+        const uint64_t body = count(i + 1, b1);
+        c += (body && o.loop_k > (CL_MAX_INSTR + 1) / body) ? uint64_t(CL_MAX_INSTR) + 1 : body * o.loop_k;
+        i = b1;
+      } else {
+        c += (o.kind == SV_GATE && o.gate == SV_CY) ? 3 : 1;
+        ++i;
+      }
+    }
+    return std::min<uint64_t>(c, uint64_t(CL_MAX_INSTR) + 1);
+  }
+
   sv_status block(size_t i0, size_t i1) {
     for (size_t i = i0; i < i1;) {
       const sv_op& o = ops[i];
@@ -425,6 +450,8 @@ sv_status sv_clifford_create(int n, const sv_op* ops, size_t n_ops, void* cuda_s
   if (n < 1 || n > svc::CL_MAXQ) return cl_fail(SV_ERR_ARG, "the Clifford path takes 1 to 64 qubits");
   if (n_ops && !ops) return cl_fail(SV_ERR_ARG, "ops is NULL");
   svc::Lowering L{ops, n, {}, {}};
+  if (L.count(0, n_ops) > svc::CL_MAX_INSTR)
+    return cl_fail(SV_ERR_UNSUPPORTED, "Clifford program longer than 2^24 instructions after unrolling");
   const sv_status s = L.block(0, n_ops);
   if (s != SV_OK) return cl_fail(s, L.err);
   std::unique_ptr<sv_clifford> c(new sv_clifford());
