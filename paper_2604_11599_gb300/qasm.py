@@ -803,15 +803,21 @@ def _main(argv: Optional[Sequence[str]] = None) -> int:
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--param", type=float, action="append", default=[], help="input values, in declaration order")
-    ap.add_argument("--engine", default="branched", choices=["branched", "per-shot", "clifford"],
-                    help="branched: one trajectory per distinct outcome path (the same records as per-shot); "
-                         "clifford: stabilizer tableaux (Clifford gates only, up to 64 qubits)")
+    ap.add_argument("--engine", default="auto", choices=["auto", "branched", "per-shot", "clifford"],
+                    help="auto: tableaux for Clifford programs, else shot branching (batched launch for small "
+                         "programs); branched: one trajectory per distinct outcome path (the same records as "
+                         "per-shot); clifford: stabilizer tableaux (Clifford gates only, up to 64 qubits)")
     a = ap.parse_args(argv)
     with open(a.file) as f:
         prog = lower(f.read())
     from . import sv
 
-    if a.engine == "clifford":
+    if a.engine == "auto":
+        from . import engines
+
+        cregs, _ = engines.sample(prog.ops, prog.n_qubits, a.shots, dtype=a.dtype, params=a.param or None,
+                                  pool=prog.pool if len(prog.pool) else None, seed=a.seed)
+    elif a.engine == "clifford":
         with sv.Clifford(prog.n_qubits, prog.ops) as cl:
             cregs = cl.sample(a.shots, seed=a.seed)
     else:
