@@ -32,6 +32,15 @@ def test_library_exports_every_declared_symbol():
     assert lib.sv_version().startswith(b"libsv")
 
 
+def test_binding_covers_every_declared_symbol():
+    """The Python binding gives every declared entry point a ctypes signature."""
+    from paper_2604_11599_gb300 import sv
+
+    L = sv.lib()
+    unbound = [n for n in declared_functions() if getattr(L, n).argtypes is None]
+    assert not unbound, unbound
+
+
 def test_op_record_layout_matches_header():
     """sv_op is 120 bytes in both the header (C compiler) and the IR dtype."""
     import subprocess
