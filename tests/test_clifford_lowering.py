@@ -65,3 +65,18 @@ def test_unroll_limit(svmod):
     c.loop(1 << 16, lambda: c.loop(1 << 9, lambda: c.h(0)))  # 2^25 instructions
     assert int(c.ops[0]["kind"]) == int(Kind.LOOP)
     _refused(svmod, 2, c.ops, "SV_ERR_UNSUPPORTED")
+
+
+def test_valid_programs_pass_the_lowering(svmod):
+    """Large valid programs (63 and 64 qubits, feed-forward, loops) pass the
+    size check and the lowering; without a GPU the first device call fails."""
+    import torch
+
+    from paper_2604_11599_gb300 import workloads as W
+
+    if torch.cuda.is_available():
+        pytest.skip("with a GPU the handle is created (covered by the GPU tests)")
+    for c, n in ((W.repetition_code(32, 10, flip_every=1, ghz=True), 63),
+                 (W.random_clifford_dynamic(21, 64, n_ops=150), 64)):
+        with pytest.raises(svmod.SVError, match="SV_ERR_CUDA"):
+            svmod.Clifford(n, c.ops)
