@@ -4,10 +4,10 @@
  * and bounded loops, with feed-forward decided on the GPU.
  *
  * The operations follow the paper's statement of the problem (arXiv
- * 2604.11599): OpenQASM 3.0 programs with "classical control structures
- * (conditionals and bounded loops)" and mid-circuit measurement (Abstract);
- * `if` statements executed as "true classical feedforward rather than
- * pre-calculated branching" (Sec. III-C); `input` parameters resolved at run
+ * 2604.11599): OpenQASM 3.0 programs with classical control (if/else and
+ * loops with a fixed trip count) and mid-circuit measurement (Abstract);
+ * `if` statements decided at run time from the measured bits, with no branch
+ * simulated ahead of time (Sec. III-C); `input` parameters resolved at run
  * time so that a kernel is compiled once and run many times (Sec. III-D);
  * energies <H> for VQE (Sec. IV-A.2, IV-D); repeated shots (Sec. IV-C).
  *

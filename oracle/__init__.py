@@ -8,7 +8,7 @@ from the product package: it reads op lists as raw 120-byte records (the
 
 The C source (``sv_oracle.c``) is the plain amplitude-loop definition; this
 wrapper adds the gradient checks built from it (parameter shift and central
-finite differences, Sec. IV-D's "algorithmic parity" of energies).
+finite differences; Sec. IV-D checks that energies agree across backends).
 
 Pinned by tests/test_oracle_*.py against closed forms, numpy's independent
 Philox, scipy matrix exponentials and dense Kronecker products.

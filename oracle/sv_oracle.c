@@ -8,11 +8,12 @@
  *
  * What it computes is the plain textbook definition of a state-vector
  * trajectory of a dynamic circuit, as the paper uses it: gates act on the
- * amplitude vector; a mid-circuit measurement collapses the state (Sec. II-C,
- * Fig. 2 and its text); an `if` on classical bits is decided from the
- * measured record at run time, "true classical feedforward rather than
- * pre-calculated branching" (Sec. III-C); bounded loops are run by repetition
- * (Abstract); runtime `input` parameters supply angles (Sec. III-D).  Every
+ * amplitude vector; a mid-circuit measurement projects the state onto the
+ * observed outcome (Sec. II-C, Fig. 2 and its text); an `if` on classical
+ * bits is decided from the measured record while the trajectory runs, not by
+ * simulating every branch in advance (Sec. III-C); loops with a fixed trip
+ * count are run by repetition (Abstract); runtime `input` parameters supply
+ * angles (Sec. III-D).  Every
  * loop below is written for obviousness, not speed: one pass over the vector
  * per gate, FP64 complex arithmetic, sums in a fixed left-to-right chunked
  * order so that results do not depend on the thread count.

@@ -6,7 +6,7 @@
 //    flags are evaluated on the device from the classical register when the
 //    COND is reached, so branches are decided by feed-forward on the GPU and
 //    never duplicated into outcome-specific copies (Sec. III-C); loops
-//    (Abstract: "bounded loops") are repeated.
+//    (Abstract: loops with a fixed trip count) are repeated.
 // 2. Segment: a measurement group is a run of measure/reset items with no
 //    gate between them on at most four distinct qubits.  The gates before a
 //    group are swept in passes; the last pass also accumulates the group's

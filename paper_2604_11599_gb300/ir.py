@@ -9,8 +9,8 @@ oracle).
 The vocabulary follows the paper's statement of what the transpiler must carry
 (Sec. III-B: standard gates and ``ctrl``/``inv`` modifiers; Sec. III-C:
 ``if`` on classical bits turned into device-side feed-forward; Sec. III-D:
-``input`` parameters resolved at run time, "compile once, run many"; Abstract:
-conditionals and bounded loops):
+``input`` parameters resolved at run time, so one compiled program serves
+every parameter set; Abstract: conditionals and loops with a fixed trip count):
 
 * ``GATE``     -- one standard gate (``Gate`` enum) on ``q[0..]``; each of its up
                   to three angles is a literal or ``scale * params[idx]``.
