@@ -12,10 +12,12 @@ which every engine of the library runs:
   float[64] theta;`` / ``input angle theta;`` (run-time parameters, in order of
   declaration), ``const float x = <expr>;``;
 * gates: the standard library (h x y z s sdg t tdg sx id rx ry rz p phase u U u1
-  u2 u3 cx CX cy cz ch swap cp cphase crx cry crz cu ccx cswap), a whole register
-  as an operand broadcasts the gate over its qubits, ``gate`` definitions are
-  expanded inline, and the modifiers ``ctrl @`` / ``ctrl(k) @``, ``inv @`` and
-  ``pow(k) @`` (integer k >= 0);
+  u2 u3 cx CX cy cz ch swap cp cphase crx cry crz cu ccx cswap, and ``gphase``),
+  the two-qubit rotations exporters emit (rxx ryy rzz rzx) and sxdg, a whole
+  register as an operand broadcasts the gate over its qubits, ``gate``
+  definitions are expanded inline, and the modifiers ``ctrl @`` / ``ctrl(k) @``,
+  ``negctrl @`` / ``negctrl(k) @`` (control on |0>: X before and after on that
+  qubit), ``inv @`` and ``pow(k) @`` (integer k >= 0);
 * ``c[i] = measure q[j];``, ``measure q[j] -> c[i];``, ``c = measure q;``,
   ``reset q;``, ``barrier ...;`` (ignored);
 * ``if (c[i] == b)``, ``if (c == v)``, ``if (c[i])``, ``if (!c[i])``, ``!=``,
@@ -614,10 +616,8 @@ class _Lowerer:
         mods: List[Tuple[str, int]] = []
         while self.peek().text in ("ctrl", "inv", "pow", "negctrl"):
             m = self.next().text
-            if m == "negctrl":
-                raise self.err("negctrl is not supported")
             k = 1
-            if m in ("ctrl", "pow") and self.accept("("):
+            if m in ("ctrl", "negctrl", "pow") and self.accept("("):
                 k = self.int_expr(env)
                 self.expect(")")
             self.expect("@")
@@ -631,6 +631,10 @@ class _Lowerer:
                 while self.accept(","):
                     args.append(self.expr(env))
                 self.expect(")")
+        if name == "gphase" and self.peek().text == ";":  # a global phase takes no qubits
+            self.expect(";")
+            self.apply(name, args, [], mods, out, tok)
+            return
         operands = [self.qoperand(env, qmap)]
         while self.accept(","):
             operands.append(self.qoperand(env, qmap))
@@ -659,11 +663,25 @@ class _Lowerer:
                 inv = not inv
             else:
                 n_ctrl += k
-        if n_ctrl >= len(qs):
+        # control qubits come first, in the order of their modifiers; negctrl ones act on |0>
+        neg, at = [], 0
+        for m, k in mods:
+            if m in ("ctrl", "negctrl"):
+                if m == "negctrl":
+                    neg += qs[at: at + k]
+                at += k
+        if name == "gphase":
+            if n_ctrl != len(qs):
+                raise self.err("gphase takes control qubits only", tok)
+        elif n_ctrl >= len(qs):
             raise self.err("more controls than qubits", tok)
         ctrls, targets = qs[:n_ctrl], qs[n_ctrl:]
+        for q in neg:
+            out.append((lambda q: lambda c: c.x(q))(q))
         for _ in range(reps):
             self.apply_one(name, args, ctrls, targets, inv, out, tok)
+        for q in neg:
+            out.append((lambda q: lambda c: c.x(q))(q))
 
     def apply_one(self, name, args, ctrls, targets, inv, out, tok) -> None:
         if name in self.gates:
@@ -672,6 +690,38 @@ class _Lowerer:
             self.expand(name, args, targets, inv, out, tok)
             return
         if name in ("id", "I"):
+            return
+        if name == "gphase":  # e^{i theta}: a phase on the controls, exact even without them
+            if len(args) != 1:
+                raise self.err("gphase takes one angle", tok)
+            th = -args[0] if inv else args[0]
+            if ctrls:
+                self.emit1(Gate.P, [th.angle()], ctrls[:-1], ctrls[-1], out, tok)
+            elif self.nq:
+                for g in (Gate.P, Gate.X, Gate.P, Gate.X):  # P(t) X P(t) X = e^{it} I on qubit 0
+                    self.emit1(g, [th.angle()] if g == Gate.P else [], [], 0, out, tok)
+            return
+        if name == "sxdg":
+            if args or len(targets) != 1:
+                raise self.err("sxdg takes one qubit", tok)
+            self.apply_one("sx", args, ctrls, targets, not inv, out, tok)
+            return
+        if name in ("rzz", "rxx", "ryy", "rzx"):  # exp(-i t/2 P_a P_b) = basis change, CX, RZ(t), CX, back
+            if len(args) != 1 or len(targets) != 2:
+                raise self.err(f"{name} takes one angle and two qubits", tok)
+            a, b = targets
+            th = -args[0] if inv else args[0]
+            pre = {"rzz": [], "rxx": [(Gate.H, [], a), (Gate.H, [], b)],
+                   "ryy": [(Gate.RX, [math.pi / 2], a), (Gate.RX, [math.pi / 2], b)],
+                   "rzx": [(Gate.H, [], b)]}[name]
+            post = [(g, [-v for v in ang], q) for g, ang, q in pre]
+            for g, ang, q in pre:
+                self.emit1(g, ang, [], q, out, tok)
+            self.emit1(Gate.X, [], [a], b, out, tok)
+            self.emit1(Gate.RZ, [th.angle()], ctrls, b, out, tok)
+            self.emit1(Gate.X, [], [a], b, out, tok)
+            for g, ang, q in post:
+                self.emit1(g, ang, [], q, out, tok)
             return
         if name == "u2":
             name, args = "u", [Lin(math.pi / 2)] + list(args)

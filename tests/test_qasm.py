@@ -174,6 +174,86 @@ def test_teleportation_program(orc):
         assert np.sum(np.abs(psi[1]) ** 2) < 1e-24
 
 
+def _apply(psi, u, qubits):
+    """u (local index bit r <-> qubits[r]) applied to a little-endian state."""
+    n = int(round(math.log2(psi.size)))
+    k = len(qubits)
+    out = np.zeros_like(psi)
+    for i in range(psi.size):
+        loc = sum(((i >> q) & 1) << r for r, q in enumerate(qubits))
+        rest = i & ~sum(1 << q for q in qubits)
+        for j in range(1 << k):
+            tgt = rest | sum(((j >> r) & 1) << q for r, q in enumerate(qubits))
+            out[tgt] += u[j, loc] * psi[i]
+    assert n >= k
+    return out
+
+
+_PREP = "OPENQASM 3; qubit[3] q; ry(0.7) q[0]; rx(1.1) q[1]; u(0.4, 0.9, -0.3) q[2]; cx q[0], q[2]; "
+
+
+def _pauli(c):
+    return {"X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+            "Z": np.array([[1, 0], [0, -1]])}[c].astype(np.complex128)
+
+
+@pytest.mark.parametrize("stmt,u,qubits", [
+    ("rzz(0.8) q[0], q[2];", None, (0, 2)),
+    ("rxx(0.8) q[1], q[0];", None, (1, 0)),
+    ("ryy(0.8) q[2], q[1];", None, (2, 1)),
+    ("rzx(0.8) q[0], q[1];", None, (0, 1)),
+    ("inv @ rzz(0.8) q[0], q[2];", "inv", (0, 2)),
+    ("sxdg q[1];", "sxdg", (1,)),
+    ("negctrl @ x q[0], q[1];", "negx", (0, 1)),
+    ("negctrl @ ctrl @ x q[2], q[0], q[1];", "negctrl-ctrl-x", (2, 0, 1)),
+    ("ctrl @ gphase(0.6) q[1];", "cphase", (1,)),
+    ("gphase(0.6);", "global", ()),
+])
+def test_extra_gates_and_modifiers_against_matrices(orc, stmt, u, qubits):
+    """Each construct against its matrix applied to the state the prefix prepares."""
+    psi0 = orc.run(qasm.lower(_PREP).ops, 3).psi
+    prog = qasm.lower(_PREP + stmt)
+    got = orc.run(prog.ops, 3, pool=prog.pool).psi
+    t = 0.8
+    name = stmt.split("(")[0].split()[0]
+    if u is None or u == "inv":
+        if u == "inv":
+            t, name = -t, "rzz"
+        pa, pb = {"rzz": "ZZ", "rxx": "XX", "ryy": "YY", "rzx": "ZX"}[name]
+        pp = np.kron(_pauli(pb), _pauli(pa))  # local bit 0 <-> first qubit
+        m = math.cos(t / 2) * np.eye(4) - 1j * math.sin(t / 2) * pp
+        want = _apply(psi0, m, qubits)
+    elif u == "sxdg":
+        sx = np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]]) / 2
+        want = _apply(psi0, sx.conj().T, qubits)
+    elif u == "negx":  # X on the target when the control is |0>
+        m = np.eye(4, dtype=np.complex128)
+        m[[0, 2]] = m[[2, 0]]
+        want = _apply(psi0, m, qubits)
+    elif u == "negctrl-ctrl-x":  # X on q[1] when q[2] = 0 and q[0] = 1
+        m = np.eye(8, dtype=np.complex128)
+        a, b = 0b010, 0b110  # local bits: r0 = q2 (0), r1 = q0 (1), r2 = target
+        m[[a, b]] = m[[b, a]]
+        want = _apply(psi0, m, qubits)
+    elif u == "cphase":
+        want = _apply(psi0, np.diag([1, np.exp(0.6j)]), qubits)
+    else:
+        want = np.exp(0.6j) * psi0
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_extra_forms_lower_to_records():
+    p = qasm.lower("OPENQASM 3; qubit[3] q; negctrl(2) @ x q[0], q[1], q[2];")
+    kinds = [int(k) for k in p.ops["kind"]]
+    assert kinds == [int(Kind.GATE)] * 2 + [int(Kind.DENSE)] + [int(Kind.GATE)] * 2
+    assert [int(g) for g in p.ops["gate"][[0, 1, 3, 4]]] == [int(Gate.X)] * 4
+    p = qasm.lower("OPENQASM 3; input float t; qubit[2] q; rzz(t) q[0], q[1];")
+    rz = p.ops[p.ops["gate"] == int(Gate.RZ)]
+    assert len(rz) == 1 and int(rz[0]["pidx"][0]) == 0 and int(rz[0]["q"][0]) == 1
+    with pytest.raises(qasm.QasmError):
+        qasm.lower("OPENQASM 3; qubit[2] q; gphase(0.1) q[0];")  # gphase takes controls only
+
+
 def test_errors_name_the_line():
     with pytest.raises(qasm.QasmError, match="line 3"):
         qasm.lower("qubit q;\nh q;\nfoo q;\n")
