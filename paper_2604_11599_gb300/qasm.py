@@ -17,9 +17,14 @@ which every engine of the library runs:
   register as an operand broadcasts the gate over its qubits, ``gate``
   definitions are expanded inline, and the modifiers ``ctrl @`` / ``ctrl(k) @``,
   ``negctrl @`` / ``negctrl(k) @`` (control on |0>: X before and after on that
-  qubit), ``inv @`` and ``pow(k) @`` (integer k >= 0);
+  qubit), ``inv @`` and ``pow(k) @`` (integer k >= 0), on standard and on user
+  gates (a user gate's body is inverted record by record in reverse order, or
+  controlled record by record);
+* operands ``q``, ``q[i]`` and inclusive slices ``q[a:b]`` / ``q[a:s:b]``;
 * ``c[i] = measure q[j];``, ``measure q[j] -> c[i];``, ``c = measure q;``,
-  ``reset q;``, ``barrier ...;`` (ignored);
+  ``bit[n] c = measure q;``, ``measure q;`` (result into bit 63, which the
+  program must leave undeclared), ``reset q;``, ``barrier ...;`` and
+  ``delay[...] ...;`` (no effect on the state);
 * ``if (c[i] == b)``, ``if (c == v)``, ``if (c[i])``, ``if (!c[i])``, ``!=``,
   with an optional ``else``: one COND record, predicate read on the device;
 * ``for uint i in [a:b]`` / ``[a:s:b]`` / ``{v, ...}``: a LOOP record when the
@@ -40,7 +45,7 @@ from typing import Callable, Dict, List, Optional, Sequence, Tuple, Union
 
 import numpy as np
 
-from .ir import Circuit, Gate, Param
+from .ir import GATE_ARITY, Circuit, Gate, Kind, Param
 
 
 class QasmError(ValueError):
@@ -145,6 +150,9 @@ class Program:
         return self.circuit.pool
 
 
+# a measurement whose result is discarded (``measure q;``) writes this bit
+HIDDEN_BIT = 63
+
 # one-qubit standard gates: IR gate, number of angles
 _G1 = {"h": (Gate.H, 0), "x": (Gate.X, 0), "y": (Gate.Y, 0), "z": (Gate.Z, 0), "s": (Gate.S, 0),
        "sdg": (Gate.SDG, 0), "t": (Gate.T, 0), "tdg": (Gate.TDG, 0), "sx": (Gate.SX, 0),
@@ -186,6 +194,38 @@ def _gate_matrix(g: Gate, a: Sequence[float]) -> np.ndarray:
     if g == Gate.U:
         return _u_matrix(*a)
     raise QasmError(f"no matrix for {g.name}")
+
+
+def _controlled_k(m: np.ndarray, nc: int) -> np.ndarray:
+    """A 2^k x 2^k unitary with nc controls in front: local bits 0..nc-1 are the
+    controls, nc.. the unitary's qubits; it acts when every control bit is 1."""
+    d = m.shape[0]
+    out = np.eye(d << nc, dtype=np.complex128)
+    cm = (1 << nc) - 1
+    for a in range(d):
+        for b in range(d):
+            out[cm | (a << nc), cm | (b << nc)] = m[a, b]
+    return out
+
+
+def _neg(a):
+    return Param(a.idx, -a.scale) if isinstance(a, Param) else -a
+
+
+def _inverse1(g: Gate, angles: List) -> Tuple[Gate, List]:
+    """Inverse of a one-qubit IR gate with its angles (literals or parameter references)."""
+    if g in (Gate.H, Gate.X, Gate.Y, Gate.Z):
+        return g, []
+    pairs = {Gate.S: Gate.SDG, Gate.SDG: Gate.S, Gate.T: Gate.TDG, Gate.TDG: Gate.T}
+    if g in pairs:
+        return pairs[g], []
+    if g in (Gate.RX, Gate.RY, Gate.RZ, Gate.P):
+        return g, [_neg(angles[0])]
+    if g == Gate.U:  # U(t, p, l)^dagger = U(-t, -l, -p)
+        return g, [_neg(angles[0]), _neg(angles[2]), _neg(angles[1])]
+    if g == Gate.SX:
+        return Gate.SX, ["inverse"]
+    raise QasmError(f"no inverse for {g.name}")
 
 
 def _controlled(m: np.ndarray, k: int) -> np.ndarray:
@@ -333,12 +373,26 @@ class _Lowerer:
         else:
             raise self.err(f"unknown qubit {name!r}")
         if self.accept("["):
-            k = self.int_expr(env)
-            self.expect("]")
-            if not 0 <= k < len(regs):
-                raise self.err(f"index {k} outside {name}[{len(regs)}]")
-            return [regs[k]]
+            return [regs[k] for k in self.index_or_slice(env, name, len(regs))]
         return list(regs)
+
+    def index_or_slice(self, env, name: str, size: int) -> List[int]:
+        """After '[': one index, or an inclusive slice a:b / a:s:b (OpenQASM 3 ranges)."""
+        k = self.int_expr(env)
+        ks = [k]
+        if self.accept(":"):
+            e = self.int_expr(env)
+            step = 1
+            if self.accept(":"):
+                step, e = e, self.int_expr(env)
+            if step == 0:
+                raise self.err("a slice with step 0")
+            ks = list(range(k, e + (1 if step > 0 else -1), step))
+        self.expect("]")
+        for i in ks:
+            if not 0 <= i < size:
+                raise self.err(f"index {i} outside {name}[{size}]")
+        return ks
 
     def coperand(self, env: Dict[str, Lin]) -> List[int]:
         name = self.ident()
@@ -346,11 +400,7 @@ class _Lowerer:
             raise self.err(f"unknown bit {name!r}")
         first, size = self.cregs[name]
         if self.accept("["):
-            k = self.int_expr(env)
-            self.expect("]")
-            if not 0 <= k < size:
-                raise self.err(f"index {k} outside {name}[{size}]")
-            return [first + k]
+            return [first + k for k in self.index_or_slice(env, name, size)]
         return list(range(first, first + size))
 
     # -- program ------------------------------------------------------------------------
@@ -383,14 +433,14 @@ class _Lowerer:
         elif t in ("qubit", "qreg"):
             self.declare_qubits()
         elif t in ("bit", "creg"):
-            self.declare_bits()
+            self.declare_bits(env, qmap, out)
         elif t == "input":
             self.declare_input()
         elif t == "const":
             self.declare_const()
         elif t == "gate":
             self.define_gate()
-        elif t == "barrier":
+        elif t in ("barrier", "delay"):  # no effect on the state (timing only)
             while self.next().text != ";":
                 pass
         elif t == "reset":
@@ -401,6 +451,11 @@ class _Lowerer:
         elif t == "measure":
             self.next()
             qs = self.qoperand(env, qmap)
+            if self.accept(";"):  # result discarded: the draw still happens, into the hidden bit
+                if self.nb >= 64:
+                    raise self.err("a measurement without a destination needs bit 63 free", tok)
+                out.extend((lambda q: lambda c: c.measure(q, HIDDEN_BIT))(q) for q in qs)
+                return
             self.expect("->")
             bs = self.coperand(env)
             self.expect(";")
@@ -442,8 +497,9 @@ class _Lowerer:
         self.qregs[name] = (self.nq, size)
         self.nq += size
 
-    def declare_bits(self) -> None:
+    def declare_bits(self, env=None, qmap=None, out=None) -> None:
         kw = self.next().text
+        tok = self.peek()
         if kw == "bit":
             size = 1
             if self.accept("["):
@@ -455,6 +511,10 @@ class _Lowerer:
             self.expect("[")
             size = self.int_expr({})
             self.expect("]")
+        init = kw == "bit" and self.accept("=")  # bit[n] c = measure q;
+        if init:
+            self.expect("measure")
+            qs = self.qoperand(env or {}, qmap)
         self.expect(";")
         if name in self.cregs or size < 1:
             raise self.err(f"bad bit register {name!r}")
@@ -462,6 +522,8 @@ class _Lowerer:
             raise self.err("more than 64 classical bits")
         self.cregs[name] = (self.nb, size)
         self.nb += size
+        if init:
+            self.emit_measure(qs, list(range(self.nb - size, self.nb)), out, tok)
 
     def declare_input(self) -> None:
         self.next()
@@ -685,9 +747,7 @@ class _Lowerer:
 
     def apply_one(self, name, args, ctrls, targets, inv, out, tok) -> None:
         if name in self.gates:
-            if ctrls:
-                raise self.err("ctrl @ on a user gate is not supported", tok)
-            self.expand(name, args, targets, inv, out, tok)
+            self.expand(name, args, targets, inv, ctrls, out, tok)
             return
         if name in ("id", "I"):
             return
@@ -814,7 +874,7 @@ class _Lowerer:
         qs = list(ctrls) + [target]
         out.append((lambda q, m: lambda c: c.dense(q, m))(qs, m))
 
-    def expand(self, name, args, targets, inv, out, tok) -> None:
+    def expand(self, name, args, targets, inv, ctrls, out, tok) -> None:
         gd = self.gates[name]
         if len(args) != len(gd.params) or len(targets) != len(gd.qargs):
             raise self.err(f"{name} takes {len(gd.params)} angles and {len(gd.qargs)} qubits", tok)
@@ -823,11 +883,58 @@ class _Lowerer:
         body: List[Callable] = []
         sub = _Lowerer(gd.body + [Tok("eof", "", tok.line)])
         sub.qregs, sub.cregs, sub.params, sub.consts, sub.gates = {}, {}, self.params, self.consts, self.gates
+        sub.nq = self.nq
         while sub.peek().kind != "eof":
             sub.gate_call(env, qmap, body)
+        if not inv and not ctrls:
+            out.extend(body)
+            return
+        # inv / ctrl on a user gate: its body as IR records, inverted (reversed, each
+        # record by its inverse) and/or controlled record by record
+        tmp = Circuit(max(self.nq, 1))
+        for f in body:
+            f(tmp)
+        recs, pool = tmp.ops, tmp.pool
         if inv:
-            raise self.err(f"inv @ on the user gate {name!r} is not supported", tok)
-        out.extend(body)
+            recs = recs[::-1]
+        for r in recs:
+            self.emit_record(r, pool, inv, list(ctrls), out, tok)
+
+    def emit_record(self, r, pool, inv: bool, ctrls: List[int], out, tok) -> None:
+        """One GATE or DENSE record of a user gate's body, inverted if `inv`, with
+        the extra controls `ctrls`."""
+        if int(r["kind"]) == int(Kind.DENSE):
+            k = int(r["nq"])
+            qs = [int(q) for q in r["q"][:k]]
+            off = int(r["dense_off"])
+            m = np.asarray(pool[off: off + (1 << (2 * k))]).reshape(1 << k, 1 << k)
+            if inv:
+                m = m.conj().T
+            if ctrls:
+                if len(ctrls) + k > 4:
+                    raise self.err("a dense unitary on more than four qubits", tok)
+                m = _controlled_k(m, len(ctrls))
+                qs = list(ctrls) + qs
+            out.append((lambda q, m: lambda c: c.dense(q, m))(qs, m))
+            return
+        g = Gate(int(r["gate"]))
+        na = GATE_ARITY[g][1]
+        angles = [Param(int(r["pidx"][i]), float(r["angle"][i])) if int(r["pidx"][i]) >= 0 else float(r["angle"][i])
+                  for i in range(na)]
+        qs = [int(q) for q in r["q"][: GATE_ARITY[g][0]]]
+        if g == Gate.SWAP:  # three CX, the middle one reversed: self-inverse in either order
+            a, b = qs
+            for c_, t_ in ((a, b), (b, a), (a, b)):
+                self.emit1(Gate.X, [], ctrls + [c_], t_, out, tok)
+            return
+        base = {Gate.CX: Gate.X, Gate.CY: Gate.Y, Gate.CZ: Gate.Z, Gate.CH: Gate.H, Gate.CP: Gate.P,
+                Gate.CRX: Gate.RX, Gate.CRY: Gate.RY, Gate.CRZ: Gate.RZ, Gate.CU: Gate.U}.get(g)
+        inner = [qs[0]] if base is not None else []
+        target = qs[-1]
+        b = base if base is not None else g
+        if inv:
+            b, angles = _inverse1(b, angles)
+        self.emit1(b, angles, ctrls + inner, target, out, tok)
 
 
 def lower(src: str) -> Program:

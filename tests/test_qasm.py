@@ -242,6 +242,53 @@ def test_extra_gates_and_modifiers_against_matrices(orc, stmt, u, qubits):
     assert np.max(np.abs(got - want)) < 1e-12
 
 
+_GDEF = ("gate g(x) a, b { s a; h b; cx a, b; rz(x) b; sx a; swap a, b; t b; u(0.3, 0.2, 0.1) a; "
+         "ctrl @ ry(0.4) b, a; } ")
+
+
+def test_inverse_of_a_user_gate(orc):
+    """g then inv @ g gives back the prepared state (records reversed, each inverted)."""
+    src = _PREP.replace("qubit[3] q; ", "qubit[3] q; " + _GDEF)
+    psi0 = orc.run(qasm.lower(src).ops, 3).psi
+    prog = qasm.lower(src + "g(0.7) q[0], q[2]; inv @ g(0.7) q[0], q[2];")
+    psi = orc.run(prog.ops, 3, pool=prog.pool).psi
+    assert np.max(np.abs(psi - psi0)) < 1e-12
+    prog = qasm.lower(src + "inv @ g(0.7) q[2], q[1]; g(0.7) q[2], q[1];")  # the other order too
+    assert np.max(np.abs(orc.run(prog.ops, 3, pool=prog.pool).psi - psi0)) < 1e-12
+
+
+def test_controlled_user_gate(orc):
+    """ctrl @ g equals diag(I, U) with U, g's unitary, assembled column by column."""
+    head = "OPENQASM 3; qubit[3] q; " + _GDEF
+    u = np.zeros((4, 4), dtype=np.complex128)
+    for col in range(4):  # local bit 0 <-> q[1], bit 1 <-> q[2]
+        prep = "".join(f"x q[{1 + r}]; " for r in range(2) if (col >> r) & 1)
+        prog = qasm.lower(head + prep + "g(0.7) q[1], q[2];")
+        psi = orc.run(prog.ops, 3, pool=prog.pool).psi
+        for row in range(4):
+            u[row, col] = psi[(row & 1) << 1 | (row >> 1) << 2]
+    cu = np.eye(8, dtype=np.complex128)  # local bit 0 <-> q[0] (control), bits 1, 2 <-> q[1], q[2]
+    for a in range(4):
+        for b in range(4):
+            cu[1 | a << 1, 1 | b << 1] = u[a, b]
+    psi0 = orc.run(qasm.lower(_PREP).ops, 3).psi
+    prog = qasm.lower(_PREP.replace("qubit[3] q; ", "qubit[3] q; " + _GDEF) + "ctrl @ g(0.7) q[0], q[1], q[2];")
+    got = orc.run(prog.ops, 3, pool=prog.pool).psi
+    assert np.max(np.abs(got - _apply(psi0, cu, (0, 1, 2)))) < 1e-12
+
+
+def test_measure_forms_slices_and_delay(orc):
+    p = qasm.lower("OPENQASM 3; qubit[4] q; x q[1:3]; delay[20ns] q; bit[2] c = measure q[0:1]; measure q[3];")
+    meas = p.ops[p.ops["kind"] == int(Kind.MEASURE)]
+    assert [(int(o["q"][0]), int(o["cbit"])) for o in meas] == [(0, 0), (1, 1), (3, qasm.HIDDEN_BIT)]
+    r = orc.run(p.ops, 4)
+    assert r.creg == 0b10 | (1 << qasm.HIDDEN_BIT)
+    p = qasm.lower("OPENQASM 3; qubit[4] q; x q[3:-2:0];")  # 3, 1
+    assert [int(o["q"][0]) for o in p.ops] == [3, 1]
+    with pytest.raises(qasm.QasmError):
+        qasm.lower("OPENQASM 3; qubit[2] q; x q[0:5];")
+
+
 def test_extra_forms_lower_to_records():
     p = qasm.lower("OPENQASM 3; qubit[3] q; negctrl(2) @ x q[0], q[1], q[2];")
     kinds = [int(k) for k in p.ops["kind"]]
