@@ -26,7 +26,9 @@ which every engine of the library runs:
   program must leave undeclared), ``reset q;``, ``barrier ...;`` and
   ``delay[...] ...;`` (no effect on the state);
 * ``if (c[i] == b)``, ``if (c == v)``, ``if (c[i])``, ``if (!c[i])``, ``!=``,
-  with an optional ``else``: one COND record, predicate read on the device;
+  ``true`` / ``false``, joined by ``&&`` (one COND predicate) and ``||`` (an
+  if / else-if chain repeating the body), with ``!( ... )`` around the whole
+  condition and an optional ``else``; predicates are read on the device;
 * ``for uint i in [a:b]`` / ``[a:s:b]`` / ``{v, ...}``: a LOOP record when the
   body does not use the loop variable, unrolled otherwise; ``while`` is refused
   (unbounded).
@@ -583,25 +585,88 @@ class _Lowerer:
         out.extend((lambda q, b: lambda c: c.measure(q, b))(q, b) for q, b in zip(qs, bs))
 
     # -- control flow -------------------------------------------------------------------
-    def if_stmt(self, env, qmap, out) -> None:
-        self.next()
-        self.expect("(")
-        neg = self.accept("!")
+    # Conditions: a disjunction (||) of conjunctions (&&) of bit tests and register
+    # equalities.  A conjunction is one COND predicate (mask, value); a disjunction
+    # becomes an if / else-if chain whose branches repeat the body, so exactly one
+    # runs; a leading !( ... ) or a register != swaps the branches.
+    def cond_value(self, env) -> int:
+        if self.peek().text in ("true", "false"):
+            return 1 if self.next().text == "true" else 0
+        return self.int_expr(env)
+
+    def cond_literal(self, env) -> Tuple[int, int, bool]:
+        """(mask, value, negated): one test; negated marks `register != v` on several bits."""
+        if self.accept("!"):
+            bits = self.coperand(env)
+            if len(bits) != 1:
+                raise self.err("'!' applies to a single bit")
+            return 1 << bits[0], 0, False
+        if self.accept("("):
+            terms, neg = self.cond_disj(env)
+            self.expect(")")
+            if len(terms) != 1 or neg:
+                raise self.err("'||' or a register '!=' inside a conjunction is not supported")
+            return terms[0][0], terms[0][1], False
         bits = self.coperand(env)
-        if not neg and self.peek().text in ("==", "!="):
+        op = None
+        if self.peek().text in ("==", "!="):
             op = self.next().text
-            v = self.int_expr(env)
-            if op == "!=":
-                neg = True
+            v = self.cond_value(env)
+        elif len(bits) == 1:
+            v = 1
         else:
-            v = 1 if len(bits) == 1 else None
-            if v is None:
-                raise self.err("a register condition needs '== value'")
-        self.expect(")")
+            raise self.err("a register condition needs '== value'")
         if v < 0 or v >= (1 << len(bits)):
             raise self.err(f"value {v} does not fit {len(bits)} bits")
         mask = sum(1 << b for b in bits)
         value = sum(((v >> k) & 1) << b for k, b in enumerate(bits))
+        if op == "!=":
+            if len(bits) == 1:
+                return mask, mask ^ value, False
+            return mask, value, True
+        return mask, value, False
+
+    def cond_conj(self, env) -> Tuple[Tuple[int, int, bool], bool]:
+        """((mask, value, possible), negated) of literals joined by &&."""
+        mask = value = 0
+        possible, negated, n = True, False, 0
+        while True:
+            m, v, ng = self.cond_literal(env)
+            n += 1
+            negated = negated or ng
+            if (value ^ v) & mask & m:  # the same bit required 0 and 1
+                possible = False
+            mask, value = mask | m, value | v
+            if not self.accept("&&"):
+                break
+        if negated and n > 1:
+            raise self.err("a register '!=' inside a conjunction is not supported")
+        return (mask, value, possible), negated
+
+    def cond_disj(self, env) -> Tuple[List[Tuple[int, int, bool]], bool]:
+        terms, negs = [], []
+        while True:
+            t, ng = self.cond_conj(env)
+            terms.append(t)
+            negs.append(ng)
+            if not self.accept("||"):
+                break
+        if any(negs) and len(terms) > 1:
+            raise self.err("a register '!=' inside a disjunction is not supported")
+        return terms, negs[0]
+
+    def if_stmt(self, env, qmap, out) -> None:
+        self.next()
+        self.expect("(")
+        if self.peek().text == "!" and self.peek(1).text == "(":
+            self.next()
+            self.next()
+            terms, neg = self.cond_disj(env)
+            self.expect(")")
+            neg = not neg
+        else:
+            terms, neg = self.cond_disj(env)
+        self.expect(")")
         then_ops: List[Callable] = []
         else_ops: List[Callable] = []
         self.block(env, qmap, then_ops)
@@ -609,10 +674,15 @@ class _Lowerer:
             self.block(env, qmap, else_ops)
         if neg:
             then_ops, else_ops = else_ops, then_ops
+        terms = [(m, v) for m, v, ok in terms if ok] or [(0, 1)]  # (0, 1): never true
 
-        def emit(c, then_ops=then_ops, else_ops=else_ops):
-            c.cond(mask, value, lambda: [f(c) for f in then_ops],
-                   (lambda: [f(c) for f in else_ops]) if else_ops else None)
+        def emit(c, then_ops=then_ops, else_ops=else_ops, terms=terms):
+            def level(i):
+                mask, value = terms[i]
+                rest = (lambda: level(i + 1)) if i + 1 < len(terms) else (
+                    (lambda: [f(c) for f in else_ops]) if else_ops else None)
+                c.cond(mask, value, lambda: [f(c) for f in then_ops], rest)
+            level(0)
         out.append(emit)
 
     def for_stmt(self, env, qmap, out) -> None:

@@ -76,7 +76,7 @@ def test_measure_reset_if_else():
     c.measure(1, 1)
     c.cond(1, 1, lambda: c.x(0), lambda: c.z(1))
     c.cond(3, 2, lambda: c.x(1))
-    c.cond(2, 2, lambda: None, lambda: c.reset(1))
+    c.cond(2, 0, lambda: c.reset(1))  # !c[1]: the bit tested for 0
     same_ops(p.ops, c.ops)
     assert p.cregs == {"c": (0, 2)} and p.n_bits == 2
 
@@ -287,6 +287,33 @@ def test_measure_forms_slices_and_delay(orc):
     assert [int(o["q"][0]) for o in p.ops] == [3, 1]
     with pytest.raises(qasm.QasmError):
         qasm.lower("OPENQASM 3; qubit[2] q; x q[0:5];")
+
+
+@pytest.mark.parametrize("cond,f", [
+    ("c[0] && !c[1]", lambda a, b: a and not b),
+    ("c[0] == 1 && c[1] == true", lambda a, b: a and b),
+    ("c[0] || c[1]", lambda a, b: a or b),
+    ("!(c[0] || c[1])", lambda a, b: not (a or b)),
+    ("!(c[0] && c[1])", lambda a, b: not (a and b)),
+    ("c == 2", lambda a, b: (not a) and b),
+    ("c != 3", lambda a, b: not (a and b)),
+    ("(c[0]) && (c[1] == 0) || c == 2", lambda a, b: (a and not b) or ((not a) and b)),
+    ("c[0] && !c[0]", lambda a, b: False),
+    ("c[1] != 1", lambda a, b: not b),
+])
+def test_compound_conditions(orc, cond, f):
+    """Two bits drawn uniformly decide an X on a third qubit through the condition:
+    its readout equals the formula on every shot, for every one of the four records."""
+    src = ("OPENQASM 3; qubit[3] q; bit[2] c; bit r; h q[0]; h q[1]; c = measure q[0:1]; "
+           f"if ({cond}) {{ x q[2]; }} else {{ }} r = measure q[2];")
+    prog = qasm.lower(src)
+    regs, _, _ = orc.run_shots(prog.ops, 3, 64, seed=5)
+    seen = set()
+    for v in regs.tolist():
+        a, b, r = v & 1, (v >> 1) & 1, (v >> 2) & 1
+        seen.add((a, b))
+        assert r == int(bool(f(a, b))), (cond, a, b, r)
+    assert len(seen) == 4
 
 
 def test_extra_forms_lower_to_records():
