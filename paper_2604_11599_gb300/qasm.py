@@ -21,6 +21,10 @@ which every engine of the library runs:
   gates (a user gate's body is inverted record by record in reverse order, or
   controlled record by record);
 * operands ``q``, ``q[i]`` and inclusive slices ``q[a:b]`` / ``q[a:s:b]``;
+* ``def`` subroutines with qubit, bit (consecutive bits) and float / angle
+  arguments, inlined at each call, returning nothing or one bit through
+  ``return measure q;`` at the top of the body (``c[i] = f(...);``; a
+  discarded result goes to bit 63); no classical declarations inside;
 * ``c[i] = measure q[j];``, ``measure q[j] -> c[i];``, ``c = measure q;``,
   ``bit[n] c = measure q;``, ``measure q;`` (result into bit 63, which the
   program must leave undeclared), ``reset q;``, ``barrier ...;`` and
@@ -130,6 +134,15 @@ _CONSTS = {"pi": math.pi, "π": math.pi, "tau": 2 * math.pi, "τ": 2 * math.pi, 
 class GateDef:
     params: List[str]
     qargs: List[str]
+    body: List[Tok]
+
+
+@dataclass
+class SubDef:
+    """A ``def`` subroutine: (kind, name, size) arguments -- kind 'qubit', 'bit'
+    or 'float' (size 0: a single qubit or bit) -- and whether it returns a bit."""
+    args: List[Tuple[str, str, int]]
+    returns_bit: bool
     body: List[Tok]
 
 
@@ -251,6 +264,10 @@ class _Lowerer:
         self.params: Dict[str, int] = {}
         self.consts: Dict[str, float] = {}
         self.gates: Dict[str, GateDef] = {}
+        self.subs: Dict[str, SubDef] = {}
+        self.ret_bit: Optional[int] = None  # inside a subroutine returning a bit: where `return measure` writes
+        self.in_sub = False
+        self.depth = 0  # block nesting (return is allowed at the top of a subroutine body only)
         self.nq = 0
         self.nb = 0
         self.ops: List[Callable[[Circuit], None]] = []  # emitted after the qubit count is known
@@ -415,6 +432,7 @@ class _Lowerer:
             self.statement({}, None, self.ops)
 
     def block(self, env, qmap, out) -> None:
+        self.depth += 1
         if self.accept("{"):
             while not self.accept("}"):
                 if self.peek().kind == "eof":
@@ -422,6 +440,7 @@ class _Lowerer:
                 self.statement(env, qmap, out)
         else:
             self.statement(env, qmap, out)
+        self.depth -= 1
 
     def statement(self, env, qmap, out) -> None:
         tok = self.peek()
@@ -442,6 +461,10 @@ class _Lowerer:
             self.declare_const()
         elif t == "gate":
             self.define_gate()
+        elif t == "def":
+            self.define_sub()
+        elif t == "return":
+            return self.return_stmt(env, qmap, out, tok)
         elif t in ("barrier", "delay"):  # no effect on the state (timing only)
             while self.next().text != ";":
                 pass
@@ -471,10 +494,17 @@ class _Lowerer:
         elif tok.kind == "id" and t in self.cregs and self.peek(1).text in ("=", "["):
             bs = self.coperand(env)
             self.expect("=")
+            if self.peek().kind == "id" and self.peek().text in self.subs:
+                if len(bs) != 1:
+                    raise self.err("a subroutine returns one bit", tok)
+                self.call_sub(env, qmap, out, bs[0])
+                return
             self.expect("measure")
             qs = self.qoperand(env, qmap)
             self.expect(";")
             self.emit_measure(qs, bs, out, tok)
+        elif tok.kind == "id" and t in self.subs:
+            self.call_sub(env, qmap, out, None)
         elif tok.kind == "id":
             self.gate_call(env, qmap, out)
         else:
@@ -500,6 +530,8 @@ class _Lowerer:
         self.nq += size
 
     def declare_bits(self, env=None, qmap=None, out=None) -> None:
+        if self.in_sub:
+            raise self.err("classical declarations inside a subroutine are not supported")
         kw = self.next().text
         tok = self.peek()
         if kw == "bit":
@@ -578,6 +610,104 @@ class _Lowerer:
                 break
             body.append(tok)
         self.gates[name] = GateDef(params, qargs, body)
+
+    def define_sub(self) -> None:
+        tok = self.next()
+        name = self.ident()
+        if name in self.subs or name in self.gates:
+            raise self.err(f"{name!r} is defined twice", tok)
+        args: List[Tuple[str, str, int]] = []
+        self.expect("(")
+        if not self.accept(")"):
+            while True:
+                kind = self.ident()
+                size = 0
+                if self.accept("["):
+                    size = self.int_expr({})
+                    self.expect("]")
+                if kind in ("float", "angle"):
+                    kind, size = "float", 0
+                elif kind not in ("qubit", "bit"):
+                    raise self.err(f"subroutine arguments are qubit, bit, float or angle, not {kind!r}")
+                args.append((kind, self.ident(), size))
+                if self.accept(")"):
+                    break
+                self.expect(",")
+        returns_bit = False
+        if self.accept("->"):
+            if self.ident() != "bit":
+                raise self.err("a subroutine returns a bit or nothing")
+            returns_bit = True
+        self.expect("{")
+        depth, body = 1, []
+        while True:
+            t = self.next()
+            if t.kind == "eof":
+                raise self.err("unterminated subroutine body")
+            depth += t.text == "{"
+            depth -= t.text == "}"
+            if depth == 0:
+                break
+            body.append(t)
+        self.subs[name] = SubDef(args, returns_bit, body)
+
+    def call_sub(self, env, qmap, out, dest: Optional[int]) -> None:
+        """Inlines a subroutine call: its body lowered with the arguments bound."""
+        tok = self.peek()
+        name = self.ident()
+        sd = self.subs[name]
+        if dest is not None and not sd.returns_bit:
+            raise self.err(f"{name!r} returns nothing", tok)
+        sub_env: Dict[str, Lin] = {}
+        sub_q: Dict[str, List[int]] = {}
+        sub_c: Dict[str, Tuple[int, int]] = {}
+        self.expect("(")
+        for k, (kind, arg, size) in enumerate(sd.args):
+            if k:
+                self.expect(",")
+            if kind == "float":
+                sub_env[arg] = self.expr(env)
+            elif kind == "qubit":
+                qs = self.qoperand(env, qmap)
+                if len(qs) != max(size, 1):
+                    raise self.err(f"argument {arg!r} of {name!r} takes {max(size, 1)} qubits", tok)
+                sub_q[arg] = qs
+            else:
+                bs = self.coperand(env)
+                if len(bs) != max(size, 1) or bs != list(range(bs[0], bs[0] + len(bs))):
+                    raise self.err(f"argument {arg!r} of {name!r} takes {max(size, 1)} consecutive bits", tok)
+                sub_c[arg] = (bs[0], len(bs))
+        self.expect(")")
+        self.expect(";")
+        if self.depth > 64:
+            raise self.err("subroutine calls nested too deeply (recursion?)", tok)
+        sub = _Lowerer(sd.body + [Tok("eof", "", tok.line)])
+        sub.qregs, sub.cregs = {}, sub_c
+        sub.params, sub.consts, sub.gates, sub.subs = self.params, self.consts, self.gates, self.subs
+        sub.nq, sub.nb = self.nq, self.nb
+        sub.in_sub = True
+        sub.depth = self.depth + 1
+        sub.ret_bit = (dest if dest is not None else HIDDEN_BIT) if sd.returns_bit else None
+        if sub.ret_bit == HIDDEN_BIT and self.nb >= 64:
+            raise self.err("a discarded return value needs bit 63 free", tok)
+        sub.depth0 = sub.depth
+        while sub.peek().kind != "eof":
+            if sub.statement(dict(env, **sub_env), sub_q, out) == "return":
+                break
+
+    def return_stmt(self, env, qmap, out, tok):
+        self.next()
+        if self.ret_bit is None:
+            raise self.err("return outside a subroutine that returns a bit", tok)
+        if self.depth != getattr(self, "depth0", -1):
+            raise self.err("return is allowed only at the top of a subroutine body", tok)
+        self.expect("measure")
+        qs = self.qoperand(env, qmap)
+        self.expect(";")
+        if len(qs) != 1:
+            raise self.err("return measure takes one qubit", tok)
+        self.emit_measure(qs, [self.ret_bit], out, tok)
+        return "return"
 
     def emit_measure(self, qs, bs, out, tok) -> None:
         if len(qs) != len(bs):

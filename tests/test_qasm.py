@@ -316,6 +316,51 @@ def test_compound_conditions(orc, cond, f):
     assert len(seen) == 4
 
 
+def test_subroutines_inline_to_the_written_out_program(orc):
+    """def subroutines (qubit, bit, float arguments; a returned measurement) lower
+    to exactly the records of the same program written out by hand."""
+    with_defs = qasm.lower("""OPENQASM 3; qubit[4] q; bit[3] c; input float t;
+        def parity(qubit a, qubit b, qubit anc) -> bit { reset anc; cx a, anc; cx b, anc; return measure anc; }
+        def flipif(qubit tq, bit s) { if (s) { x tq; } }
+        def rot(qubit tq, float th) { rx(th) tq; rz(th / 2) tq; }
+        def layer(qubit[2] r, float th) { for int i in [0:1] { rot(r[i], th); } cx r[0], r[1]; }
+        h q[0]; h q[1];
+        c[0] = parity(q[0], q[1], q[3]);
+        flipif(q[2], c[0]);
+        layer(q[1:2], t);
+        c[1] = measure q[2];
+        parity(q[1], q[2], q[3]);
+        c[2] = parity(q[0], q[2], q[3]);
+    """)
+    written = qasm.lower("""OPENQASM 3; qubit[4] q; bit[3] c; input float t;
+        h q[0]; h q[1];
+        reset q[3]; cx q[0], q[3]; cx q[1], q[3]; c[0] = measure q[3];
+        if (c[0]) { x q[2]; }
+        rx(t) q[1]; rz(t / 2) q[1]; rx(t) q[2]; rz(t / 2) q[2]; cx q[1], q[2];
+        c[1] = measure q[2];
+        reset q[3]; cx q[1], q[3]; cx q[2], q[3]; measure q[3];
+        reset q[3]; cx q[0], q[3]; cx q[2], q[3]; c[2] = measure q[3];
+    """)
+    same_ops(with_defs.ops, written.ops)
+    r = orc.run(with_defs.ops, 4, params=[0.3], seed=1)
+    assert r.status == 0
+
+
+@pytest.mark.parametrize("src,msg", [
+    ("def f(qubit a) -> bit { return measure a; } qubit[2] q; f(q);", "takes 1 qubits"),
+    ("def f(qubit a) { return measure a; } qubit q; f(q);", "return outside"),
+    ("def f(qubit a, bit s) -> bit { if (s) { return measure a; } } qubit q; bit[2] c; c[0] = f(q, c[1]);",
+     "top of a subroutine"),
+    ("def f(qubit a) { bit b; } qubit q; f(q);", "classical declarations"),
+    ("def f(qubit a) { f(a); } qubit q; f(q);", "nested too deeply"),
+    ("def f(qubit a) { x a; } qubit q; bit c; c = f(q);", "returns nothing"),
+    ("def f(bit[2] b) { } qubit q; bit[4] c; f(c[0:2:2]);", "consecutive bits"),
+])
+def test_subroutine_errors(src, msg):
+    with pytest.raises(qasm.QasmError, match=msg):
+        qasm.lower("OPENQASM 3; " + src)
+
+
 def test_extra_forms_lower_to_records():
     p = qasm.lower("OPENQASM 3; qubit[3] q; negctrl(2) @ x q[0], q[1], q[2];")
     kinds = [int(k) for k in p.ops["kind"]]
