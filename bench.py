@@ -331,6 +331,27 @@ def measure_forms(sv, torch):
         out["clifford"] = clifford_form(sv, W, np)
     except Exception as e:
         out["clifford"] = {"error": repr(e)}
+    # noise by trajectories: the n=5 program with depolarising, readout and reset channels (ancilla lowering)
+    try:
+        from paper_2604_11599_gb300 import noise
+
+        nz = noise.with_noise(W.plain_small(), noise.NoiseModel(p1=1e-3, p2=1e-2, p_meas=1e-2, p_reset=1e-2))
+        with sv.Batch("c128") as b:
+            p = b.add_program(nz.ops, nz.n)
+            b.run([p] * 64, np.zeros(64), np.arange(64))
+            t0 = time.perf_counter()
+            b.run([p] * 1000, np.zeros(1000), np.arange(1000))
+            t_ps = time.perf_counter() - t0
+            b.sample_branched([p], [0], [1000])
+            t0 = time.perf_counter()
+            _, nst = b.sample_branched([p], [0], [10_000])
+            t_br = time.perf_counter() - t0
+        out["noise"] = {"workload": "the n=5 plain-path program with depolarising (1e-3 / 1e-2), readout (1e-2) and "
+                                    "reset (1e-2) channels lowered through one ancilla, complex128",
+                        "records": int(len(nz.ops)), "batched_per_shot_shots_per_s": 1000 / t_ps,
+                        "batched_branched_shots_per_s": 1e4 / t_br, "branched_paths": nst["paths"]}
+    except Exception as e:
+        out["noise"] = {"error": repr(e)}
     # VQE: n=20 hardware-efficient ansatz, 320 parameters, 200 Pauli terms
     c = W.hea(20, 8)
     terms = W.heisenberg_fields(9, 20, 200)
