@@ -42,7 +42,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "amplitude-gate updates/s"
 UNIT = "updates/s"
-GEN_SEED = {(28, "c128"): 2, (28, "c64"): 3, (30, "c128"): 4, (30, "c64"): 5}
 
 
 def parse():
@@ -79,7 +78,7 @@ def circuit(n, dtype, kind="layered"):
 
     if kind == "dense4":
         return workloads.dense_layers(12, n, layers=6)
-    return workloads.layered(GEN_SEED.get((n, dtype), 5), n, layers=20)
+    return workloads.layered(workloads.LAYERED_SEEDS.get((n, dtype), 5), n, layers=20)
 
 
 # FP64 operations the sweep kernels execute per amplitude for each IR gate (complex128):
@@ -102,6 +101,28 @@ def fp64_ops_per_step(ops, n_passes, n):
         g = Gate(int(r["gate"]))
         total += per.get(g, 7 if g >= Gate.CX else 14)
     return float(total + 6 * n_passes) * float(1 << n)
+
+
+def near_threshold(st, prog, steps, stream_id, dtype):
+    """The timed steps' draws again (untimed): how many fell within 1e-9 of the
+    outcome threshold, and within the dtype's parity band, by the margins the
+    GPU itself computed, |u - p0/(p0+p1)|."""
+    import numpy as np
+
+    band = 1e-5 if dtype == "c64" else 1e-9
+    tot = n9 = nb = 0
+    mn = float("inf")
+    for i in range(steps):
+        st.launch(prog, seed=0, stream_id=stream_id, shot=i)
+        tr = st.trace()
+        if len(tr):
+            m = np.abs(tr["u"] - tr["p0"] / (tr["p0"] + tr["p1"]))
+            tot += len(m)
+            n9 += int((m < 1e-9).sum())
+            nb += int((m < band).sum())
+            mn = min(mn, float(m.min()))
+    return {"draws": tot, "within_1e-9": n9, f"within_{band:g}": nb, "min_margin": mn,
+            "margins": "GPU-side |u - p0/(p0+p1)| of the timed steps' draws"}
 
 
 def measured_peaks():
@@ -275,6 +296,12 @@ def measure_forms(sv, torch):
             st.run(c.ops, seed=0, shot=shot)
             lat.append(time.perf_counter() - t1)
         lat.sort()
+        m_all = []  # near-threshold draws of the 1,000 shots (GPU-side margins, untimed)
+        for shot in range(1000):
+            st.run(c.ops, seed=0, shot=shot)
+            tr = st.trace()
+            m_all.extend(np.abs(tr["u"] - tr["p0"] / (tr["p0"] + tr["p1"])).tolist())
+        m_all = np.asarray(m_all)
         st.sample_branched(c.ops, 50)
         t0 = time.perf_counter()
         _, pst = st.sample_branched(c.ops, 1000)
@@ -299,7 +326,10 @@ def measure_forms(sv, torch):
                                      "branched_batched_shots_per_s": 1000 / tbb,
                                      "branched_paths": pst["paths"], "branched_levels": bst["levels"],
                                      "branched_batched_100k_shots_per_s": 100_000 / tbb5,
-                                     "branched_100k_paths": bst5["paths"]}
+                                     "branched_100k_paths": bst5["paths"],
+                                     "near_threshold_draws": {"draws": int(m_all.size),
+                                                              "within_1e-9": int((m_all < 1e-9).sum()),
+                                                              "min_margin": float(m_all.min())}}
     # autotuned batched launch: gates per pass timed on 2,048 trajectories of the same mix, then the
     # 65,536-trajectory launch again with the chosen setting (cache in a scratch file)
     try:
@@ -513,7 +543,6 @@ def main():
     st.launch(prog, seed=0, shot=999)  # first launch compiles the specialised kernels (once per program)
     torch.cuda.synchronize()
     stats = prog.stats
-    upd = float(stats["gates"] + stats["draws"]) * float(1 << n)
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
@@ -538,7 +567,11 @@ def main():
     st.profile(False)
     clk = clocks.stop()
     ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    # updates of the work that ran: gate records executed (not-taken if/else arms
+    # excluded) and draws executed, counted by the pass kernels on the device
+    upd = float(prof["gates"] + prof["draws"]) * float(1 << n) / args.steps
     value = replicas.whole_job_rate(upd, ms / 1000.0, world)
+    near = near_threshold(st, prog, args.steps, stream_id, dtype) if rank == 0 else None
 
     # end to end through the public API with host buffers, plan lowered + copied each step
     e2e = None
@@ -563,7 +596,12 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "kernel": "sv_jit_passes (k_pass specialised)" if stats["specialised"] else "k_pass",
                 "peak_kind": f"of {kind}", "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
-                "avg_launch_ms": prof["ms"] / max(1, prof["launches"])}
+                "avg_launch_ms": prof["ms"] / max(1, prof["launches"]),
+                "bytes_counted": "state bytes the pass kernels read and wrote, counted on the device "
+                                 "(tiles copied in, tiles stored); passes that moved nothing add nothing",
+                "bytes_read_per_step": prof["bytes_read"] / args.steps,
+                "bytes_written_per_step": prof["bytes_written"] / args.steps,
+                "passes_moving_data_per_step": prof["passes"] / args.steps}
     if dtype == "c128":  # FP64-bound: the arithmetic the kernels execute against the FP64 rate
         flops = fp64_ops_per_step(c.ops, stats["passes"], n)
         tf = flops / (prof["ms"] / 1000.0) / 1e12 if prof["ms"] > 0 else 0.0
@@ -589,12 +627,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if dtype == "c64" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(n, dtype, args.circuit), "n": n, "state": dtype,
-                       "gates_per_step": stats["gates"], "draws_per_step": stats["draws"],
+                       "gates_per_step": prof["gates"] / args.steps, "draws_per_step": prof["draws"] / args.steps,
+                       "gate_records_in_program": stats["gates"],
                        "passes_per_step": stats["passes"], "tile_bits": stats["tile_bits"],
                        "low_bits": stats["low_bits"], "l2": "inputs larger than L2 (state 2^n amplitudes)",
                        "specialised_kernels": bool(stats["specialised"]),
                        "compile_seconds": round(stats["compile_seconds"], 2),
                        "parallelism": f"replicas x{world}"},
+            "near_threshold_draws": near,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * stats["kernels_per_run"], "clocks": clk, "forms": forms,
         }

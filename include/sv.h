@@ -143,7 +143,9 @@ typedef struct sv_branch_stats {
 #ifndef __CUDACC_RTC__ /* device code compiled at run time needs the types above only */
 
 /*
- * Create a state of n qubits (1 <= n <= 34) in |0...0>.
+ * Create a state of n qubits (1 <= n <= 34) in |0...0>: the amplitude vector
+ * that state-vector simulation of a circuit evolves (Sec. II-C, CUDA-Q's
+ * state-vector backends; Sec. IV-A.2, state vectors compared for validation).
  *   dev_buf  NULL: the library allocates 2^n amplitudes on the current device.
  *            Otherwise caller-owned device memory of `bytes` >= 2^max(n,10) *
  *            amplitude size, which must outlive the handle (e.g. a torch tensor).
@@ -152,10 +154,13 @@ typedef struct sv_branch_stats {
  */
 sv_status sv_create(int n, sv_dtype dtype, void* dev_buf, size_t bytes, sv_state** out);
 
-/* Release the handle and everything the library allocated for it (not dev_buf). */
+/* Release the handle and everything the library allocated for it (not dev_buf).
+ * Resource management of this library; the paper has no counterpart. */
 sv_status sv_destroy(sv_state* h);
 
-/* Enqueue all later work of h on this cudaStream_t (NULL: legacy default stream). */
+/* Enqueue all later work of h on this cudaStream_t (NULL: legacy default stream).
+ * Resource management of this library; the paper has no counterpart.
+ * SV_ERR_ARG for a null handle. */
 sv_status sv_bind_stream(sv_state* h, void* cuda_stream);
 
 /* Copy a host complex128 pool (interleaved re, im; n_complex entries) used by DENSE ops. */
@@ -182,14 +187,27 @@ sv_status sv_program_info(const sv_program* p, sv_program_stats* out);
 /*
  * Run one trajectory of a prepared program from |0...0> on the bound stream,
  * with parameters already on the device (dev_params: n_params doubles, may be
- * NULL if the program has no parameter references).  Asynchronous.
+ * NULL if the program has no parameter references).  Asynchronous.  A
+ * trajectory applies the gates, measures mid-circuit (the state collapses onto
+ * the outcome, Sec. II-C, Fig. 2), resets, and decides each `if` from the
+ * measured bits when it is reached, with no branch simulated ahead of time
+ * (Sec. III-C); loops repeat a fixed number of times (Abstract); angles may
+ * reference run-time `input` parameters, so one lowered program serves every
+ * parameter set (Sec. III-D).  SV_ERR_ARG for a null handle or program, a
+ * program prepared for another state, or fewer parameters than the program
+ * references; SV_ERR_CUDA if a launch fails.
  */
 sv_status sv_launch(sv_state* h, sv_program* p, const double* dev_params, size_t n_params,
                     uint64_t seed, uint64_t stream_id, uint64_t shot);
 
 /*
  * Prepare (cached by content) + copy params to the device + launch, then if
- * creg_out is non-NULL wait and write the classical register there.
+ * creg_out is non-NULL wait and write the classical register there.  One
+ * trajectory of the dynamic circuit as in sv_launch (Sec. II-C Fig. 2,
+ * Sec. III-C, Sec. III-D).  ops and params (host memory) are read during the
+ * call only.  Errors: those of sv_prepare and sv_launch; with creg_out,
+ * SV_ERR_NUMERIC if a measurement met a zero-norm state and SV_ERR_TIMEOUT if
+ * a bounded device wait ran out.
  */
 sv_status sv_run(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
                  uint64_t seed, uint64_t stream_id, uint64_t shot, uint64_t* creg_out);
@@ -199,7 +217,8 @@ sv_status sv_get_creg(sv_state* h, uint64_t* creg);
 sv_status sv_get_trace(sv_state* h, sv_draw* out, size_t max, size_t* n_out);
 
 /*
- * `shots` shots of a program.  With MEASURE/RESET in the program, shot s runs
+ * `shots` shots of a program (repeated shots of a dynamic circuit, Sec. IV-C:
+ * the conditional reset checked over 10^4 shots).  With MEASURE/RESET in the program, shot s runs
  * its own trajectory (counter shot = s) and creg_out[s] receives its
  * register; otherwise the program runs once.  bits_out (nullable) receives
  * one terminal sample per shot (counter (s, 2^32)).  Waits for the outputs.
@@ -227,13 +246,20 @@ sv_status sv_sample_branched(sv_state* h, const sv_op* ops, size_t n_ops, const 
                              uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out,
                              sv_branch_stats* stats);
 
-/* Terminal samples of the current state: out[s] for counter (shot0 + s, 2^32). */
+/* Terminal samples of the current state: out[s] for counter (shot0 + s, 2^32)
+ * (measurement of every qubit at the end of a shot, Sec. IV-C).  out is a host
+ * array of `shots` indices; waits for it.  SV_ERR_ARG for a null handle or
+ * output. */
 sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
                           uint64_t* out);
 
 /*
- * <psi| sum_t coeff_t P_t |psi> of the current state (FP64 accumulation).
- * total (nullable) receives the sum, per_term (nullable, n_terms) each <P_t>.
+ * <psi| sum_t coeff_t P_t |psi> of the current state (FP64 accumulation): the
+ * energy <H> of a Hamiltonian given as a Pauli sum, as in the VQE experiments
+ * (Sec. II-D; Sec. IV-A.2, H = Z0 Z1; Sec. IV-D).  terms is a host array read
+ * during the call; total (nullable) receives the sum, per_term (nullable,
+ * n_terms host doubles) each <P_t>.  Waits for the result.  SV_ERR_ARG for a
+ * null handle or terms, or a term on a qubit >= n.
  */
 sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* total, double* per_term);
 
@@ -257,10 +283,14 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
  * Asynchronous: it returns once the work is enqueued.  The first call on a
  * device looks up the static array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * The address is kept for the life of the process: do not call it again on a
+ * device that was reset with cudaDeviceReset.  dev_state and dev_out must be
+ * device (or managed) memory of the current device.
  * Every call shares the one array, so calls that overlap on the GPU (e.g.
  * on different streams) race and give wrong results; calls in stream order
- * are safe.  Errors: SV_ERR_ARG for bad n, dtype, pointers, alignment or
- * term count; SV_ERR_CUDA if a launch fails (message in sv_last_error()).
+ * are safe.  Errors: SV_ERR_ARG for bad n, dtype, pointers (null, not device
+ * memory, or on another device), alignment or term count; SV_ERR_CUDA if a
+ * launch fails (message in sv_last_error()).
  */
 sv_status sv_expval_static(const void* dev_state, int n, sv_dtype dtype, const sv_pauli* terms, size_t n_terms,
                            double* dev_out, void* cuda_stream);
@@ -379,7 +409,11 @@ sv_status sv_expval_grad_batch(int n, sv_dtype dtype, const sv_op* ops, size_t n
                                size_t n_sets, size_t n_params, const sv_pauli* terms, size_t n_terms, double* val_out,
                                double* grad_out, void* cuda_stream);
 
-/* Copy amplitudes [first, first+count) to / from host memory (amplitude-size elements). */
+/* Copy amplitudes [first, first+count) to / from host memory (amplitude-size
+ * elements: 8 bytes for SV_C64, 16 for SV_C128), waiting for the copy: the
+ * state vector itself, which the paper's validation compares between
+ * simulators (Sec. III-E, Sec. IV-A.2).  The host buffer is the caller's.
+ * SV_ERR_ARG for a null handle or pointer or a range beyond 2^n. */
 sv_status sv_get_amplitudes(sv_state* h, void* host_dst, size_t first, size_t count);
 sv_status sv_set_amplitudes(sv_state* h, const void* host_src, size_t first, size_t count);
 
@@ -390,14 +424,44 @@ sv_status sv_state_buffer(sv_state* h, void** dev_ptr, size_t* bytes);
 sv_status sv_set_tuning(sv_state* h, int tile_bits, int low_bits, int max_pass_gates);
 
 /*
- * Kernel timing of the state-sweep passes.  While enabled, every pass launch
- * is bracketed by CUDA events on the bound stream.  sv_profile_read waits,
- * then reports the summed event time (ms), the number of pass launches and
- * their algorithmic bytes (state read + written once per storing pass, read
- * once per read-only pass), and resets the counters.
+ * Kernel timing and work counts of the state-sweep passes.  While enabled,
+ * every pass launch is bracketed by CUDA events on the bound stream, and the
+ * pass kernels themselves count on the device what they did: bytes of the
+ * state read (tiles copied in; tiles that a pending projector zeroes, and the
+ * first pass that generates |0...0>, read nothing), bytes written (tiles
+ * stored; a pass whose gates were all predicated off, or a final flush with
+ * no projector pending, writes nothing), gate records executed (gates of
+ * not-taken if/else arms excluded), draws executed and passes that touched
+ * the state.  sv_profile_read waits, then reports the summed event time (ms),
+ * the number of pass launches and the bytes read + written, and resets the
+ * timing and the counters.  sv_profile_work reads the counters without
+ * resetting them.  Enabling zeroes the counters.  Errors: SV_ERR_ARG for a
+ * null handle or output, SV_ERR_CUDA if a copy fails.
  */
+#define SV_WORK_COUNTERS 8
+typedef struct sv_work_counts {
+  uint64_t bytes_read, bytes_written; /* state bytes moved by the pass kernels     */
+  uint64_t gates;                     /* gate records executed                       */
+  uint64_t draws;                     /* measure / reset draws executed              */
+  uint64_t passes;                    /* pass launches that read or wrote the state  */
+} sv_work_counts;
 sv_status sv_profile(sv_state* h, int enable);
 sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, double* bytes);
+sv_status sv_profile_work(sv_state* h, sv_work_counts* out);
+
+/*
+ * Self test of the failure path of bounded device waits (the tensor-core
+ * completion wait of the sweep kernels).  Runs that same wait -- mbarrier
+ * try_wait polled at most `polls` times -- in a one-warp kernel on the bound
+ * stream, on an mbarrier that nothing ever arrives at, so it always runs out.
+ * The kernel issues no MMA and allocates no tensor memory; the outcome reaches
+ * the caller exactly as a timed-out pass reports it: the control block's
+ * status, read back by the host.  Returns SV_ERR_TIMEOUT (the expected
+ * outcome; the handle stays usable and the next run starts clean),
+ * SV_ERR_ARG for a null handle or polls > 2^24, SV_ERR_CUDA on a launch error.
+ * The paper has no counterpart: it describes no device waits.
+ */
+sv_status sv_selftest_wait(sv_state* h, uint32_t polls);
 
 /*
  * Program cache of sv_run / sv_sample (on by default): a repeated op list
@@ -440,7 +504,8 @@ sv_status sv_set_dense_tc(sv_state* h, int enable);
 sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
                        size_t n_complex, char* log, size_t log_len);
 
-/* Wait for all work of h. */
+/* Wait for all work of h.  Resource management of this library; the paper
+ * has no counterpart.  SV_ERR_CUDA if earlier asynchronous work failed. */
 sv_status sv_sync(sv_state* h);
 
 /* Thread-local message of the last error on this thread ("" if none). */

@@ -157,7 +157,18 @@ struct TcCtx {
   uint32_t tmem;   // tensor-memory base address
   uint32_t phase;  // completed MMA batches (parity of the next wait)
   bool on;         // dense gates of this pass go to the tensor cores
-  bool ok;         // false after a wait ran out
+  bool ok;         // false (for the whole warp) after a wait ran out: the warp neither
+                   // writes nor reads tensor memory again, and thread 0 issues no MMA
+  bool drain;      // thread 0: a batch it committed was not seen to complete
 };
+
+// Give-up path of a completion wait that ran out (SV_ERR_TIMEOUT): before the
+// CTA frees its tensor memory, the issuing thread waits once more, again
+// bounded, for the last batch it committed, so that no MMA it issued can
+// still write columns the CTA no longer owns when that batch does finish in
+// time.  Called by every thread of the CTA; uniform barriers.
+__device__ __forceinline__ void tc_drain(TcCtx& tc) {
+  if (threadIdx.x == 0 && tc.drain) mbar_wait(&tc.s->bar, (tc.phase - 1u) & 1u, TC_WAIT_POLLS);
+}
 
 }  // namespace svk

@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(256) k_expval_static(const StaticTerms a, unsi
 
 thread_local std::string t_err;
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (the first
+// call with that device current).  cudaDeviceReset unloads the library's
+// device image; a process that resets a device must not call
+// sv_expval_static on it again, since the cached address would be stale.
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
@@ -192,6 +195,21 @@ static sv_status expval_static_impl(const void* dev_state, int n, sv_dtype dtype
   if (st != SV_OK) return st;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
+  // the state and the output must live on the current device, whose copy of
+  // the scratch array the kernel uses
+  for (const void* p : {dev_state, static_cast<const void*>(dev_out)}) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();
+      t_err = "sv_expval_static: state or output is not a CUDA pointer";
+      return SV_ERR_ARG;
+    }
+    const bool dev_mem = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    if (!dev_mem || (pa.type == cudaMemoryTypeDevice && pa.device != dev)) {
+      t_err = "sv_expval_static: state and output must be device memory of the current device";
+      return SV_ERR_ARG;
+    }
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const uint64_t work = (1ull << n) / 256;

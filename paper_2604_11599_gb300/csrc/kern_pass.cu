@@ -229,6 +229,26 @@ cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The pass kernels' bounded completion wait (mbar_wait, dev_tc.cuh) on an
+// mbarrier that nothing arrives at: phase 0 never completes, so the wait gives
+// up after `polls` polls and the kernel reports what a timed-out pass reports.
+// One warp, no MMA, no tensor memory.
+__global__ void k_wait_probe(uint32_t polls, int32_t* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const bool done = mbar_wait(&bar, 0u, polls);
+  if (__all_sync(0xffffffffu, !done) && threadIdx.x == 0) atomicCAS(status, 0, int32_t(SV_ERR_TIMEOUT));
+}
+
+cudaError_t launch_wait_probe(uint32_t polls, int32_t* status, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(polls, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s) {
   const uint64_t want = (n_amp + 255) / 256;
   const int blocks = int(want < uint64_t(sms) * 8 ? want : uint64_t(sms) * 8);

@@ -25,6 +25,10 @@ struct PassArgs {
   int pass;          // pass index (specialised kernels select their stage program by it)
   int dense_tc;      // 1: dense four-qubit gates of complex64 2^12-amplitude tiles on the tensor cores
   int gen_init;      // 1: this launch is the program's first pass and generates |0...0> instead of loading it
+  // work counters (nullable; grid passes only): [0] bytes of the state read,
+  // [1] bytes of it written, [2] gate records executed (predicated-off ones
+  // excluded), [3] draws executed, [4] passes that touched the state
+  unsigned long long* work;
 };
 
 struct PrepArgs {
@@ -49,6 +53,8 @@ cudaError_t launch_prep(int dtype, const PrepArgs& p, cudaStream_t s);
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t launch_init_state(int dtype, void* state, uint64_t n_amp, int sms, cudaStream_t s);
+// bounded-wait self test: a one-warp kernel whose mbarrier wait always runs out
+cudaError_t launch_wait_probe(uint32_t polls, int32_t* status, cudaStream_t s);
 #endif
 #ifndef __CUDACC_RTC__
 // dense: the pass holds a dense four-qubit gate (its tensor-core variant runs when a.dense_tc)

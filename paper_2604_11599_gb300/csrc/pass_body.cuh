@@ -267,7 +267,7 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
   const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
   const uint32_t half = uint32_t(warp >> 2);
-  {  // this thread's row, 16 columns at a time: high parts (columns 0..31), low parts (32..63)
+  if (tc.ok) {  // this thread's row, 16 columns at a time: high parts (columns 0..31), low parts (32..63)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t w[16];
@@ -281,7 +281,7 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
       tmem_st16(tc.tmem + lane_base + 64u * half + 16u * uint32_t(q), w);
     }
   }
-  tmem_wait_st();
+  if (tc.ok) tmem_wait_st();
   tc_fence_before();
   __syncthreads();  // all rows in tensor memory, previous results read
   if (tid == 0 && tc.ok) {
@@ -301,16 +301,24 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
     }
     mma_commit(&s.bar);
   }
-  // after a wait ran out, no further MMAs or waits (the barriers stay): the
-  // pass ends quickly and the run reports SV_ERR_TIMEOUT
-  if (tc.ok && !mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS)) tc.ok = false;
+  // After a wait ran out the warp stops touching tensor memory (tcgen05.st /
+  // ld are warp-collective, so the decision is made per warp) and thread 0
+  // issues no further MMA; the block barriers stay uniform, the pass ends, the
+  // CTA drains (tc_drain) before it frees tensor memory, and the run reports
+  // SV_ERR_TIMEOUT with the state undefined.
+  const bool issued = tid == 0 && tc.ok;
+  if (tc.ok) tc.ok = mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS);
+  tc.ok = __all_sync(0xffffffffu, tc.ok);
+  if (issued && !tc.ok) tc.drain = true;
   ++tc.phase;
   tc_fence_after();
-  uint32_t r[32];
-  tmem_ld32(tc.tmem + lane_base + 128u + 32u * half, r);
-  tmem_wait_ld();
+  if (tc.ok) {
+    uint32_t r[32];
+    tmem_ld32(tc.tmem + lane_base + 128u + 32u * half, r);
+    tmem_wait_ld();
 #pragma unroll
-  for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+    for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+  }
 }
 
 // A dense four-qubit unitary: on the tensor cores where the pass enabled them
@@ -635,6 +643,7 @@ static __device__ __noinline__ void scalar_phase(const PassArgs& A, const DPass&
     if (mass > 0) nps *= 1.0 / sqrt(mass);
     else W->status = SV_ERR_NUMERIC;
   }
+  if (A.work) A.work[3] += mc - W->m;  // draws executed (one thread of one CTA per pass)
   W->creg = creg;
   W->m = mc;
   W->pm = npm;
@@ -818,6 +827,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     act_any |= int(on);
   }
   const bool any_gate = __syncthreads_or(act_any) != 0;
+  if (!CTA && A.work && blockIdx.x == 0 && tid == 0 && any_gate) {  // gate records this run executes
+    unsigned long long k = 0;
+    for (int g = 0; g < int(sp.ng); ++g) k += (sgk[g] & SGK_ON) ? 1ull : 0ull;
+    atomicAdd(A.work + 2, k);
+  }
   int need = 0;
   if (sp.gk) {
     if (sp.group_always) need = 1;
@@ -837,7 +851,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const bool do_work = do_store || needed;
   const bool need_ticket = sp.nc > 0 || (do_store && !ident);
 
-  TcCtx tc{tc_shared(sh), nullptr, 0u, 0u, false, true};
+  TcCtx tc{tc_shared(sh), nullptr, 0u, 0u, false, true, false};
   if (do_work) {
     if (any_gate)
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];
@@ -956,6 +970,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     const uint64_t umask = upair ? (omask & ~(xo & (~xo + 1))) : omask;  // unit index bits
     const uint64_t pxi = PROJ ? (px & tmask & (sizeof(T) == 4 ? ~1ull : ~0ull)) : 0;  // inner flip, granule-aligned
     int cur = 0;
+    unsigned long long n_rd = 0, n_wr = 0;
     // Unit bases advance by masked addition instead of a bit-by-bit deposit per unit.
     const uint64_t sstep = pdep64(ustep, umask);
     const uint64_t sahead = pdep64(uint64_t(NBUF - 1) * ustep, umask);
@@ -972,6 +987,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
             src = Uk.src;
             go = Uk.act && !gen;
           }
+          n_rd += go ? 1ull : 0ull;
           if (go) {
             V* dst = buffer(k);
 #pragma unroll
@@ -987,6 +1003,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     }
 
     double tacc = 0.0;  // this lane's measurement-table slot over the tiles (all group qubits in the tile)
+    // tiles this CTA read from / wrote to the state (thread 0 counts; grid passes report them)
     for (uint64_t u = ustart; u < nunits; u += ustep) {
       uint64_t tl[2] = {u, 0};
       int cnt = 1;
@@ -1057,6 +1074,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           tb = tile;
           base = pair ? pdep64(tl[k2], omask) : bcur;
           const bool zero_tile = !ident && (((base ^ px) & pm & omask) != (pv & omask));
+          n_rd += (gen || zero_tile) ? 0ull : 1ull;
           // a'[i] = ps * a[i ^ px] if ((i ^ px) & pm) == pv, else 0
 #pragma unroll
           for (int k = 0; k < NVT; ++k) {
@@ -1130,6 +1148,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
                 go = Un.act;
               }
             }
+            n_rd += go ? 1ull : 0ull;
             if (go) {
               V* nb = buffer((cur + NBUF - 1) % NBUF);
 #pragma unroll
@@ -1191,6 +1210,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
 
         // ---- store
         if (do_store) {
+          n_wr += upair ? 2ull : 1ull;
 #pragma unroll
           for (int k = 0; k < NVT && !stored; ++k) {
             const uint32_t ch = c0 + (uint32_t(k) << (VB - L));
@@ -1231,6 +1251,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       bcur = spread_add(bcur, sstep, umask);
     }
     if (pipe) cp_async_wait<0>();
+    if (!CTA && A.work && tid == 0) {
+      atomicAdd(A.work + 0, n_rd * (unsigned long long)TILE_BYTES);
+      atomicAdd(A.work + 1, n_wr * (unsigned long long)TILE_BYTES);
+      if (blockIdx.x == 0) atomicAdd(A.work + 4, 1ull);
+    }
     if (needed && sp.kin == sp.gk) {  // the lanes' table slots, combined over warps in a fixed order
       if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = tacc;
       __syncthreads();
@@ -1250,6 +1275,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     if (!tc.ok)  // a completion wait ran out, or a dense gate reached this variant with the path off
       atomicCAS(&A.ctrl->status, 0, int32_t(tc.on ? SV_ERR_TIMEOUT : SV_ERR_UNSUPPORTED));
     if (tc.on) {
+      tc_drain(tc);
       tc_fence_before();
       __syncthreads();  // every tensor-memory read of this CTA is complete
       if (warp == 0) {

@@ -125,7 +125,7 @@ struct sv_state {
   bool profiling = false;
   std::vector<cudaEvent_t> events;
   size_t ev_used = 0;
-  double prof_bytes = 0;
+  unsigned long long* work = nullptr;  // device work counters of the profiled launches (svk::PassArgs::work)
   bool use_cache = true;
   bool use_jit = false;
   bool dense_tc = true;  // dense four-qubit gates on the tensor cores where the kernel supports it
@@ -212,7 +212,7 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
     a.partials = h->partials.p;
     a.n = h->n_int;
     a.dense_tc = h->dense_tc ? 1 : 0;
-    const double sbytes = double(1ull << h->n_int) * double(h->amp_bytes);
+    a.work = h->profiling ? h->work : nullptr;
     for (size_t i = 0; i < P.passes.size(); ++i) {
       a.gen_init = (P.gen_init && i == 0) ? 1 : 0;
       if (h->profiling) {
@@ -233,8 +233,6 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
       if (h->profiling) {
         SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], s));
         h->ev_used += 2;
-        const svp::DPass& d = P.passes[i];
-        h->prof_bytes += a.gen_init ? sbytes : ((d.ng > 0 || d.flush) ? 2 * sbytes : sbytes);  // generated: write only
       }
     }
   }
@@ -338,12 +336,14 @@ sv_status sv_create(int n, sv_dtype dtype, void* dev_buf, size_t bytes, sv_state
   }
   if (cudaMalloc(&h->ctrl, sizeof(Ctrl)) != cudaSuccess ||
       cudaMalloc(&h->trace, sizeof(DTrace) * svp::MAX_TRACE) != cudaSuccess ||
-      cudaMalloc(&h->exp_ticket, sizeof(unsigned)) != cudaSuccess) {
+      cudaMalloc(&h->exp_ticket, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&h->work, sizeof(unsigned long long) * SV_WORK_COUNTERS) != cudaSuccess) {
     if (h->owns_state) cudaFree(h->state);
     return fail(SV_ERR_OOM, "control block allocation");
   }
   SV_CUDA(cudaMemset(h->ctrl, 0, sizeof(Ctrl)));
   SV_CUDA(cudaMemset(h->exp_ticket, 0, sizeof(unsigned)));
+  SV_CUDA(cudaMemset(h->work, 0, sizeof(unsigned long long) * SV_WORK_COUNTERS));
   SV_CUDA(svk::launch_init_state(h->dtype, h->state, 1ull << h->n_int, h->sms, nullptr));
   SV_CUDA(cudaDeviceSynchronize());
   *out = h.release();
@@ -358,6 +358,7 @@ sv_status sv_destroy(sv_state* h) {
   if (h->ctrl) cudaFree(h->ctrl);
   if (h->trace) cudaFree(h->trace);
   if (h->exp_ticket) cudaFree(h->exp_ticket);
+  if (h->work) cudaFree(h->work);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   delete h;
   return SV_OK;
@@ -1287,7 +1288,22 @@ sv_status sv_set_cache(sv_state* h, int enable) {
 
 sv_status sv_profile(sv_state* h, int enable) {
   if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (enable && !h->profiling)
+    SV_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned long long) * SV_WORK_COUNTERS, h->stream));
   h->profiling = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_profile_work(sv_state* h, sv_work_counts* out) {
+  if (!h || !out) return fail(SV_ERR_ARG, "null argument");
+  unsigned long long w[SV_WORK_COUNTERS];
+  SV_CUDA(cudaMemcpyAsync(w, h->work, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
+  SV_CUDA(cudaStreamSynchronize(h->stream));
+  out->bytes_read = w[0];
+  out->bytes_written = w[1];
+  out->gates = w[2];
+  out->draws = w[3];
+  out->passes = w[4];
   return SV_OK;
 }
 
@@ -1300,12 +1316,25 @@ sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, dou
     SV_CUDA(cudaEventElapsedTime(&t, h->events[i], h->events[i + 1]));
     ms += t;
   }
+  sv_work_counts w{};
+  const sv_status st = sv_profile_work(h, &w);
+  if (st != SV_OK) return st;
   if (total_ms) *total_ms = ms;
   if (launches) *launches = h->ev_used / 2;
-  if (bytes) *bytes = h->prof_bytes;
+  if (bytes) *bytes = double(w.bytes_read) + double(w.bytes_written);
   h->ev_used = 0;
-  h->prof_bytes = 0;
+  SV_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned long long) * SV_WORK_COUNTERS, h->stream));
   return SV_OK;
+}
+
+sv_status sv_selftest_wait(sv_state* h, uint32_t polls) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (polls > (1u << 24)) return fail(SV_ERR_ARG, "polls must be at most 2^24");
+  SV_CUDA(cudaMemsetAsync(&h->ctrl->status, 0, sizeof(int32_t), h->stream));
+  SV_CUDA(svk::launch_wait_probe(polls, &h->ctrl->status, h->stream));
+  const sv_status st = check_status(h);
+  if (st == SV_ERR_TIMEOUT) g_err = "bounded device wait ran out (self test: nothing arrives at its mbarrier)";
+  return st;
 }
 
 sv_status sv_sync(sv_state* h) {

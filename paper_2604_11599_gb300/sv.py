@@ -44,6 +44,11 @@ class ProgramStats(C.Structure):
                 ("block_barriers", C.c_uint64), ("warp_barriers", C.c_uint64), ("kernels_per_run", C.c_uint64)]
 
 
+class WorkCounts(C.Structure):
+    _fields_ = [("bytes_read", C.c_uint64), ("bytes_written", C.c_uint64), ("gates", C.c_uint64),
+                ("draws", C.c_uint64), ("passes", C.c_uint64)]
+
+
 class BranchStats(C.Structure):
     _fields_ = [("shots", C.c_uint64), ("paths", C.c_uint64), ("levels", C.c_uint64), ("max_draws", C.c_uint64)]
 
@@ -96,6 +101,8 @@ def lib():
         "sv_jit_check": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
+        "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
+        "sv_selftest_wait": ([vp, C.c_uint32], st),
         "sv_batch_create": ([i32, vp, C.POINTER(vp)], st),
         "sv_batch_add_program": ([vp, i32, vp, sz, vp, sz, vp, sz, C.POINTER(C.c_uint32)], st),
         "sv_batch_set_items": ([vp, vp, vp, vp, sz], st),
@@ -328,9 +335,20 @@ class State:
         _check(lib().sv_profile(self._h, 1 if enable else 0))
 
     def profile_read(self) -> dict:
+        """Pass-kernel time, launches and the device work counters since
+        profiling was enabled or last read (then reset)."""
+        w = WorkCounts()
+        _check(lib().sv_profile_work(self._h, C.byref(w)))
         ms, n, b = C.c_double(0), C.c_uint64(0), C.c_double(0)
         _check(lib().sv_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(b)))
-        return {"ms": ms.value, "launches": int(n.value), "bytes": b.value}
+        out = {"ms": ms.value, "launches": int(n.value), "bytes": b.value}
+        out.update({k: int(getattr(w, k)) for k, _ in WorkCounts._fields_})
+        return out
+
+    def selftest_wait(self, polls: int = 1000) -> None:
+        """Runs a bounded device wait that always runs out; raises SVError
+        (SV_ERR_TIMEOUT) exactly as a timed-out pass does."""
+        _check(lib().sv_selftest_wait(self._h, int(polls)))
 
     def tensor(self):
         """Zero-copy torch view (complex) of the state, or None without torch."""

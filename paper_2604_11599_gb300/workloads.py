@@ -103,6 +103,11 @@ def plain_small(seed: int = 1, n: int = 5, n_gates: int = 40, every: int = 8) ->
     return c
 
 
+# generator seed of the layered program for each (n, state type) of the plain-path
+# workload at full size: n=28/30 in complex128 and complex64
+LAYERED_SEEDS = {(28, "c128"): 2, (28, "c64"): 3, (30, "c128"): 4, (30, "c64"): 5}
+
+
 def layered(seed: int, n: int, layers: int = 20, block: int = 4) -> Circuit:
     """Layered dynamic circuit: each layer is a random rotation on every qubit
     then CX on a random perfect matching; after every ``block`` layers, measure

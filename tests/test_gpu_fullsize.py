@@ -1,0 +1,127 @@
+"""Oracle parity at the benchmarked sizes.
+
+* The plain-path layered program at n=28 and n=30, complex64 and complex128
+  (20 layers of rotations and CX matchings, measure + reset of two qubits every
+  four layers, a 3-bit feed-forward cond): the program, seed and kernels the
+  benchmark times.  Records bit-exact (near-threshold draws counted), all 2^n
+  amplitudes compared chunk by chunk against the FP64 oracle.  State offsets
+  pass 4 GiB here (n >= 29 complex64, n >= 28 complex128), the measurement
+  tables sum hundreds of tiles per CTA, and the copy pipeline runs in steady
+  state.
+* The batched launch of 65,536 trajectories (n ~ U{12..20} data qubits + one
+  ancilla, sequential feed-forward, loop(4) repeat-until-success): a seeded
+  subset of 4,096 trajectories, every qubit count included, against the oracle.
+* The n=20 hardware-efficient ansatz with 320 parameters and 200 Pauli terms:
+  energies of 16 parameter sets, every gradient entry of one set against the
+  oracle's parameter shift, and the gradient of every set along two random
+  directions against a 4-point stencil of the oracle's energy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2604_11599_gb300 import workloads as W
+
+from paritylib import AMP_TOL, BAND, compare_large, oracle_pool, tally, _orc_traj
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "c128": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def svmod():
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import sv
+
+    return sv
+
+
+@pytest.mark.parametrize("n,dtype", [(28, "c64"), (28, "c128"), (30, "c64"), (30, "c128")])
+def test_layered_full_size(svmod, orc, n, dtype):
+    """The benchmark's program and kernels (per-program specialised passes)."""
+    c = W.layered(W.LAYERED_SEEDS[(n, dtype)], n, layers=20)
+    with svmod.State(n, dtype) as st:
+        st.set_jit(True)
+        creg, err = compare_large(st, orc, c.ops, n, dtype, seed=0, shot=0,
+                                  label=f"layered n={n} {dtype}, full size (bench program)")
+        assert st.prepare(c.ops).stats["specialised"] == 1
+    print(f"n={n} {dtype}: creg {creg:#x}, max-abs amplitude error {err:.3g}")
+
+
+@pytest.fixture(scope="module")
+def batching_run(svmod):
+    """The whole 65,536-trajectory batched launch (seed 0, stream = trajectory id)."""
+    wl = W.batching(seed=6, n_traj=65536)
+    with svmod.Batch("c64") as b:
+        pid = {n: b.add_program(c.ops, n + 1) for n, c in wl.circuits.items()}
+        ids = np.array([pid[int(n)] for n in wl.traj_n])
+        got = b.run(ids, np.arange(len(ids)), np.zeros(len(ids)), seed=0)
+    return wl, got
+
+
+def test_batching_config_subset_vs_oracle(batching_run):
+    """4,096 seeded trajectories of the 65,536 (all qubit counts, 13..21 with the
+    ancilla) against the oracle: records bit-exact unless the oracle saw a draw
+    inside the complex64 band."""
+    wl, got = batching_run
+    r = np.random.default_rng(606)
+    pick = np.sort(r.choice(len(wl.traj_n), size=4096, replace=False))
+    assert set(int(wl.traj_n[i]) for i in pick) == set(range(12, 21))
+    jobs = [(wl.circuits[int(wl.traj_n[i])].ops, int(wl.traj_n[i]) + 1, 0, int(i), 0) for i in pick]
+    with oracle_pool() as pool:
+        res = pool.map(_orc_traj, jobs, chunksize=1)
+    bad = []
+    for i, (status, creg, margins, _) in zip(pick, res):
+        assert status == 0
+        in_band = bool((margins < BAND["c64"]).any())
+        mism = int(got[i]) != creg
+        tally("batching 4,096 of 65,536 trajectories, c64", margins, "c64", mismatch_in_band=int(mism and in_band))
+        if mism and not in_band:
+            bad.append(int(i))
+    assert not bad, f"{len(bad)} trajectories differ away from the threshold band, e.g. {bad[:5]}"
+
+
+@pytest.fixture(scope="module")
+def vqe_case():
+    n = 20
+    c = W.hea(n=n, layers=8)
+    terms = W.heisenberg_fields(seed=9, n=n, n_terms=200)
+    params = W.hea_params(seed=8, sets=16, n_params=320)
+    return n, c, terms, params
+
+
+@pytest.fixture(scope="module")
+def vqe_oracle(orc, vqe_case):
+    """Oracle energies of the 16 sets, parameter shift of every entry of set 0,
+    and 4-point-stencil directional derivatives of every set."""
+    n, c, terms, params = vqe_case
+    e = np.array([orc.energy(c.ops, n, p, terms) for p in params])
+    g0 = orc.param_shift_grad(c.ops, n, params[0], terms)
+    r = np.random.default_rng(808)
+    dirs = r.normal(size=(len(params), 2, params.shape[1]))
+    dirs /= np.linalg.norm(dirs, axis=2, keepdims=True)
+    h = 2e-4
+    dd = np.zeros((len(params), 2))
+    for s in range(len(params)):
+        for k in range(2):
+            f = [orc.energy(c.ops, n, params[s] + d * h * dirs[s, k], terms) for d in (2, 1, -1, -2)]
+            dd[s, k] = (-f[0] + 8 * f[1] - 8 * f[2] + f[3]) / (12 * h)
+    return e, g0, dirs, dd
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_vqe_config_16_sets(svmod, vqe_case, vqe_oracle, dtype):
+    """Per-term tolerance scaled by sum |c_t| (about 160 here) for sums and
+    gradients; the directional check adds the stencil's own error bound."""
+    n, c, terms, params = vqe_case
+    e, g0, dirs, dd = vqe_oracle
+    scale = float(np.abs(terms["coeff"]).sum())
+    val, grad = svmod.expval_grad_batch(c.ops, n, params, terms, dtype)
+    assert np.max(np.abs(val - e)) <= TOL[dtype] * scale
+    assert np.max(np.abs(grad[0] - g0)) <= TOL[dtype] * scale
+    got_dd = np.einsum("sp,skp->sk", grad, dirs)
+    assert np.max(np.abs(got_dd - dd)) <= TOL[dtype] * scale + 1e-9

@@ -168,7 +168,8 @@ def test_plain_small_config_records(svmod, orc):
     stats = {}
     with svmod.State(5, "c128") as st:
         for shot in range(1000):
-            compare_run(st, orc, c.ops, 5, "c128", seed=0, shot=shot, check_amps=(shot % 50 == 0), stats=stats)
+            compare_run(st, orc, c.ops, 5, "c128", seed=0, shot=shot, check_amps=(shot % 50 == 0), stats=stats,
+                        label="n=5 c128 feed-forward program, 1,000 shots (plain path)")
     assert stats["draws"] == 5000
     assert stats.get("forced", 0) == 0
 
@@ -183,7 +184,7 @@ def test_layered_config_small_sizes(svmod, orc, dtype, n, jit):
     with svmod.State(n, dtype) as st:
         st.set_jit(jit)
         for shot in range(2):
-            compare_run(st, orc, c.ops, n, dtype, seed=0, shot=shot)
+            compare_run(st, orc, c.ops, n, dtype, seed=0, shot=shot, label=f"layered n={n} {dtype} (small sizes)")
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
