@@ -254,6 +254,18 @@ sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t s
                           uint64_t* out);
 
 /*
+ * sv_sample_state with the samples left on the device: dev_out is a
+ * caller-owned device array of `shots` uint64 indices.  Asynchronous on the
+ * bound stream (for consumers on the GPU, e.g. a torch tensor); while
+ * profiling (sv_profile) its kernels are timed as one launch.  The two-level
+ * CDF scratch (8 bytes per 32 amplitudes plus 16 per 8,192) is allocated on
+ * first use and kept with the handle.  SV_ERR_ARG for a null handle or
+ * output, SV_ERR_CUDA on a launch error.
+ */
+sv_status sv_sample_state_device(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                                 uint64_t* dev_out);
+
+/*
  * <psi| sum_t coeff_t P_t |psi> of the current state (FP64 accumulation): the
  * energy <H> of a Hamiltonian given as a Pauli sum, as in the VQE experiments
  * (Sec. II-D; Sec. IV-A.2, H = Z0 Z1; Sec. IV-D).  terms is a host array read

@@ -1,11 +1,13 @@
 // kern_measure.cu -- terminal sampling and Pauli-sum expectation values.
 //
-// Sampling (shots, Sec. IV-C): FP64 block sums of |amp|^2 over fixed
-// 4096-amplitude blocks, an exclusive scan of the block sums, then one warp
-// per shot: Philox draw u for (seed, stream, shot, 2^32), binary search of the
-// block whose running CDF passes u * total, and a warp-scan walk through that
-// block for the smallest index with CDF > u * total.
-//
+// Sampling (shots, Sec. IV-C): shot s draws u for (seed, stream, s, 2^32)
+// and takes the smallest index i whose FP64 CDF exceeds u * total.  The CDF
+// is held at two levels, built in one read of the state: the state is cut
+// into runs of 32 amplitudes and blocks of 256 runs; k_cdf_runs sums each
+// run's |amp|^2 in index order (FP64) and stores, per run, the inclusive
+// prefix of run sums within its block; k_scan_blocks scans the block totals.
+// A shot then binary-searches the block prefixes, binary-searches the run
+// prefixes of its block, and walks the 32 amplitudes of one run.
 // Expectation (the energy <H> of the paper's VQE checks, Sec. IV-A.2 and
 // IV-D): terms that share an X mask x are evaluated in one read of the state.
 // For P = i^{|x&z|} X^x Z^z (Y where both bits are set),
@@ -18,9 +20,14 @@
 namespace svk {
 using namespace svp;
 
-constexpr int SAMPLE_BLOCK_BITS = 12;
+constexpr int RUN_BITS = 5;                 // 32 amplitudes per run
+constexpr int RUNS_PER_BLOCK_BITS = 8;      // 256 runs per block (one CTA of 256 threads)
+constexpr int SAMPLE_BLOCK_BITS = RUN_BITS + RUNS_PER_BLOCK_BITS;
 
+// blocks of the two-level CDF (states of fewer than 2^13 amplitudes: one block
+// of 2^(n - 5) runs)
 uint64_t sample_blocks(int n) { return n > SAMPLE_BLOCK_BITS ? (1ull << (n - SAMPLE_BLOCK_BITS)) : 1ull; }
+uint64_t sample_runs(int n) { return n > RUN_BITS ? (1ull << (n - RUN_BITS)) : 1ull; }
 
 template <typename T>
 __device__ __forceinline__ double abs2d(typename CxT<T>::V v) {
@@ -33,28 +40,57 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// |amp|^2 of the 32 amplitudes of run r, summed in index order (FP64), with
+// 16-byte loads: the same order the shot walk accumulates in.
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_sums(SampleArgs a, int bbits) {
-  using V = typename CxT<T>::V;
-  const V* s = reinterpret_cast<const V*>(a.state);
-  __shared__ double ws[8];
-  const uint64_t b = blockIdx.x;
-  const int tid = threadIdx.x;
-  const uint64_t base = b << bbits;
-  const int per = (1 << bbits);
+__device__ __forceinline__ double run_sum(const void* state, uint64_t r) {
   double acc = 0;
-  for (int i = tid; i < per; i += 256) acc += abs2d<T>(s[base + i]);
-  acc = warp_sum_d(acc);
-  if ((tid & 31) == 0) ws[tid >> 5] = acc;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0;
-    for (int w = 0; w < 8; ++w) t += ws[w];
-    a.block_sums[b] = t;
+  if constexpr (sizeof(T) == 4) {
+    const float4* s = reinterpret_cast<const float4*>(state) + (r << (RUN_BITS - 1));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float4 q = __ldcs(s + k);
+      acc += abs2d<T>(make_float2(q.x, q.y));
+      acc += abs2d<T>(make_float2(q.z, q.w));
+    }
+  } else {
+    const double2* s = reinterpret_cast<const double2*>(state) + (r << RUN_BITS);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc += abs2d<T>(__ldcs(s + k));
   }
+  return acc;
 }
 
-// exclusive scan of nb block sums by one CTA (fixed order)
+// One CTA per block, one thread per run: run sums, their inclusive prefix
+// within the block (warp scans, then warp totals in a fixed order), the
+// block total.  runs_in_block = 2^(bits of the block) / 32.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_block) {
+  __shared__ double wsum[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t b = blockIdx.x;
+  const bool live = tid < runs_in_block;
+  const uint64_t r = b * uint64_t(runs_in_block) + uint64_t(tid);
+  double v = live ? run_sum<T>(a.state, r) : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
+    const double y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  double off = 0;
+  for (int w = 0; w < warp; ++w) off += wsum[w];
+  v += off;
+  if (live) a.run_cum[r] = v;
+  if (tid == runs_in_block - 1) a.block_sums[b] = v;
+}
+
+// exclusive scan of nb block sums by one CTA (chunk sums per thread, chunk
+// bases in a fixed order).  At chunk boundaries block_prefix[i + 1] may differ
+// from block_prefix[i] + block_sums[i] by rounding; the shot walk then falls
+// back to the last nonzero amplitude of the block (a draw within an ulp of a
+// boundary).
 __global__ void __launch_bounds__(1024) k_scan_blocks(SampleArgs a, uint64_t nb) {
   __shared__ double tsum[1024];
   const int tid = threadIdx.x;
@@ -81,12 +117,12 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(SampleArgs a, uint64_t nb)
   }
 }
 
+// One thread per shot.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sample_search(SampleArgs a, uint64_t nb, int bbits) {
+__global__ void __launch_bounds__(256) k_sample_search(SampleArgs a, uint64_t nb, int runs_in_block) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
-  const int lane = threadIdx.x & 31;
-  const uint64_t shot = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t shot = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (shot >= a.shots) return;
   const double total = a.block_prefix[nb];
   const double u = draw_uniform(a.seed, a.stream, a.shot0 + shot, 1ull << 32);
@@ -98,41 +134,47 @@ __global__ void __launch_bounds__(256) k_sample_search(SampleArgs a, uint64_t nb
     if (a.block_prefix[mid + 1] > target) hi = mid;
     else lo = mid + 1;
   }
-  const uint64_t per = 1ull << bbits;
-  uint64_t found = ~0ull, last_nz = 0;
-  for (uint64_t b = lo; b < nb && found == ~0ull; ++b) {
-    double run = a.block_prefix[b];
-    for (uint64_t c = 0; c < per; c += 32) {
-      const uint64_t i = (b << bbits) + c + lane;
-      const double p = abs2d<T>(st[i]);
-      double inc = p;  // inclusive warp scan
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-      }
-      const unsigned hit = __ballot_sync(0xffffffffu, run + inc > target && p > 0);
-      const unsigned nz = __ballot_sync(0xffffffffu, p > 0);
-      if (nz) last_nz = (b << bbits) + c + (31 - __clz(nz));
-      if (hit) {
-        found = (b << bbits) + c + (__ffs(hit) - 1);
+  const uint64_t b = lo;
+  const double base = a.block_prefix[b];
+  const double* rc = a.run_cum + b * uint64_t(runs_in_block);
+  // smallest run r with base + rc[r] > target (non-decreasing in r)
+  int rl = 0, rh = runs_in_block - 1;
+  while (rl < rh) {
+    const int mid = (rl + rh) >> 1;
+    if (base + rc[mid] > target) rh = mid;
+    else rl = mid + 1;
+  }
+  // walk the run in the order its sum was taken
+  uint64_t found = ~0ull;
+  for (int r = rl; r >= 0 && found == ~0ull; --r) {
+    const uint64_t i0 = (b * uint64_t(runs_in_block) + uint64_t(r)) << RUN_BITS;
+    double c = base + (r > 0 ? rc[r - 1] : 0.0);
+    uint64_t last_nz = ~0ull;
+    for (int j = 0; j < 32; ++j) {
+      const double p = abs2d<T>(st[i0 + j]);
+      c += p;
+      if (p > 0) last_nz = i0 + j;
+      if (p > 0 && c > target && r == rl) {
+        found = i0 + j;
         break;
       }
-      run += __shfl_sync(0xffffffffu, inc, 31);
     }
+    // rounding at a run boundary (the target within an ulp of it), or a run
+    // of zeros: the last amplitude with nonzero probability at or before it
+    if (found == ~0ull && last_nz != ~0ull) found = last_nz;
   }
-  if (lane == 0) a.out[shot] = found != ~0ull ? found : last_nz;
+  a.out[shot] = found != ~0ull ? found : (b << (RUN_BITS + RUNS_PER_BLOCK_BITS));
 }
 
 template <typename T>
 static cudaError_t launch_sample_t(const SampleArgs& a, int sms, cudaStream_t s) {
-  const int bbits = a.n > SAMPLE_BLOCK_BITS ? SAMPLE_BLOCK_BITS : a.n;
   const uint64_t nb = sample_blocks(a.n);
-  k_block_sums<T><<<unsigned(nb), 256, 0, s>>>(a, bbits);
+  const int runs_in_block = int((a.n > SAMPLE_BLOCK_BITS ? (1ull << SAMPLE_BLOCK_BITS) : (1ull << a.n)) >> RUN_BITS);
+  k_cdf_runs<T><<<unsigned(nb), 256, 0, s>>>(a, runs_in_block);
   k_scan_blocks<<<1, 1024, 0, s>>>(a, nb);
   if (a.shots) {
-    const uint64_t warps = a.shots, blocks = (warps * 32 + 255) / 256;
-    k_sample_search<T><<<unsigned(blocks), 256, 0, s>>>(a, nb, bbits);
+    const uint64_t blocks = (a.shots + 255) / 256;
+    k_sample_search<T><<<unsigned(blocks), 256, 0, s>>>(a, nb, runs_in_block);
   }
   (void)sms;
   return cudaGetLastError();
@@ -143,28 +185,41 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------- expectation values
-constexpr int EXP_TERMS = 32;
+constexpr int EXP_TERMS = 32;  // terms per launch (launches of one X group share the read pattern)
 constexpr int EXP_CHUNK = 16;  // pairs summed in the state precision before an FP64 add
 
-template <typename T>
+// NT: the smallest power of two >= the launch's term count, so a group of one
+// or two terms carries one or two accumulators (FP32 chunk sums, then FP64),
+// not thirty-two; with NT <= 8 the Z masks and phases sit in registers.
+template <typename T, int NT>
 __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
-  __shared__ uint64_t zs[EXP_TERMS];
-  __shared__ int ks[EXP_TERMS];
-  __shared__ double red[8][EXP_TERMS];
+  __shared__ uint64_t zs[NT];
+  __shared__ int ks[NT];
+  __shared__ double red[8][NT];
   __shared__ int s_last;
   const int tid = threadIdx.x;
-  if (tid < a.nterms) {
-    zs[tid] = a.z_masks[tid];
-    ks[tid] = a.phase[tid];
+  const int nt = a.nterms;
+  if (tid < NT) {
+    zs[tid] = tid < nt ? a.z_masks[tid] : 0ull;
+    ks[tid] = tid < nt ? a.phase[tid] : 0;
   }
   __syncthreads();
-  const int nt = a.nterms;
-  double acc[EXP_TERMS];
-  T part[EXP_TERMS];
+  constexpr bool REG = NT <= 8;
+  uint64_t zr[REG ? NT : 1];
+  int kr[REG ? NT : 1];
+  if constexpr (REG) {
 #pragma unroll
-  for (int t = 0; t < EXP_TERMS; ++t) {
+    for (int t = 0; t < NT; ++t) {
+      zr[t] = zs[t];
+      kr[t] = ks[t];
+    }
+  }
+  double acc[NT];
+  T part[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
     acc[t] = 0;
     part[t] = 0;
   }
@@ -177,11 +232,13 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
       const V v = st[i];
       const T p = fma(v.x, v.x, v.y * v.y);
 #pragma unroll
-      for (int t = 0; t < EXP_TERMS; ++t)
-        if (t < nt) part[t] += (__popcll(i & zs[t]) & 1) ? -p : p;
+      for (int t = 0; t < NT; ++t) {
+        const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
+        part[t] += (__popcll(i & z) & 1) ? -p : p;
+      }
       if (++cnt == EXP_CHUNK) {
 #pragma unroll
-        for (int t = 0; t < EXP_TERMS; ++t) {
+        for (int t = 0; t < NT; ++t) {
           acc[t] += double(part[t]);
           part[t] = 0;
         }
@@ -198,18 +255,16 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
       // w = conj(psi_i) psi_j
       const T wr = fma(pi_.x, pj.x, pi_.y * pj.y), wi = fma(pi_.x, pj.y, -pi_.y * pj.x);
 #pragma unroll
-      for (int t = 0; t < EXP_TERMS; ++t) {
-        if (t < nt) {
-          const int k = ks[t];
-          T c = (k & 1) ? wi : wr;
-          if (k >= 2) c = -c;
-          c = c + c;
-          part[t] += (__popcll(i & zs[t]) & 1) ? -c : c;
-        }
+      for (int t = 0; t < NT; ++t) {
+        const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
+        const int k = REG ? kr[REG ? t : 0] : ks[t];
+        const T c = (k & 1) ? wi : wr;
+        const bool neg = ((__popcll(i & z) & 1) != 0) != (k >= 2);
+        part[t] += neg ? -c : c;
       }
       if (++cnt == EXP_CHUNK) {
 #pragma unroll
-        for (int t = 0; t < EXP_TERMS; ++t) {
+        for (int t = 0; t < NT; ++t) {
           acc[t] += double(part[t]);
           part[t] = 0;
         }
@@ -217,17 +272,19 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
       }
     }
   }
+  // a pair contributes twice its value (the pair (i^x, i) is not visited)
+  const double pw = x == 0 ? 1.0 : 2.0;
 #pragma unroll
-  for (int t = 0; t < EXP_TERMS; ++t) acc[t] += double(part[t]);
+  for (int t = 0; t < NT; ++t) acc[t] = pw * (acc[t] + double(part[t]));
   // block reduction (fixed order)
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-  for (int t = 0; t < EXP_TERMS; ++t) {
+  for (int t = 0; t < NT; ++t) {
     const double v = warp_sum_d(acc[t]);
     if (lane == 0) red[warp][t] = v;
   }
   __syncthreads();
-  if (tid < EXP_TERMS) {
+  if (tid < NT) {
     double s = 0;
     for (int w = 0; w < 8; ++w) s += red[w][tid];
     a.partials[blockIdx.x * EXP_TERMS + tid] = s;
@@ -246,10 +303,21 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   if (tid == 0) *a.ticket = 0;
 }
 
-cudaError_t launch_expval_group(int dtype, const ExpvalArgs& a, int grid, cudaStream_t s) {
-  if (dtype == SV_C64) k_expval_group<float><<<grid, 256, 0, s>>>(a);
-  else k_expval_group<double><<<grid, 256, 0, s>>>(a);
+template <typename T>
+static cudaError_t launch_expval_t(const ExpvalArgs& a, int grid, cudaStream_t s) {
+  const int nt = a.nterms;
+  if (nt <= 1) k_expval_group<T, 1><<<grid, 256, 0, s>>>(a);
+  else if (nt <= 2) k_expval_group<T, 2><<<grid, 256, 0, s>>>(a);
+  else if (nt <= 4) k_expval_group<T, 4><<<grid, 256, 0, s>>>(a);
+  else if (nt <= 8) k_expval_group<T, 8><<<grid, 256, 0, s>>>(a);
+  else if (nt <= 16) k_expval_group<T, 16><<<grid, 256, 0, s>>>(a);
+  else k_expval_group<T, 32><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_expval_group(int dtype, const ExpvalArgs& a, int grid, cudaStream_t s) {
+  if (a.nterms > EXP_TERMS) return cudaErrorInvalidValue;
+  return dtype == SV_C64 ? launch_expval_t<float>(a, grid, s) : launch_expval_t<double>(a, grid, s);
 }
 
 }  // namespace svk

@@ -181,11 +181,12 @@ cudaError_t launch_adjoint(int dtype, const AdjArgs& a, int grid, cudaStream_t s
 cudaError_t adjoint_occupancy(int dtype, uint32_t nterms, int* blocks_per_sm);
 #endif
 
-// terminal sampling: block sums -> scan -> per-shot search
+// terminal sampling: run sums and in-block prefixes -> block scan -> per-shot search
 struct SampleArgs {
   const void* state;
-  int n;                 // simulated qubits
+  int n;                 // simulated qubits (>= 10)
   int n_logical;
+  double* run_cum;       // [2^(n-5)] inclusive prefix of 32-amplitude run sums within each block
   double* block_sums;    // [nblocks]
   double* block_prefix;  // [nblocks] exclusive prefix; [nblocks] total at the end
   uint64_t shots, seed, stream, shot0;
@@ -196,6 +197,7 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 #endif
 #ifndef __CUDACC_RTC__
 uint64_t sample_blocks(int n);
+uint64_t sample_runs(int n);
 #endif
 
 // Pauli expectation values of one group of terms sharing an X mask

@@ -287,14 +287,15 @@ bool has_draws(const sv_op* ops, size_t n_ops) {
 
 sv_status sample_current(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
                          uint64_t* dev_out) {
-  const uint64_t nb = svk::sample_blocks(h->n_int);
-  SV_CUDA(h->sample_buf.reserve(2 * nb + 1));
+  const uint64_t nb = svk::sample_blocks(h->n_int), nr = svk::sample_runs(h->n_int);
+  SV_CUDA(h->sample_buf.reserve(nr + 2 * nb + 1));
   svk::SampleArgs a{};
   a.state = h->state;
   a.n = h->n_int;
   a.n_logical = h->n;
-  a.block_sums = h->sample_buf.p;
-  a.block_prefix = h->sample_buf.p + nb;
+  a.run_cum = h->sample_buf.p;
+  a.block_sums = h->sample_buf.p + nr;
+  a.block_prefix = h->sample_buf.p + nr + nb;
   a.shots = shots;
   a.seed = seed;
   a.stream = stream_id;
@@ -530,6 +531,27 @@ sv_status sv_sample_state(sv_state* h, uint64_t shots, uint64_t seed, uint64_t s
   return SV_OK;
 }
 
+sv_status sv_sample_state_device(sv_state* h, uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t shot0,
+                                 uint64_t* dev_out) {
+  if (!h || (shots && !dev_out)) return fail(SV_ERR_ARG, "null argument");
+  if (!shots) return SV_OK;
+  if (h->profiling) {
+    while (h->events.size() < h->ev_used + 2) {
+      cudaEvent_t e;
+      SV_CUDA(cudaEventCreate(&e));
+      h->events.push_back(e);
+    }
+    SV_CUDA(cudaEventRecord(h->events[h->ev_used], h->stream));
+  }
+  const sv_status st = sample_current(h, shots, seed, stream_id, shot0, dev_out);
+  if (st != SV_OK) return st;
+  if (h->profiling) {
+    SV_CUDA(cudaEventRecord(h->events[h->ev_used + 1], h->stream));
+    h->ev_used += 2;
+  }
+  return SV_OK;
+}
+
 sv_status sv_sample(sv_state* h, const sv_op* ops, size_t n_ops, const double* params, size_t n_params,
                     uint64_t shots, uint64_t seed, uint64_t stream_id, uint64_t* creg_out, uint64_t* bits_out) {
   if (!h) return fail(SV_ERR_ARG, "null handle");
@@ -655,7 +677,7 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
   SV_CUDA(h->exp_z.upload(zs, h->stream));
   SV_CUDA(h->exp_k.upload(ks, h->stream));
   SV_CUDA(h->exp_out.reserve(std::max<size_t>(nt, 1)));
-  const int grid = std::max(1, std::min(h->sms * 4, int((1ull << h->n_int) / 256)));
+  const int grid = std::max(1, std::min(h->sms * 8, int((1ull << h->n_int) / 256)));
   SV_CUDA(h->exp_partials.reserve(size_t(grid) * 32));
   size_t slot = 0;
   for (uint64_t x : keys) {

@@ -82,6 +82,7 @@ def lib():
         "sv_get_trace": ([vp, vp, sz, C.POINTER(sz)], st),
         "sv_sample": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, vp], st),
         "sv_sample_state": ([vp, u64, u64, u64, u64, vp], st),
+        "sv_sample_state_device": ([vp, u64, u64, u64, u64, vp], st),
         "sv_sample_branched": ([vp, vp, sz, vp, sz, u64, u64, u64, vp, C.POINTER(BranchStats)], st),
         "sv_batch_sample_branched": ([vp, vp, vp, vp, sz, u64, vp, C.POINTER(BranchStats)], st),
         "sv_clifford_create": ([i32, vp, sz, vp, C.POINTER(vp)], st),
@@ -308,6 +309,11 @@ class State:
         out = np.zeros(shots, dtype=np.uint64)
         _check(lib().sv_sample_state(self._h, shots, seed, stream_id, shot0, _ptr(out)))
         return out
+
+    def sample_state_device(self, out, seed: int = 0, stream_id: int = 0, shot0: int = 0) -> None:
+        """Terminal samples into a device tensor (uint64 / int64, one per shot);
+        asynchronous on the bound stream."""
+        _check(lib().sv_sample_state_device(self._h, int(out.numel()), seed, stream_id, shot0, out.data_ptr()))
 
     def expval(self, terms: np.ndarray):
         terms = np.ascontiguousarray(terms)

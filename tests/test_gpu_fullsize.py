@@ -48,7 +48,10 @@ def test_layered_full_size(svmod, orc, n, dtype):
         st.set_jit(True)
         creg, err = compare_large(st, orc, c.ops, n, dtype, seed=0, shot=0,
                                   label=f"layered n={n} {dtype}, full size (bench program)")
-        assert st.prepare(c.ops).stats["specialised"] == 1
+        prog = st.prepare(c.ops)  # a private copy: compiled at its first launch
+        st.launch(prog, seed=0, shot=0)
+        st.sync()
+        assert prog.stats["specialised"] == 1
     print(f"n={n} {dtype}: creg {creg:#x}, max-abs amplitude error {err:.3g}")
 
 

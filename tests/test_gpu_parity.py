@@ -310,6 +310,60 @@ def test_terminal_samples_vs_oracle(svmod, orc, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+def test_terminal_samples_large_state_vs_oracle(svmod, orc, dtype):
+    """A state of many CDF blocks (n=19: 64 blocks of 256 runs) against the oracle."""
+    n = 19
+    c = W.layered(31, n, layers=3)
+    with svmod.State(n, dtype) as st:
+        st.run(c.ops, seed=2)
+        got = st.sample_state(4000, seed=5, stream_id=3)
+    ref = orc.run(c.ops, n, seed=2)
+    want, margin = orc.sample(ref.psi, 4000, seed=5, stream=3)
+    band = 1e-12 if dtype == "c128" else 1e-4
+    bad = (got != want) & (margin > band)
+    assert not bad.any(), f"{int(bad.sum())} samples differ away from CDF ties"
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_terminal_samples_sparse_and_uniform_states(svmod, orc, dtype):
+    """Closed forms: a basis state |x> always gives x; GHZ gives 0 or 2^n - 1
+    only (runs and blocks of zeros between them); |+>^n gives floor(u 2^n)
+    (all |amp|^2 equal, so the CDF is proportional to i + 1 up to the
+    summation's rounding; draws within 1e-6 of an index boundary are left
+    out)."""
+    import torch
+
+    n = 20
+    for x in (0, 1, 12345, (1 << n) - 1, 1 << 19):
+        c = Circuit(n)
+        for q in range(n):
+            if (x >> q) & 1:
+                c.x(q)
+        with svmod.State(n, dtype) as st:
+            st.run(c.ops)
+            assert (st.sample_state(500, seed=x) == x).all()
+            dev = torch.empty(300, dtype=torch.int64, device="cuda")
+            st.sample_state_device(dev, seed=x)
+            assert (dev.cpu().numpy() == x).all()
+    with svmod.State(n, dtype) as st:
+        st.run(W.ghz(n).ops)
+        got = st.sample_state(4000, seed=7)
+        assert set(np.unique(got).tolist()) == {0, (1 << n) - 1}
+        assert 1800 < int((got == 0).sum()) < 2200
+        c = Circuit(n)
+        for q in range(n):
+            c.h(q)
+        st.run(c.ops)
+        got = st.sample_state(3000, seed=8, stream_id=2, shot0=11)
+    t = np.array([orc.uniform(8, 2, 11 + s, 1 << 32) * (1 << n) for s in range(3000)])
+    want = np.floor(t).astype(np.uint64)
+    frac = t - np.floor(t)
+    ok = np.minimum(frac, 1 - frac) > 1e-6
+    assert ok.mean() > 0.99
+    assert np.array_equal(got[ok], want[ok])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 def test_sample_program_shots(svmod, orc, dtype):
     c = W.plain_small(seed=3)
     with svmod.State(5, dtype) as st:
