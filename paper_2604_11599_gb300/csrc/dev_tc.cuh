@@ -157,18 +157,17 @@ struct TcCtx {
   uint32_t tmem;   // tensor-memory base address
   uint32_t phase;  // completed MMA batches (parity of the next wait)
   bool on;         // dense gates of this pass go to the tensor cores
-  bool ok;         // false (for the whole warp) after a wait ran out: the warp neither
-                   // writes nor reads tensor memory again, and thread 0 issues no MMA
-  bool drain;      // thread 0: a batch it committed was not seen to complete
+  bool ok;         // false after a wait ran out: the thread issues and waits no more
+  uint32_t drain;  // thread 0: 1 + parity of the batch whose wait ran out (0: none)
 };
 
 // Give-up path of a completion wait that ran out (SV_ERR_TIMEOUT): before the
 // CTA frees its tensor memory, the issuing thread waits once more, again
-// bounded, for the last batch it committed, so that no MMA it issued can
-// still write columns the CTA no longer owns when that batch does finish in
-// time.  Called by every thread of the CTA; uniform barriers.
+// bounded, for the batch it gave up on (the last one it committed), so that
+// no MMA it issued can still write columns the CTA no longer owns if that
+// batch finishes within the second wait.  Called by every thread of the CTA.
 __device__ __forceinline__ void tc_drain(TcCtx& tc) {
-  if (threadIdx.x == 0 && tc.drain) mbar_wait(&tc.s->bar, (tc.phase - 1u) & 1u, TC_WAIT_POLLS);
+  if (threadIdx.x == 0 && tc.drain) mbar_wait(&tc.s->bar, tc.drain - 1u, TC_WAIT_POLLS);
 }
 
 }  // namespace svk

@@ -40,38 +40,44 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// |amp|^2 of the 32 amplitudes of run r, summed in index order (FP64), with
-// 16-byte loads: the same order the shot walk accumulates in.
-template <typename T>
-__device__ __forceinline__ double run_sum(const void* state, uint64_t r) {
-  double acc = 0;
-  if constexpr (sizeof(T) == 4) {
-    const float4* s = reinterpret_cast<const float4*>(state) + (r << (RUN_BITS - 1));
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float4 q = __ldcs(s + k);
-      acc += abs2d<T>(make_float2(q.x, q.y));
-      acc += abs2d<T>(make_float2(q.z, q.w));
-    }
-  } else {
-    const double2* s = reinterpret_cast<const double2*>(state) + (r << RUN_BITS);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc += abs2d<T>(__ldcs(s + k));
-  }
-  return acc;
-}
-
-// One CTA per block, one thread per run: run sums, their inclusive prefix
-// within the block (warp scans, then warp totals in a fixed order), the
-// block total.  runs_in_block = 2^(bits of the block) / 32.
+// One CTA per block, one warp per 32 runs (1,024 amplitudes), loaded
+// coalesced: at step k, complex64 lane l holds amplitudes 64k + 2l, +1 (run
+// 2k + l/16), complex128 lane l holds amplitude 32k + l (run k).  A run's sum
+// is a reduction over its lanes (|amp|^2 in FP64, each lane's own pair in
+// index order, then a fixed butterfly), handed to lane (run mod 32); then the
+// inclusive prefix of the block's run sums (warp scans, warp totals in a
+// fixed order) and the block total.  runs_in_block: 2^(block bits) / 32.
 template <typename T>
 __global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_block) {
   __shared__ double wsum[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t b = blockIdx.x;
-  const bool live = tid < runs_in_block;
-  const uint64_t r = b * uint64_t(runs_in_block) + uint64_t(tid);
-  double v = live ? run_sum<T>(a.state, r) : 0.0;
+  const int r_local = warp * 32 + lane;  // the run this lane ends up holding
+  const bool live = r_local < runs_in_block;
+  const uint64_t a0 = (b * uint64_t(runs_in_block) + uint64_t(warp) * 32u) << RUN_BITS;  // warp's first amplitude
+  const int wruns = runs_in_block - warp * 32 < 32 ? runs_in_block - warp * 32 : 32;  // runs of this warp
+  double mine = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    const float4* s = reinterpret_cast<const float4*>(a.state) + (a0 >> 1);
+    for (int k = 0; 2 * k < wruns; ++k) {
+      const float4 q = __ldcs(s + 32 * k + lane);
+      double v = abs2d<T>(make_float2(q.x, q.y)) + abs2d<T>(make_float2(q.z, q.w));
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      const double lo = __shfl_sync(0xffffffffu, v, 0), hi = __shfl_sync(0xffffffffu, v, 16);
+      if (lane == 2 * k) mine = lo;
+      if (lane == 2 * k + 1) mine = hi;
+    }
+  } else {
+    const double2* s = reinterpret_cast<const double2*>(a.state) + a0;
+    for (int k = 0; k < wruns; ++k) {
+      double v = abs2d<T>(__ldcs(s + 32 * k + lane));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == k) mine = v;
+    }
+  }
+  double v = live ? mine : 0.0;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scan
     const double y = __shfl_up_sync(0xffffffffu, v, o);
@@ -82,8 +88,9 @@ __global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_bloc
   double off = 0;
   for (int w = 0; w < warp; ++w) off += wsum[w];
   v += off;
+  const uint64_t r = b * uint64_t(runs_in_block) + uint64_t(r_local);
   if (live) a.run_cum[r] = v;
-  if (tid == runs_in_block - 1) a.block_sums[b] = v;
+  if (r_local == runs_in_block - 1) a.block_sums[b] = v;
 }
 
 // exclusive scan of nb block sums by one CTA (chunk sums per thread, chunk
@@ -144,7 +151,9 @@ __global__ void __launch_bounds__(256) k_sample_search(SampleArgs a, uint64_t nb
     if (base + rc[mid] > target) rh = mid;
     else rl = mid + 1;
   }
-  // walk the run in the order its sum was taken
+  // walk the run; its amplitudes were summed in another order for the run
+  // sums, so a target within rounding of the run's end may find no crossing
+  // here (handled below)
   uint64_t found = ~0ull;
   for (int r = rl; r >= 0 && found == ~0ull; --r) {
     const uint64_t i0 = (b * uint64_t(runs_in_block) + uint64_t(r)) << RUN_BITS;
@@ -187,6 +196,7 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 // ---------------------------------------------------------------------- expectation values
 constexpr int EXP_TERMS = 32;  // terms per launch (launches of one X group share the read pattern)
 constexpr int EXP_CHUNK = 16;  // pairs summed in the state precision before an FP64 add
+constexpr int EXP_UNROLL = 4;  // loads in flight per thread
 
 // NT: the smallest power of two >= the launch's term count, so a group of one
 // or two terms carries one or two accumulators (FP32 chunk sums, then FP64),
@@ -226,50 +236,69 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   const uint64_t N = 1ull << a.n;
   const uint64_t x = a.x_mask;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  // EXP_UNROLL independent loads in flight per thread (grid-stride order kept)
+  constexpr int U = NT >= 16 ? 1 : EXP_UNROLL;
   int cnt = 0;
-  if (x == 0) {
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + tid; i < N; i += stride) {
-      const V v = st[i];
-      const T p = fma(v.x, v.x, v.y * v.y);
+  auto flush = [&]() {
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
-        part[t] += (__popcll(i & z) & 1) ? -p : p;
+    for (int t = 0; t < NT; ++t) {
+      acc[t] += double(part[t]);
+      part[t] = 0;
+    }
+    cnt = 0;
+  };
+  if (x == 0) {
+    for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + tid; i0 < N; i0 += U * stride) {
+      V v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + uint64_t(u) * stride;
+        v[u] = i < N ? st[i] : mkc(T(0), T(0));
       }
-      if (++cnt == EXP_CHUNK) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = i0 + uint64_t(u) * stride;
+        const T p = fma(v[u].x, v[u].x, v[u].y * v[u].y);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          acc[t] += double(part[t]);
-          part[t] = 0;
+          const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
+          part[t] += (__popcll(i & z) & 1) ? -p : p;
         }
-        cnt = 0;
       }
+      cnt += U;
+      if (cnt >= EXP_CHUNK) flush();
     }
   } else {
     const int h = 63 - __clzll((long long)x);
     const uint64_t half = N >> 1;
     const uint64_t lowm = (1ull << h) - 1;
-    for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + tid; r < half; r += stride) {
-      const uint64_t i = ((r >> h) << (h + 1)) | (r & lowm);  // bit h of i is 0
-      const V pi_ = st[i], pj = st[i ^ x];
-      // w = conj(psi_i) psi_j
-      const T wr = fma(pi_.x, pj.x, pi_.y * pj.y), wi = fma(pi_.x, pj.y, -pi_.y * pj.x);
+    for (uint64_t r0 = uint64_t(blockIdx.x) * blockDim.x + tid; r0 < half; r0 += U * stride) {
+      V pi_[U], pj[U];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
-        const int k = REG ? kr[REG ? t : 0] : ks[t];
-        const T c = (k & 1) ? wi : wr;
-        const bool neg = ((__popcll(i & z) & 1) != 0) != (k >= 2);
-        part[t] += neg ? -c : c;
+      for (int u = 0; u < U; ++u) {
+        const uint64_t r = r0 + uint64_t(u) * stride;
+        const uint64_t i = ((r >> h) << (h + 1)) | (r & lowm);  // bit h of i is 0
+        const bool ok = r < half;
+        pi_[u] = ok ? st[i] : mkc(T(0), T(0));
+        pj[u] = ok ? st[i ^ x] : mkc(T(0), T(0));
       }
-      if (++cnt == EXP_CHUNK) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t r = r0 + uint64_t(u) * stride;
+        const uint64_t i = ((r >> h) << (h + 1)) | (r & lowm);
+        // w = conj(psi_i) psi_j
+        const T wr = fma(pi_[u].x, pj[u].x, pi_[u].y * pj[u].y), wi = fma(pi_[u].x, pj[u].y, -pi_[u].y * pj[u].x);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          acc[t] += double(part[t]);
-          part[t] = 0;
+          const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
+          const int k = REG ? kr[REG ? t : 0] : ks[t];
+          const T c = (k & 1) ? wi : wr;
+          const bool neg = ((__popcll(i & z) & 1) != 0) != (k >= 2);
+          part[t] += neg ? -c : c;
         }
-        cnt = 0;
       }
+      cnt += U;
+      if (cnt >= EXP_CHUNK) flush();
     }
   }
   // a pair contributes twice its value (the pair (i^x, i) is not visited)

@@ -267,7 +267,7 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
   const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
   const uint32_t half = uint32_t(warp >> 2);
-  if (tc.ok) {  // this thread's row, 16 columns at a time: high parts (columns 0..31), low parts (32..63)
+  {  // this thread's row, 16 columns at a time: high parts (columns 0..31), low parts (32..63)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t w[16];
@@ -281,7 +281,7 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
       tmem_st16(tc.tmem + lane_base + 64u * half + 16u * uint32_t(q), w);
     }
   }
-  if (tc.ok) tmem_wait_st();
+  tmem_wait_st();
   tc_fence_before();
   __syncthreads();  // all rows in tensor memory, previous results read
   if (tid == 0 && tc.ok) {
@@ -301,24 +301,23 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
     }
     mma_commit(&s.bar);
   }
-  // After a wait ran out the warp stops touching tensor memory (tcgen05.st /
-  // ld are warp-collective, so the decision is made per warp) and thread 0
-  // issues no further MMA; the block barriers stay uniform, the pass ends, the
-  // CTA drains (tc_drain) before it frees tensor memory, and the run reports
-  // SV_ERR_TIMEOUT with the state undefined.
-  const bool issued = tid == 0 && tc.ok;
-  if (tc.ok) tc.ok = mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS);
-  tc.ok = __all_sync(0xffffffffu, tc.ok);
-  if (issued && !tc.ok) tc.drain = true;
+  // After a wait ran out the thread issues and waits no more (the barriers
+  // stay uniform), so the pass ends within one more wait period and the run
+  // reports SV_ERR_TIMEOUT with the state undefined; tensor-memory reads of
+  // an unfinished batch only yield garbage.  The issuing thread remembers
+  // the batch it gave up on: the CTA drains it (tc_drain) before it frees
+  // its tensor memory, so no MMA can write columns it no longer owns.
+  if (tc.ok && !mbar_wait(&s.bar, tc.phase & 1u, TC_WAIT_POLLS)) {
+    tc.ok = false;
+    if (tid == 0) tc.drain = 1u + (tc.phase & 1u);
+  }
   ++tc.phase;
   tc_fence_after();
-  if (tc.ok) {
-    uint32_t r[32];
-    tmem_ld32(tc.tmem + lane_base + 128u + 32u * half, r);
-    tmem_wait_ld();
+  uint32_t r[32];
+  tmem_ld32(tc.tmem + lane_base + 128u + 32u * half, r);
+  tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-  }
+  for (int j = 0; j < 16; ++j) a[j] = mkc(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
 }
 
 // A dense four-qubit unitary: on the tensor cores where the pass enabled them
@@ -851,7 +850,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
   const bool do_work = do_store || needed;
   const bool need_ticket = sp.nc > 0 || (do_store && !ident);
 
-  TcCtx tc{tc_shared(sh), nullptr, 0u, 0u, false, true, false};
+  TcCtx tc{tc_shared(sh), nullptr, 0u, 0u, false, true, 0u};
   if (do_work) {
     if (any_gate)
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) smat[i] = reinterpret_cast<const V*>(A.mats)[sp.mat0 + i];

@@ -330,28 +330,88 @@ struct Builder {
     uint32_t mat = 0;
     uint32_t dots = 0;
 
-    // stages: greedy, four register bits, dependency order preserved
+    // stages: four register bits each, dependency order preserved.  Two
+    // packings are built and the one with fewer stages is kept (each stage
+    // moves the tile through shared memory once): first fit in program order,
+    // and one that gives each stage the register set (among all sets of
+    // reg_bits of the remaining gates' local bits) under which the most
+    // remaining gates can run.
     std::vector<uint32_t> stS;
     std::vector<std::vector<int>> stG;
-    std::vector<int> rem(chosen);
-    while (!rem.empty()) {
-      uint32_t S = 0, blocked = 0;
-      std::vector<int> sg, left;
-      for (int idx : rem) {
-        const Item& it = items[idx];
+    {
+      std::vector<uint32_t> lmask(chosen.size());
+      for (size_t i = 0; i < chosen.size(); ++i) {
+        const Item& it = items[chosen[i]];
         uint32_t lm = 0;
         for (int k = 0; k < it.nq; ++k) lm |= 1u << loc[it.q[k]];
-        if ((lm & blocked) || popc(S | lm) > reg_bits) {
-          blocked |= lm;
-          left.push_back(idx);
-          continue;
-        }
-        S |= lm;
-        sg.push_back(idx);
+        lmask[i] = lm;
       }
-      rem.swap(left);
-      stS.push_back(S);
-      stG.push_back(sg);
+      // gates (positions into chosen) that run under register set S, in order
+      auto take = [&](const std::vector<int>& rem, uint32_t S, std::vector<int>& sg, std::vector<int>& left,
+                      bool grow) -> uint32_t {
+        uint32_t blocked = 0, used = 0;
+        for (int i : rem) {
+          const uint32_t lm = lmask[size_t(i)];
+          const bool fits = grow ? popc(used | lm) <= reg_bits : (lm & ~S) == 0;
+          if ((lm & blocked) || !fits) {
+            blocked |= lm;
+            left.push_back(i);
+            continue;
+          }
+          used |= lm;
+          sg.push_back(i);
+        }
+        return used;
+      };
+      auto pack = [&](bool best, std::vector<uint32_t>& oS, std::vector<std::vector<int>>& oG) {
+        std::vector<int> rem(chosen.size());
+        for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
+        while (!rem.empty()) {
+          std::vector<int> sg, left;
+          uint32_t S = 0;
+          if (!best) {
+            S = take(rem, 0, sg, left, true);
+          } else {
+            uint32_t bits = 0;
+            for (int i : rem) bits |= lmask[size_t(i)];
+            std::vector<int> bl;
+            for (int j = 0; j < 32; ++j)
+              if ((bits >> j) & 1) bl.push_back(j);
+            const int k = std::min<int>(reg_bits, int(bl.size()));
+            size_t bestn = 0;
+            uint32_t bestS = 0;
+            std::vector<int> pick(static_cast<size_t>(k));
+            for (int i = 0; i < k; ++i) pick[size_t(i)] = i;
+            while (true) {  // every k-subset of the remaining gates' local bits
+              uint32_t Sc = 0;
+              for (int i : pick) Sc |= 1u << bl[size_t(i)];
+              std::vector<int> a, b;
+              take(rem, Sc, a, b, false);
+              if (a.size() > bestn) {
+                bestn = a.size();
+                bestS = Sc;
+              }
+              int i = k - 1;
+              while (i >= 0 && pick[size_t(i)] == int(bl.size()) - k + i) --i;
+              if (i < 0) break;
+              ++pick[size_t(i)];
+              for (int j = i + 1; j < k; ++j) pick[size_t(j)] = pick[size_t(j - 1)] + 1;
+            }
+            S = take(rem, bestS, sg, left, false);
+          }
+          for (int& i : sg) i = chosen[size_t(i)];
+          rem.swap(left);
+          oS.push_back(S);
+          oG.push_back(sg);
+        }
+      };
+      std::vector<uint32_t> s1, s2;
+      std::vector<std::vector<int>> g1, g2;
+      pack(false, s1, g1);
+      if (!adjoint && s1.size() > 1) pack(true, s2, g2);
+      const bool use_best = !s2.empty() && s2.size() < s1.size();
+      stS = use_best ? s2 : s1;
+      stG = use_best ? g2 : g1;
     }
 
     // Warp ownership.  With 2^m >= 16 * PASS_THREADS every thread holds one
