@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--circuit", default="layered", choices=["layered", "dense4"],
                     help="layered: the plain dynamic-circuit workload; dense4: layers of dense 4-qubit unitaries")
     ap.add_argument("--no-dense-tc", action="store_true", help="dense 4-qubit gates on the FP32 pipes")
+    ap.add_argument("--first-fit", action="store_true", help="plan tiles by first fit instead of by the gates they unlock")
     return ap.parse_args()
 
 
@@ -268,6 +269,11 @@ def measure_forms(sv, torch):
         b.launch(0)
         b.results()
         tb = time.perf_counter() - t0
+        b.profile(True)  # the same launch once more with the device work counters on
+        b.launch(0)
+        b.results()
+        bw = b.work()
+        b.profile(False)
     sample = wl.traj_n[:256]
     states = {}
     for n in sorted(set(int(v) for v in sample)):
@@ -282,7 +288,15 @@ def measure_forms(sv, torch):
     out["batching"] = {"workload": "65,536 trajectories, n~U{12..20}+ancilla, 10 layers, sequential feed-forward "
                                    "+ loop(4) RUS, complex64, one persistent launch",
                        "trajectories_per_s": len(ids) / tb, "plain_path_trajectories_per_s": 256 / tp,
-                       "plain_path_sample": "first 256 trajectories, one sv_run each", "seconds": tb}
+                       "plain_path_sample": "first 256 trajectories, one sv_run each", "seconds": tb,
+                       "updates_per_s": bw["updates"] / tb,
+                       "updates_counted": "executed gates and draws x 2^n (n = 13..21 with the ancilla), counted "
+                                          "on the device in a second, identical launch",
+                       "state_bytes_per_s": (bw["bytes_read"] + bw["bytes_written"]) / tb,
+                       "state_bytes_frac_of_hbm": (bw["bytes_read"] + bw["bytes_written"]) / tb / 1e9
+                       / measured_peaks()[0]["hbm_gbs"],
+                       "state_bytes_note": "tile reads and writes of the per-CTA state slots (2^13..2^21 "
+                                           "amplitudes, largely L2-resident), against the HBM copy peak"}
     # plain small program, 1,000 shots, complex128
     c = W.plain_small()
     with sv.State(5, "c128") as st:
@@ -386,8 +400,10 @@ def measure_forms(sv, torch):
     c = W.hea(20, 8)
     terms = W.heisenberg_fields(9, 20, 200)
     vqe = {}
-    for dt, sets in (("c64", 1024), ("c128", 256)):
+    for dt in ("c64", "c128"):
+        sets = 1024
         h = sv.Grad(c.ops, 20, terms, dt)
+        gi = h.info()
         prm = torch.tensor(W.hea_params(8, sets, 320), device="cuda")
         h.run(prm[:4])
         torch.cuda.synchronize()
@@ -395,9 +411,25 @@ def measure_forms(sv, torch):
         h.run(prm)
         torch.cuda.synchronize()
         dts = time.perf_counter() - t0
-        vqe[dt] = {"parameter_sets": sets, "gradient_sets_per_s": sets / dts, "seconds": dts}
+        amp = 8 if dt == "c64" else 16
+        S = float(1 << gi["state_qubits"]) * amp
+        # per set: |0> written, forward passes read + write psi, lambda = H psi gathers psi once per
+        # term group and writes lambda, backward passes read + write psi and lambda
+        per_set = S * (1 + 2 * gi["forward_passes"] + gi["term_groups"] + 2 + 4 * gi["backward_passes"])
+        upd = float(gi["gates"]) * 3 * float(1 << gi["state_qubits"])  # forward, then U^dagger on psi and lambda
+        vqe[dt] = {"parameter_sets": sets, "gradient_sets_per_s": sets / dts, "seconds": dts,
+                   "updates_per_s": sets * upd / dts,
+                   "updates_counted": "(forward gates + backward gates on psi and on lambda) x 2^20 per set",
+                   "state_bytes_per_s": sets * per_set / dts,
+                   "state_bytes_frac_of_hbm": sets * per_set / dts / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                   "work_per_set": gi}
         h.close()
     out["vqe_adjoint"] = vqe
+    # the plain path's other sizes and state types (the headline line is n=30 complex64)
+    p2 = {}
+    for n2, dt2 in ((28, "c64"), (28, "c128"), (30, "c128")):
+        p2[f"n{n2}_{dt2}"] = plain_line(sv, torch, n2, dt2)
+    out["plain_layered_other_sizes"] = p2
     # terminal sampling and Pauli-sum expectation on an n=28 complex64 state (one read of the
     # state per sampling call; one per group of terms that share an X mask)
     peaks, kind = measured_peaks()
@@ -478,26 +510,97 @@ def measure_forms(sv, torch):
                 "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_kind": f"of {kind}",
                 "dense_tflops_useful": useful / (prof["ms"] / 1000.0) / 1e12}
     out["dense4"] = dense
-    # serving: a bounded slice of the Poisson request stream, server vs sequential plain path
-    stream = W.serving_stream(seed=10, gen_seed=11, rate=200.0, duration=1.0, n_lo=10, n_hi=22, d_lo=10,
-                              d_hi=40, max_shots=256)
+    # serving, the stated request mix (n log-uniform 10-30, depth 10-100, 1-8 measures with
+    # cond/loop feed-forward, shots log-uniform 1-4,096, Poisson 200 req/s) on a shortened stream
+    out["serving"] = serving_form(sv, torch, W, serve, np)
+    return out
+
+
+def plain_line(sv, torch, n, dtype, steps=3, warmup=2):
+    """One configuration of the plain layered workload: device time of whole
+    trajectories, updates and bytes counted by the pass kernels."""
+    c = circuit(n, dtype)
+    peaks, kind = measured_peaks()
+    with sv.State(n, dtype) as st:
+        st.set_jit(True)
+        prog = st.prepare(c.ops)
+        st.launch(prog, shot=999)
+        for i in range(warmup):
+            st.launch(prog, shot=1000 + i)
+        torch.cuda.synchronize()
+        st.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            st.launch(prog, shot=i)
+        e1.record()
+        e1.synchronize()
+        prof = st.profile_read()
+        st.profile(False)
+        stats = prog.stats
+    ms = e0.elapsed_time(e1) / steps
+    gbs = prof["bytes"] / (prof["ms"] / 1000.0) / 1e9
+    line = {"workload": workload_name(n, dtype), "ms_per_step": ms,
+            "updates_per_s": prof["updates"] / steps / (ms / 1000.0), "passes": stats["passes"],
+            "pass_kernels_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"], "hbm_peak_kind": f"of {kind}"}
+    if dtype == "c128":
+        tf = fp64_ops_per_step(c.ops, stats["passes"], n) / (prof["ms"] / steps / 1000.0) / 1e12
+        line.update({"bound": "alu", "fp64_tflops": tf, "fp64_frac_of_nominal": tf / FP64_PEAK_TFLOPS})
+    return line
+
+
+def serving_form(sv, torch, W, serve, np, duration=0.5):
+    """The serving configuration's request mix, Poisson 200 req/s, cut to
+    `duration` seconds of arrivals (draining a 60 s stream takes far longer
+    than a bench run), served to completion by the continuous-batching server.
+    The sequential plain path (one request at a time, one trajectory per shot)
+    would need shots x (one trajectory) per request -- hours for the n=28..30
+    requests -- so it is modelled: one trajectory of every request is timed on
+    the plain path, its service time is shots x that time, and a FIFO queue
+    over the same arrivals gives its wall time and latencies."""
+    stream = W.serving_stream(seed=10, gen_seed=11, rate=200.0, duration=duration, n_lo=10, n_hi=30,
+                              d_lo=10, d_hi=100, max_shots=4096)
     reqs = serve.requests_from_stream(stream)
+    shots = int(sum(r.shots for r in reqs))
     be = serve.GpuBackend("c64", seed=0)
     srv = serve.Server(be)
-    srv.serve(reqs[:4])
-    _, st_srv = srv.serve(reqs)
+    warm = W.serving_stream(seed=12, gen_seed=13, rate=200.0, duration=0.05, n_lo=10, n_hi=20, d_lo=10,
+                            d_hi=20, max_shots=64)
+    srv.serve(serve.requests_from_stream(warm))
+    res, st_srv = srv.serve(reqs)
     srv.close()
-    be1 = serve.GpuBackend("c64", seed=0, branching=False)
-    srv = serve.Server(be1)
-    srv.serve(reqs[:4])
-    _, st_srv1 = srv.serve(reqs)
-    srv.close()
-    _, st_seq = serve.serve_sequential(be, reqs)
-    out["serving"] = {"workload": f"{len(reqs)} requests (Poisson 200/s for 1 s), n log-uniform 10-22, depth "
-                                  "10-40 layers, 1-8 measures with cond/loop feed-forward, shots log-uniform 1-256",
-                      "server": st_srv, "server_one_trajectory_per_shot": st_srv1,
-                      "sequential_plain_path": st_seq}
-    return out
+    # the sequential plain path, modelled from one timed trajectory of each request
+    t1 = {}
+    for r in reqs:
+        with sv.State(r.n, "c64") as st:
+            st.run(r.ops, seed=0, stream_id=r.rid, shot=0)
+            t0 = time.perf_counter()
+            st.run(r.ops, seed=0, stream_id=r.rid, shot=1)
+            t1[r.rid] = time.perf_counter() - t0
+    clock, lat = 0.0, []
+    for r in sorted(reqs, key=lambda q: (q.arrival, q.rid)):
+        clock = max(clock, r.arrival) + r.shots * t1[r.rid]
+        lat.append(clock - r.arrival)
+    ns = np.array([r.n for r in reqs])
+    offered_span = max(r.arrival for r in reqs)
+    return {
+        "workload": (f"{len(reqs)} requests: Poisson 200 req/s for {duration:g} s (the configuration's 60 s "
+                     "shortened so that the stream drains within the bench run), n log-uniform 10-30, depth "
+                     "log-uniform 10-100 layers, 1-8 mid-circuit measures each with cond or loop(k<=4) "
+                     "feed-forward, shots log-uniform 1-4,096, complex64, admission by HBM footprint"),
+        "requests": len(reqs), "shots": shots, "requests_n_ge_28": int((ns >= 28).sum()),
+        "offered": {"requests_per_s": len(reqs) / duration, "shots_per_s": shots / duration,
+                    "arrival_span_s": offered_span},
+        "server": dict(st_srv, drain_after_last_arrival_s=st_srv["wall_s"] - offered_span,
+                       achieved_requests_per_s=len(reqs) / st_srv["wall_s"]),
+        "sequential_plain_path_model": {
+            "shots_per_s": shots / clock, "wall_s": clock,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "how": "one trajectory per request timed on the plain path (sv_run, record read back); service "
+                   "time = shots x that time; FIFO over the same arrivals"},
+        "server_vs_sequential_shots_per_s": (shots / st_srv["wall_s"]) / (shots / clock),
+    }
 
 
 def run_reference(args, rank, world):
@@ -554,6 +657,7 @@ def main():
     st = sv.State(n, dtype)
     st.set_jit(not args.no_jit)
     st.set_dense_tc(not args.no_dense_tc)
+    st.set_tile_select(not args.first_fit)
     if len(c.pool):
         st.set_dense_pool(c.pool)
     prog = st.prepare(c.ops)

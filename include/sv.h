@@ -167,6 +167,16 @@ sv_status sv_bind_stream(sv_state* h, void* cuda_stream);
 sv_status sv_set_dense_pool(sv_state* h, const double* pool, size_t n_complex);
 
 /*
+ * How the planner picks each pass's tile qubits (the L contiguous low qubits
+ * plus m - L gathered ones; a pass runs the gates, in order, whose qubits are
+ * all tile qubits).  1 (default): the gathered qubits are chosen one at a time
+ * (a pair when no single qubit helps) for the number of further gates they let
+ * the pass run, so a program needs fewer passes; 0: first fit in program
+ * order.  Programs planned from now on use it.  SV_ERR_ARG for a null handle.
+ */
+sv_status sv_set_tile_select(sv_state* h, int closure);
+
+/*
  * Lower an op list for this state's n and dtype.  The caller's ops are read
  * during the call only.  SV_ERR_ARG for a malformed list (qubit >= n,
  * duplicate qubits, cbit >= 64, lengths out of range, nesting > 64),
@@ -350,6 +360,7 @@ sv_status sv_batch_destroy(sv_batch* b);
  */
 sv_status sv_batch_set_tuning(sv_batch* b, int low_bits, int max_pass_gates);
 
+
 /*
  * Clifford fast path: programs whose gates are all Clifford (I, H, X, Y, Z,
  * S, SDG, SX, CX, CY, CZ, SWAP) with MEASURE, RESET, COND and LOOP records,
@@ -417,6 +428,16 @@ sv_status sv_grad_create(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, 
 sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_t n_params, double* dev_val,
                       double* dev_grad);
 sv_status sv_grad_destroy(sv_grad* g);
+/* Shape of the work of one parameter set (for throughput and roofline
+ * accounting): forward and backward state passes, gates, Pauli term groups
+ * (one gather of the state each while lambda = H psi is formed), terms, the
+ * state's qubits after padding, and the parameter sets resident at once (one
+ * per CTA).  SV_ERR_ARG for a null argument. */
+typedef struct sv_grad_stats {
+  uint64_t forward_passes, backward_passes, gates;
+  uint32_t term_groups, terms, state_qubits, resident_sets;
+} sv_grad_stats;
+sv_status sv_grad_info(const sv_grad* g, sv_grad_stats* out);
 sv_status sv_expval_grad_batch(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* params,
                                size_t n_sets, size_t n_params, const sv_pauli* terms, size_t n_terms, double* val_out,
                                double* grad_out, void* cuda_stream);
@@ -456,10 +477,21 @@ typedef struct sv_work_counts {
   uint64_t gates;                     /* gate records executed                       */
   uint64_t draws;                     /* measure / reset draws executed              */
   uint64_t passes;                    /* pass launches that read or wrote the state  */
+  uint64_t updates;                   /* amplitude-gate updates: (gates + draws) x 2^n */
 } sv_work_counts;
 sv_status sv_profile(sv_state* h, int enable);
 sv_status sv_profile_read(sv_state* h, double* total_ms, uint64_t* launches, double* bytes);
 sv_status sv_profile_work(sv_state* h, sv_work_counts* out);
+
+/* Work counters of the batched launches (see sv_profile_work): while enabled,
+ * every trajectory's passes count on the device the state bytes they read and
+ * wrote (state slots, often resident in L2 for small n), the gate records and
+ * draws they executed and the amplitude-gate updates (2^n per executed gate
+ * or draw, n the trajectory's padded qubit count).  Enabling zeroes the
+ * counters; sv_batch_work waits for the batch's stream and reads them.
+ * SV_ERR_ARG for a null argument. */
+sv_status sv_batch_profile(sv_batch* b, int enable);
+sv_status sv_batch_work(sv_batch* b, sv_work_counts* out);
 
 /*
  * Self test of the failure path of bounded device waits (the tensor-core

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(PASS_THREADS, (sizeof(T) == 4 ? 2 : 1)) k_batc
     A.pass = 0;
     A.dense_tc = 0;  // tensor-core dense gates are a grid-pass feature
     A.gen_init = 0;  // each trajectory's slot is initialised by this kernel
-    A.work = nullptr;
+    A.work = B.work;
     for (uint32_t pi = 0; pi < P.npasses; ++pi) pass_body<T, M, true>(A, int(pi), sh, smem_raw);
     if (tid == 0) {
       B.creg_out[w.out] = C->creg;

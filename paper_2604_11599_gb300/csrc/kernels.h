@@ -25,9 +25,10 @@ struct PassArgs {
   int pass;          // pass index (specialised kernels select their stage program by it)
   int dense_tc;      // 1: dense four-qubit gates of complex64 2^12-amplitude tiles on the tensor cores
   int gen_init;      // 1: this launch is the program's first pass and generates |0...0> instead of loading it
-  // work counters (nullable; grid passes only): [0] bytes of the state read,
-  // [1] bytes of it written, [2] gate records executed (predicated-off ones
-  // excluded), [3] draws executed, [4] passes that touched the state
+  // work counters (nullable): [0] bytes of the state read, [1] bytes of it
+  // written, [2] gate records executed (predicated-off ones excluded), [3]
+  // draws executed, [4] passes that touched the state, [5] amplitude-gate
+  // updates (executed gates and draws, 2^n each)
   unsigned long long* work;
 };
 
@@ -115,6 +116,7 @@ struct BatchArgs {
   BrDraw* trace_out;         // [n_items][trace_cap]
   uint32_t trace_cap;
   uint64_t* m_out;           // [n_items] draws executed
+  unsigned long long* work;  // work counters of PassArgs::work (nullable)
 };
 constexpr int BATCH_TILE_BITS = 12;
 #ifndef __CUDACC_RTC__

@@ -573,6 +573,47 @@ __device__ __forceinline__ A warp_transpose_reduce16(A (&v)[16], int lane) {
   }
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
+// Double-float values: an unevaluated sum hi + lo of two FP32 numbers (about
+// 44 significant bits).  two_sum is Knuth's error-free addition, |x|^2 via the
+// FMA error-free product; used by the complex64 measurement table so that its
+// per-warp partial sums keep FP64-level accuracy before the FP64 accumulation.
+struct DF {
+  float hi, lo;
+};
+static __device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF{s, e};
+}
+static __device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s.hi, lo);  // renormalise (|s.hi| >= |lo|)
+  return DF{h, __fsub_rn(lo, __fsub_rn(h, s.hi))};
+}
+static __device__ __forceinline__ DF df_abs2(float2 x) {
+  const float p = __fmul_rn(x.x, x.x), q = __fmul_rn(x.y, x.y);
+  return df_add(DF{p, __fmaf_rn(x.x, x.x, -p)}, DF{q, __fmaf_rn(x.y, x.y, -q)});
+}
+// warp_transpose_reduce16 on double-float values (same lane -> slot map)
+__device__ __forceinline__ DF warp_transpose_reduce16_df(DF (&v)[16], int lane) {
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int o = 16 >> st, h = 8 >> st;
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const DF send = up ? v[i] : v[i + h];
+      const DF keep = up ? v[i + h] : v[i];
+      const DF got{__shfl_xor_sync(0xffffffffu, send.hi, o), __shfl_xor_sync(0xffffffffu, send.lo, o)};
+      v[i] = df_add(keep, got);
+    }
+  }
+  const DF got{__shfl_xor_sync(0xffffffffu, v[0].hi, 1), __shfl_xor_sync(0xffffffffu, v[0].lo, 1)};
+  return df_add(v[0], got);
+}
+
 static __device__ __forceinline__ int transpose_slot(int lane) {
   return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
 }
@@ -642,7 +683,10 @@ static __device__ __noinline__ void scalar_phase(const PassArgs& A, const DPass&
     if (mass > 0) nps *= 1.0 / sqrt(mass);
     else W->status = SV_ERR_NUMERIC;
   }
-  if (A.work) A.work[3] += mc - W->m;  // draws executed (one thread of one CTA per pass)
+  if (A.work && mc > W->m) {  // draws executed, and their amplitude updates (2^n each)
+    atomicAdd(A.work + 3, (unsigned long long)(mc - W->m));
+    atomicAdd(A.work + 5, (unsigned long long)(mc - W->m) << A.n);
+  }
   W->creg = creg;
   W->m = mc;
   W->pm = npm;
@@ -826,10 +870,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     act_any |= int(on);
   }
   const bool any_gate = __syncthreads_or(act_any) != 0;
-  if (!CTA && A.work && blockIdx.x == 0 && tid == 0 && any_gate) {  // gate records this run executes
+  if (A.work && (CTA || blockIdx.x == 0) && tid == 0 && any_gate) {  // gate records this run executes
     unsigned long long k = 0;
     for (int g = 0; g < int(sp.ng); ++g) k += (sgk[g] & SGK_ON) ? 1ull : 0ull;
     atomicAdd(A.work + 2, k);
+    atomicAdd(A.work + 5, k << A.n);
   }
   int need = 0;
   if (sp.gk) {
@@ -1168,27 +1213,41 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
 
         // ---- measurement-group table (a zeroed tile adds nothing)
         if (needed && act) {
-          Acc acc[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
           uint32_t off[16];
           reg_offsets(sp.red_R, off);
-          for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
-            const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+          double r;
+          if constexpr (sizeof(T) == 4) {  // complex64: double-float partial sums
+            DF acc[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const V x = tb[b ^ off[j]];
-              acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
+            for (int j = 0; j < 16; ++j) acc[j] = DF{0.f, 0.f};
+            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+              const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+#pragma unroll
+              for (int j = 0; j < 16; ++j) acc[j] = df_add(acc[j], df_abs2(tb[b ^ off[j]]));
             }
+            const DF d = warp_transpose_reduce16_df(acc, lane);
+            r = double(d.hi) + double(d.lo);
+          } else {  // complex128: FP64 throughout
+            Acc acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = Acc(0);
+            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+              const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const V x = tb[b ^ off[j]];
+                acc[j] = fma(Acc(x.x), Acc(x.x), Acc(x.y) * Acc(x.y)) + acc[j];
+              }
+            }
+            r = double(warp_transpose_reduce16(acc, lane));
           }
-          const Acc r = warp_transpose_reduce16(acc, lane);
           if (sp.kin == sp.gk) {
             // every measured qubit is a tile qubit, so a lane's table slot is the
             // same in every tile: lanes accumulate across tiles in FP64 (tile
             // order) and the warps are combined once, after the tile loop
-            if ((lane & 1) == 0) tacc += double(r);
+            if ((lane & 1) == 0) tacc += r;
           } else {
-            if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = double(r);
+            if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = r;
             __syncthreads();
             if (tid < 16) {
               double s2 = 0;
@@ -1250,10 +1309,10 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       bcur = spread_add(bcur, sstep, umask);
     }
     if (pipe) cp_async_wait<0>();
-    if (!CTA && A.work && tid == 0) {
+    if (A.work && tid == 0) {
       atomicAdd(A.work + 0, n_rd * (unsigned long long)TILE_BYTES);
       atomicAdd(A.work + 1, n_wr * (unsigned long long)TILE_BYTES);
-      if (blockIdx.x == 0) atomicAdd(A.work + 4, 1ull);
+      if (CTA || blockIdx.x == 0) atomicAdd(A.work + 4, 1ull);
     }
     if (needed && sp.kin == sp.gk) {  // the lanes' table slots, combined over warps in a fixed order
       if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = tacc;

@@ -231,6 +231,7 @@ struct Builder {
   const std::vector<Item>& items;
   int B;  // log2 amplitudes per 16-byte granule (1: complex64, 0: complex128)
   int max_pass_gates;
+  int tile_select = 1;  // Tuning::tile_select
   int reg_bits = REG_BITS;  // gate register bits per stage (ADJ_REG_BITS for backward plans)
   bool adjoint = false;     // backward plan: derivative items, then U^dagger, per gate
 
@@ -746,27 +747,101 @@ struct Builder {
       emit_pass({}, tq, &seg, false);
       return;
     }
-    while (!rem.empty()) {
-      uint64_t T = low, blocked = 0;
-      std::vector<int> chosen, left;
+    const size_t cap = max_pass_gates > 0 ? size_t(max_pass_gates) : size_t(MAX_PASS_GATES);
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    // The gates (in order) a tile of qubits T runs: a gate runs when its qubits
+    // are tile qubits and no earlier gate on one of them was left out; the
+    // pass's record, matrix and derivative capacities bound it.  grow: first
+    // fit, T takes the qubits of every gate that still fits in m.
+    auto take = [&](const std::vector<int>& from, uint64_t& T, bool grow, std::vector<int>* chosen,
+                    std::vector<int>* left) -> size_t {
+      uint64_t blocked = 0;
       uint32_t mat = 0, dots = 0, recs = 0;
-      const size_t cap = max_pass_gates > 0 ? size_t(max_pass_gates) : size_t(MAX_PASS_GATES);
-      for (int idx : rem) {
+      size_t k = 0;
+      for (int idx : from) {
         const Item& it = items[idx];
         const uint64_t qm = it.qmask();
         const uint32_t ml = uint32_t(mat_len(it));
         const uint32_t nd = uint32_t(n_dots(it));
-        if ((qm & blocked) || popc(T | qm) > m || recs + 1 + nd > cap || mat + ml > MAX_PASS_MAT ||
-            dots + nd > MAX_PASS_DOTS) {
+        const bool fits = grow ? popc(T | qm) <= m : (qm & ~T) == 0;
+        if ((qm & blocked) || !fits || recs + 1 + nd > cap || mat + ml > MAX_PASS_MAT || dots + nd > MAX_PASS_DOTS) {
           blocked |= qm;
-          left.push_back(idx);
+          if (left) left->push_back(idx);
           continue;
         }
-        T |= qm;
+        if (grow) T |= qm;
         mat += ml;
         dots += nd;
         recs += 1 + nd;
-        chosen.push_back(idx);
+        ++k;
+        if (chosen) chosen->push_back(idx);
+      }
+      return k;
+    };
+    while (!rem.empty()) {
+      uint64_t T = low;
+      if (tile_select && popc(all) > m) {
+        // gathered qubits chosen one at a time for the gates they let this
+        // pass run (a pair when no single qubit adds any; else the qubits of
+        // the first gate that still fits), ties to the lowest qubit
+        size_t have = take(rem, T, false, nullptr, nullptr);
+        while (popc(T) < m) {
+          int bq = -1;
+          size_t bv = 0;
+          for (int q = 0; q < n; ++q) {
+            if ((T >> q) & 1) continue;
+            uint64_t T2 = T | (1ull << q);
+            const size_t v = take(rem, T2, false, nullptr, nullptr);
+            if (v > bv) {
+              bv = v;
+              bq = q;
+            }
+          }
+          if (bq >= 0 && bv > have) {
+            T |= 1ull << bq;
+            have = bv;
+            continue;
+          }
+          uint64_t bp = 0;
+          if (popc(T) + 2 <= m)
+            for (int a = 0; a < n; ++a) {
+              if ((T >> a) & 1) continue;
+              for (int b2 = a + 1; b2 < n; ++b2) {
+                if ((T >> b2) & 1) continue;
+                uint64_t T2 = T | (1ull << a) | (1ull << b2);
+                const size_t v = take(rem, T2, false, nullptr, nullptr);
+                if (v > bv) {
+                  bv = v;
+                  bp = (1ull << a) | (1ull << b2);
+                }
+              }
+            }
+          if (bp && bv > have) {
+            T |= bp;
+            have = bv;
+            continue;
+          }
+          // nothing more runs with one or two more qubits: the qubits of the
+          // first gate (in order) that fits, if any; else the tile is done
+          bool grew = false;
+          for (int idx : rem) {
+            const uint64_t qm = items[idx].qmask();
+            if ((qm & ~T) && popc(T | qm) <= m) {
+              T |= qm;
+              grew = true;
+              break;
+            }
+          }
+          if (!grew) break;
+          have = take(rem, T, false, nullptr, nullptr);
+        }
+      }
+      std::vector<int> chosen, left;
+      take(rem, T, !tile_select || popc(all) <= m, &chosen, &left);
+      if (chosen.empty()) {  // cannot happen (the first gate always fits an empty tile); first fit
+        left.clear();
+        T = low;
+        take(rem, T, true, &chosen, &left);
       }
       rem.swap(left);
       const bool last = rem.empty();
@@ -961,6 +1036,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   }
 
   Builder b(P, U.items, dtype == SV_C64 ? 1 : 0, tune.max_pass_gates);
+  b.tile_select = tune.tile_select;
   for (const Segment& s : segs) {
     if (s.gates.empty() && !s.has_group) continue;
     b.emit_segment(s);

@@ -15,6 +15,7 @@ struct Tuning {
   int low_bits = -1;       // L: contiguous low qubits of every tile (-1: per dtype)
   int max_pass_gates = 0;  // 0: up to MAX_PASS_GATES
   int min_qubits = 10;     // states are padded to at least this many qubits
+  int tile_select = 1;     // 1: each tile's gathered qubits chosen for the gates they unlock; 0: first fit
 };
 
 struct Plan {

@@ -392,6 +392,12 @@ sv_status sv_set_tuning(sv_state* h, int tile_bits, int low_bits, int max_pass_g
   return SV_OK;
 }
 
+sv_status sv_set_tile_select(sv_state* h, int closure) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  h->tune.tile_select = closure ? 1 : 0;
+  return SV_OK;
+}
+
 sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out) {
   if (!h || !out) return fail(SV_ERR_ARG, "null argument");
   sv_program* cached = nullptr;
@@ -741,6 +747,8 @@ struct sv_batch {
   std::vector<uint32_t> prog_draws;  // draw items of each program (a bound on the draws a trajectory executes)
   std::vector<svk::BatchItem> items_host;  // staging of the last quick item upload
   int tune_low = 0, tune_gates = 0;           // planner tuning of programs added from now on (0: default)
+  DevBuf<unsigned long long> work;            // device work counters while profiling (sv_batch_profile)
+  bool profiling = false;
   DevBuf<DTrace> tslots;
   DevBuf<svk::BrDraw> tout;
   DevBuf<uint64_t> mout;
@@ -917,6 +925,7 @@ sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   a.seed = seed;
   a.creg_out = b->cregs.p;
   a.status_out = b->status.p;
+  a.work = b->profiling ? b->work.p : nullptr;
   uint64_t key = fnv1a(&a, sizeof(a));
   key = fnv1a(&b->grid, sizeof(b->grid), key);
   if (!b->gexec || key != b->gkey) {
@@ -944,6 +953,32 @@ sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   SV_CUDA(cudaGraphLaunch(b->gexec, b->own));
   SV_CUDA(cudaEventRecord(b->ev_out, b->own));
   SV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return SV_OK;
+}
+
+sv_status sv_batch_profile(sv_batch* b, int enable) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  if (enable) {
+    SV_CUDA(b->work.reserve(SV_WORK_COUNTERS));
+    SV_CUDA(cudaMemsetAsync(b->work.p, 0, sizeof(unsigned long long) * SV_WORK_COUNTERS, b->own));
+  }
+  b->profiling = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_batch_work(sv_batch* b, sv_work_counts* out) {
+  if (!b || !out) return fail(SV_ERR_ARG, "null argument");
+  *out = sv_work_counts{};
+  if (!b->work.p) return SV_OK;
+  unsigned long long w[SV_WORK_COUNTERS];
+  SV_CUDA(cudaMemcpyAsync(w, b->work.p, sizeof(w), cudaMemcpyDeviceToHost, b->own));
+  SV_CUDA(cudaStreamSynchronize(b->own));
+  out->bytes_read = w[0];
+  out->bytes_written = w[1];
+  out->gates = w[2];
+  out->draws = w[3];
+  out->passes = w[4];
+  out->updates = w[5];
   return SV_OK;
 }
 
@@ -1246,6 +1281,18 @@ sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_
   return SV_OK;
 }
 
+sv_status sv_grad_info(const sv_grad* g, sv_grad_stats* out) {
+  if (!g || !out) return fail(SV_ERR_ARG, "null argument");
+  out->forward_passes = g->fwd.plan.passes.size();
+  out->backward_passes = g->bwd.plan.passes.size();
+  out->gates = g->fwd.plan.stats.gates;
+  out->term_groups = g->ngroups;
+  out->terms = g->nterms;
+  out->state_qubits = uint32_t(g->fwd.plan.n_int);
+  out->resident_sets = uint32_t(g->grid);
+  return SV_OK;
+}
+
 sv_status sv_grad_destroy(sv_grad* g) {
   if (!g) return SV_OK;
   cudaStreamSynchronize(g->stream);
@@ -1326,6 +1373,7 @@ sv_status sv_profile_work(sv_state* h, sv_work_counts* out) {
   out->gates = w[2];
   out->draws = w[3];
   out->passes = w[4];
+  out->updates = w[5];
   return SV_OK;
 }
 

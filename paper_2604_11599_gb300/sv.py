@@ -46,7 +46,13 @@ class ProgramStats(C.Structure):
 
 class WorkCounts(C.Structure):
     _fields_ = [("bytes_read", C.c_uint64), ("bytes_written", C.c_uint64), ("gates", C.c_uint64),
-                ("draws", C.c_uint64), ("passes", C.c_uint64)]
+                ("draws", C.c_uint64), ("passes", C.c_uint64), ("updates", C.c_uint64)]
+
+
+class GradStats(C.Structure):
+    _fields_ = [("forward_passes", C.c_uint64), ("backward_passes", C.c_uint64), ("gates", C.c_uint64),
+                ("term_groups", C.c_uint32), ("terms", C.c_uint32), ("state_qubits", C.c_uint32),
+                ("resident_sets", C.c_uint32)]
 
 
 class BranchStats(C.Structure):
@@ -104,6 +110,10 @@ def lib():
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
         "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
         "sv_selftest_wait": ([vp, C.c_uint32], st),
+        "sv_set_tile_select": ([vp, i32], st),
+        "sv_grad_info": ([vp, C.POINTER(GradStats)], st),
+        "sv_batch_profile": ([vp, i32], st),
+        "sv_batch_work": ([vp, C.POINTER(WorkCounts)], st),
         "sv_batch_create": ([i32, vp, C.POINTER(vp)], st),
         "sv_batch_add_program": ([vp, i32, vp, sz, vp, sz, vp, sz, C.POINTER(C.c_uint32)], st),
         "sv_batch_set_items": ([vp, vp, vp, vp, sz], st),
@@ -246,6 +256,10 @@ class State:
 
     def set_cache(self, enable: bool) -> None:
         _check(lib().sv_set_cache(self._h, 1 if enable else 0))
+
+    def set_tile_select(self, closure: bool = True) -> None:
+        """Tile qubits chosen for the gates they unlock (True) or by first fit."""
+        _check(lib().sv_set_tile_select(self._h, 1 if closure else 0))
 
     def set_tuning(self, tile_bits: int = 0, low_bits: int = 0, max_pass_gates: int = 0) -> None:
         _check(lib().sv_set_tuning(self._h, tile_bits, low_bits, max_pass_gates))
@@ -439,6 +453,15 @@ class Batch:
         self.n_items = 0
         return cregs, st.as_dict()
 
+    def profile(self, enable: bool = True) -> None:
+        """Device work counters of the following launches (zeroed on enable)."""
+        _check(lib().sv_batch_profile(self._h, 1 if enable else 0))
+
+    def work(self) -> dict:
+        w = WorkCounts()
+        _check(lib().sv_batch_work(self._h, C.byref(w)))
+        return {k: int(getattr(w, k)) for k, _ in WorkCounts._fields_}
+
     def close(self):
         if getattr(self, "_h", None):
             lib().sv_batch_destroy(self._h)
@@ -525,6 +548,12 @@ class Grad:
         grad = torch.empty(P, n_params, dtype=torch.float64, device=params.device)
         _check(lib().sv_grad_run(self._h, params.data_ptr(), P, n_params, val.data_ptr(), grad.data_ptr()))
         return val, grad
+
+    def info(self) -> dict:
+        """Passes, gates, term groups and resident sets of one parameter set's work."""
+        g = GradStats()
+        _check(lib().sv_grad_info(self._h, C.byref(g)))
+        return {k: int(getattr(g, k)) for k, _ in GradStats._fields_}
 
     def close(self):
         if getattr(self, "_h", None):

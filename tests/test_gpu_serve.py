@@ -36,3 +36,29 @@ def test_alone_vs_mix_and_plain_path():
     for q in reqs[:24]:
         assert np.array_equal(mix2[q.rid].cregs, mix[q.rid].cregs), q.rid
     srv2.close()
+
+
+def test_alone_vs_mix_64_requests_with_large_states():
+    """64 seeded requests of 10-27 qubits (eight of 25 or more, on resident
+    states), served together with continuous batching and then each alone:
+    every record is the same (the draws of shot s of request r are keyed by
+    (seed, r, s, draw index), and the engines are deterministic)."""
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import serve
+
+    stream = W.serving_stream(seed=20, gen_seed=120, rate=200.0, duration=1.0, n_lo=10, n_hi=27, d_lo=10,
+                              d_hi=30, max_shots=128, limit=64)
+    reqs = serve.requests_from_stream(stream)
+    assert len(reqs) == 64 and sum(r.n >= 25 for r in reqs) >= 5
+    be = serve.GpuBackend("c64", seed=9)
+    srv = serve.Server(be, batch_max_n=18, large_workers=4)
+    mix, stats = srv.serve(reqs)
+    assert stats["requests"] == 64
+    paths = {r.rid: r.path for r in mix}
+    assert "large" in paths.values() and "batch" in paths.values()
+    for q in reqs:
+        alone, _ = srv.serve([serve.Req(q.rid, 0.0, q.n, q.ops, q.shots)])
+        assert np.array_equal(alone[0].cregs, mix[q.rid].cregs), (q.rid, q.n)
+    srv.close()
