@@ -88,14 +88,19 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
         for (uint32_t g = 0; g < J.ngroups; ++g) {
           const uint64_t j = i ^ J.hx[g];
           const V pj = phi[j];
-          double wr = 0, wi = 0;
+          // the group's coefficient at j, sum_t c_t i^k_t (-1)^{|j & z_t|}, in the
+          // state's precision (complex64: FP32, whose error stays far below the
+          // state's own; FP64 per term per amplitude would bound this step at
+          // GB300's FP64 rate)
+          Acc wr = 0, wi = 0;
           for (uint32_t t = J.hg0[g]; t < J.hg0[g + 1]; ++t) {
-            const double sgn = (__popcll(j & hz[t]) & 1) ? -1.0 : 1.0;
-            wr += sgn * hc[t].x;
-            wi += sgn * hc[t].y;
+            const bool neg = __popcll(j & hz[t]) & 1;
+            const Acc cr = Acc(hc[t].x), ci = Acc(hc[t].y);
+            wr += neg ? -cr : cr;
+            wi += neg ? -ci : ci;
           }
-          ar += Acc(wr) * pj.x - Acc(wi) * pj.y;
-          ai += Acc(wr) * pj.y + Acc(wi) * pj.x;
+          ar += wr * pj.x - wi * pj.y;
+          ai += wr * pj.y + wi * pj.x;
         }
         lam[i] = mkc(ar, ai);
         const V pi_ = phi[i];

@@ -34,6 +34,24 @@ __device__ __forceinline__ double abs2d(typename CxT<T>::V v) {
   return fma(double(v.x), double(v.x), double(v.y) * double(v.y));
 }
 
+// double-float helpers (an unevaluated sum hi + lo of FP32 values; Knuth's
+// error-free sum, the FMA error-free product)
+struct DFv {
+  float hi, lo;
+};
+__device__ __forceinline__ DFv dfv_add(DFv a, DFv b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, lo);
+  return DFv{h, __fsub_rn(lo, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DFv dfv_abs2(float x, float y) {
+  const float p = __fmul_rn(x, x), q = __fmul_rn(y, y);
+  return dfv_add(DFv{p, __fmaf_rn(x, x, -p)}, DFv{q, __fmaf_rn(y, y, -q)});
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -58,13 +76,20 @@ __global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_bloc
   const int wruns = runs_in_block - warp * 32 < 32 ? runs_in_block - warp * 32 : 32;  // runs of this warp
   double mine = 0.0;
   if constexpr (sizeof(T) == 4) {
+    // complex64: |amp|^2 and the run sums as double-float values (error-free
+    // products and sums in FP32, about 44 bits), converted to FP64 once per
+    // run -- FP64 arithmetic per amplitude would bound this read at GB300's
+    // FP64 rate
     const float4* s = reinterpret_cast<const float4*>(a.state) + (a0 >> 1);
+#pragma unroll 4
     for (int k = 0; 2 * k < wruns; ++k) {
       const float4 q = __ldcs(s + 32 * k + lane);
-      double v = abs2d<T>(make_float2(q.x, q.y)) + abs2d<T>(make_float2(q.z, q.w));
+      DFv v = dfv_add(dfv_abs2(q.x, q.y), dfv_abs2(q.z, q.w));
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      const double lo = __shfl_sync(0xffffffffu, v, 0), hi = __shfl_sync(0xffffffffu, v, 16);
+      for (int o = 8; o > 0; o >>= 1)
+        v = dfv_add(v, DFv{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+      const double w = double(v.hi) + double(v.lo);
+      const double lo = __shfl_sync(0xffffffffu, w, 0), hi = __shfl_sync(0xffffffffu, w, 16);
       if (lane == 2 * k) mine = lo;
       if (lane == 2 * k + 1) mine = hi;
     }
@@ -196,36 +221,45 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 // ---------------------------------------------------------------------- expectation values
 constexpr int EXP_TERMS = 32;  // terms per launch (launches of one X group share the read pattern)
 constexpr int EXP_CHUNK = 16;  // pairs summed in the state precision before an FP64 add
-constexpr int EXP_UNROLL = 4;  // loads in flight per thread
 
-// NT: the smallest power of two >= the launch's term count, so a group of one
-// or two terms carries one or two accumulators (FP32 chunk sums, then FP64),
-// not thirty-two; with NT <= 8 the Z masks and phases sit in registers.
+// One X group (x) per launch, up to 32 of its terms.  The pair index r runs
+// over the 2^n / 2 pairs (i, i ^ x) with bit h = top bit of x clear in i (for
+// x = 0 over the 2^n amplitudes, f = |psi_i|^2); f(r) = conj(psi_i) psi_{i^x}.
+// A half-warp holds 16 consecutive r; four shuffle butterflies give lane l the
+// Walsh-Hadamard coefficient F(l) = sum_l' (-1)^{|l & l'|} f(l'), so a term
+// whose Z mask restricted to the half-warp's index bits is zl takes F(zl) from
+// one lane, with the sign (-1)^{|i0 & zh|} of the rest (i0: the half-warp's
+// first index).  Per term that is one predicated add per 32 pairs instead of
+// a parity and an add per pair.  NT: the smallest power of two >= the term
+// count (that many FP32 chunk sums and FP64 accumulators per lane).
 template <typename T, int NT>
 __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
-  __shared__ uint64_t zs[NT];
+  __shared__ uint64_t zhs[NT];
+  __shared__ uint32_t zls[NT];
   __shared__ int ks[NT];
   __shared__ double red[8][NT];
   __shared__ int s_last;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = a.nterms;
+  const uint64_t x = a.x_mask;
+  const int h = x ? 63 - __clzll((long long)x) : 64;
+  // index bits of i behind the four low bits of r (bit h skipped)
+  const uint64_t lmask = h < 4 ? (0x1Full & ~(1ull << h)) : 0xFull;
   if (tid < NT) {
-    zs[tid] = tid < nt ? a.z_masks[tid] : 0ull;
+    const uint64_t z = tid < nt ? a.z_masks[tid] : 0ull;
+    uint32_t zl = 0, k = 0;
+    for (int b = 0; b < 5; ++b)
+      if ((lmask >> b) & 1) {
+        zl |= uint32_t((z >> b) & 1) << k;
+        ++k;
+      }
+    zls[tid] = tid < nt ? zl : 0xFFu;  // unused slots match no lane
+    zhs[tid] = z & ~lmask;
     ks[tid] = tid < nt ? a.phase[tid] : 0;
   }
   __syncthreads();
-  constexpr bool REG = NT <= 8;
-  uint64_t zr[REG ? NT : 1];
-  int kr[REG ? NT : 1];
-  if constexpr (REG) {
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      zr[t] = zs[t];
-      kr[t] = ks[t];
-    }
-  }
   double acc[NT];
   T part[NT];
 #pragma unroll
@@ -234,71 +268,50 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
     part[t] = 0;
   }
   const uint64_t N = 1ull << a.n;
-  const uint64_t x = a.x_mask;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  // EXP_UNROLL independent loads in flight per thread (grid-stride order kept)
-  constexpr int U = NT >= 16 ? 1 : EXP_UNROLL;
+  const uint64_t npairs = x ? (N >> 1) : N;
+  const uint64_t lowm = h < 64 ? ((1ull << h) - 1) : ~0ull;
+  const uint32_t l16 = uint32_t(lane & 15);
+  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
   int cnt = 0;
-  auto flush = [&]() {
+  // whole warps iterate together (npairs is a multiple of 32: states have >= 2^10 amplitudes)
+  for (uint64_t wb = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb << 5) < npairs; wb += warps) {
+    const uint64_t r = (wb << 5) | uint64_t(lane);
+    const uint64_t i = x ? (((r >> h) << (h + 1)) | (r & lowm)) : r;
+    const uint64_t r0 = r & ~15ull;  // the half-warp's first pair
+    const uint64_t i0 = x ? (((r0 >> h) << (h + 1)) | (r0 & lowm)) : r0;
+    const V pi_ = st[i];
+    T fr, fi;
+    if (x) {
+      const V pj = st[i ^ x];
+      fr = fma(pi_.x, pj.x, pi_.y * pj.y);   // Re conj(psi_i) psi_j
+      fi = fma(pi_.x, pj.y, -pi_.y * pj.x);  // Im
+    } else {
+      fr = fma(pi_.x, pi_.x, pi_.y * pi_.y);
+      fi = T(0);
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {  // Walsh-Hadamard over the half-warp
+      const T qr = __shfl_xor_sync(0xffffffffu, fr, o), qi = __shfl_xor_sync(0xffffffffu, fi, o);
+      const bool up = l16 & uint32_t(o);
+      fr = up ? qr - fr : fr + qr;
+      fi = up ? qi - fi : fi + qi;
+    }
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      acc[t] += double(part[t]);
-      part[t] = 0;
+      if (zls[t] == l16) {
+        const int k = ks[t];
+        const T c = (k & 1) ? fi : fr;
+        const bool neg = ((__popcll(i0 & zhs[t]) & 1) != 0) != (k >= 2);
+        part[t] += neg ? -c : c;
+      }
     }
-    cnt = 0;
-  };
-  if (x == 0) {
-    for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + tid; i0 < N; i0 += U * stride) {
-      V v[U];
+    if (++cnt == EXP_CHUNK) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t i = i0 + uint64_t(u) * stride;
-        v[u] = i < N ? st[i] : mkc(T(0), T(0));
+      for (int t = 0; t < NT; ++t) {
+        acc[t] += double(part[t]);
+        part[t] = 0;
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t i = i0 + uint64_t(u) * stride;
-        const T p = fma(v[u].x, v[u].x, v[u].y * v[u].y);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
-          part[t] += (__popcll(i & z) & 1) ? -p : p;
-        }
-      }
-      cnt += U;
-      if (cnt >= EXP_CHUNK) flush();
-    }
-  } else {
-    const int h = 63 - __clzll((long long)x);
-    const uint64_t half = N >> 1;
-    const uint64_t lowm = (1ull << h) - 1;
-    for (uint64_t r0 = uint64_t(blockIdx.x) * blockDim.x + tid; r0 < half; r0 += U * stride) {
-      V pi_[U], pj[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t r = r0 + uint64_t(u) * stride;
-        const uint64_t i = ((r >> h) << (h + 1)) | (r & lowm);  // bit h of i is 0
-        const bool ok = r < half;
-        pi_[u] = ok ? st[i] : mkc(T(0), T(0));
-        pj[u] = ok ? st[i ^ x] : mkc(T(0), T(0));
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t r = r0 + uint64_t(u) * stride;
-        const uint64_t i = ((r >> h) << (h + 1)) | (r & lowm);
-        // w = conj(psi_i) psi_j
-        const T wr = fma(pi_[u].x, pj[u].x, pi_[u].y * pj[u].y), wi = fma(pi_[u].x, pj[u].y, -pi_[u].y * pj[u].x);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          const uint64_t z = REG ? zr[REG ? t : 0] : zs[t];
-          const int k = REG ? kr[REG ? t : 0] : ks[t];
-          const T c = (k & 1) ? wi : wr;
-          const bool neg = ((__popcll(i & z) & 1) != 0) != (k >= 2);
-          part[t] += neg ? -c : c;
-        }
-      }
-      cnt += U;
-      if (cnt >= EXP_CHUNK) flush();
+      cnt = 0;
     }
   }
   // a pair contributes twice its value (the pair (i^x, i) is not visited)
@@ -306,7 +319,6 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
 #pragma unroll
   for (int t = 0; t < NT; ++t) acc[t] = pw * (acc[t] + double(part[t]));
   // block reduction (fixed order)
-  const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     const double v = warp_sum_d(acc[t]);
@@ -314,9 +326,9 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   }
   __syncthreads();
   if (tid < NT) {
-    double s = 0;
-    for (int w = 0; w < 8; ++w) s += red[w][tid];
-    a.partials[blockIdx.x * EXP_TERMS + tid] = s;
+    double sum = 0;
+    for (int w = 0; w < 8; ++w) sum += red[w][tid];
+    a.partials[blockIdx.x * EXP_TERMS + tid] = sum;
   }
   __threadfence();
   __syncthreads();
@@ -325,9 +337,9 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   if (!s_last) return;
   __threadfence();
   if (tid < nt) {
-    double s = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(a.partials + b * EXP_TERMS + tid);
-    a.out[tid] = s;
+    double sum = 0;
+    for (unsigned b2 = 0; b2 < gridDim.x; ++b2) sum += __ldcg(a.partials + b2 * EXP_TERMS + tid);
+    a.out[tid] = sum;
   }
   if (tid == 0) *a.ticket = 0;
 }
