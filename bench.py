@@ -61,6 +61,13 @@ def parse():
                     help="layered: the plain dynamic-circuit workload; dense4: layers of dense 4-qubit unitaries")
     ap.add_argument("--no-dense-tc", action="store_true", help="dense 4-qubit gates on the FP32 pipes")
     ap.add_argument("--first-fit", action="store_true", help="plan tiles by first fit instead of by the gates they unlock")
+    ap.add_argument("--jit-blocks", type=int, default=0, help="CTAs per SM of the specialised kernels (0: default)")
+    ap.add_argument("--form", default=None, choices=["batching", "adjoint", "sample_expval"],
+                    help="run only this auxiliary measurement (for profiling) and print its JSON")
+    ap.add_argument("--items", type=int, default=65536, help="--form batching: trajectories")
+    ap.add_argument("--sets", type=int, default=1024, help="--form adjoint: parameter sets")
+    ap.add_argument("--tile-bits", type=int, default=0, help="qubits per shared-memory tile (0: default 12)")
+    ap.add_argument("--low-bits", type=int, default=0, help="contiguous low qubits per tile (0: default 4)")
     return ap.parse_args()
 
 
@@ -603,6 +610,62 @@ def serving_form(sv, torch, W, serve, np, duration=0.5):
     }
 
 
+def single_form(args):
+    """One auxiliary measurement on its own (the commands the kernel profiles use)."""
+    import numpy as np
+    import torch
+
+    from paper_2604_11599_gb300 import build
+
+    build.build()
+    from paper_2604_11599_gb300 import sv, workloads as W
+
+    out = {"form": args.form}
+    if args.form == "batching":
+        wl = W.batching(seed=6, n_traj=args.items)
+        with sv.Batch("c64") as b:
+            pid = {n: b.add_program(c.ops, n + 1) for n, c in wl.circuits.items()}
+            ids = np.array([pid[int(n)] for n in wl.traj_n])
+            b.set_items(ids, np.arange(len(ids)), np.zeros(len(ids)))
+            for _ in range(2):
+                t0 = time.perf_counter()
+                b.launch(0)
+                b.results()
+                dt = time.perf_counter() - t0
+        out.update({"trajectories": args.items, "seconds": dt, "trajectories_per_s": args.items / dt})
+    elif args.form == "adjoint":
+        c = W.hea(20, 8)
+        terms = W.heisenberg_fields(9, 20, 200)
+        h = sv.Grad(c.ops, 20, terms, args.dtype)
+        prm = torch.tensor(W.hea_params(8, args.sets, 320), device="cuda")
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.run(prm)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        out.update({"sets": args.sets, "seconds": dt, "gradient_sets_per_s": args.sets / dt, "work_per_set": h.info()})
+        h.close()
+    else:
+        n = 28
+        c = W.layered(3, n, layers=2)
+        terms = W.heisenberg_fields(9, n, 10 * n)
+        with sv.State(n, "c64") as st:
+            st.run(c.ops)
+            dev = torch.empty(1 << 20, dtype=torch.int64, device="cuda")
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st.sample_state_device(dev, seed=5)
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+                t0 = time.perf_counter()
+                st.expval(terms)
+                te = time.perf_counter() - t0
+        out.update({"state": "n=28 complex64", "sample_1M_seconds": ts, "expval_280_terms_seconds": te})
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, rank, world):
     """--impl reference: the oracle on the host cores, same metric and config."""
     if rank != 0:
@@ -634,6 +697,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.form:
+        return single_form(args)
 
     import torch
 
@@ -658,6 +723,9 @@ def main():
     st.set_jit(not args.no_jit)
     st.set_dense_tc(not args.no_dense_tc)
     st.set_tile_select(not args.first_fit)
+    st.set_jit_blocks(args.jit_blocks)
+    if args.tile_bits or args.low_bits:
+        st.set_tuning(args.tile_bits, args.low_bits, 0)
     if len(c.pool):
         st.set_dense_pool(c.pool)
     prog = st.prepare(c.ops)

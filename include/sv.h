@@ -177,6 +177,14 @@ sv_status sv_set_dense_pool(sv_state* h, const double* pool, size_t n_complex);
 sv_status sv_set_tile_select(sv_state* h, int closure);
 
 /*
+ * CTAs per SM the specialised pass kernels are compiled for (their register
+ * budget follows: 65,536 / (256 x blocks) per thread) and launched with; 0
+ * (default) keeps 2 for complex64 and 1 for complex128.  Programs planned
+ * from now on use it.  SV_ERR_ARG for a null handle or a value outside 0..4.
+ */
+sv_status sv_set_jit_blocks(sv_state* h, int blocks_per_sm);
+
+/*
  * Lower an op list for this state's n and dtype.  The caller's ops are read
  * during the call only.  SV_ERR_ARG for a malformed list (qubit >= n,
  * duplicate qubits, cbit >= 64, lengths out of range, nesting > 64),

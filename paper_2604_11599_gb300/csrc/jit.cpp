@@ -229,7 +229,8 @@ std::string generate_chunk(const svp::Plan& P, size_t p0, size_t p1) {
   for (int v = 0; v < 4; ++v) {
     const bool vt = v & 1, vp = v & 2;
     if (!chunk_has_variant(P, p0, p1, vt, vp)) continue;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1) << ") "
+    const int minb = P.jit_min_blocks > 0 ? P.jit_min_blocks : (c64 ? 2 : 1);
+    o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << minb << ") "
       << variant_name(vt, vp) << "(const svk::PassArgs A) {\n"
       << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
       << "  __shared__ svk::PassShared<" << T << ", " << (vt ? "true" : "false") << "> sh;\n"

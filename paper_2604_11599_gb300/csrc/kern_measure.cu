@@ -76,23 +76,44 @@ __global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_bloc
   const int wruns = runs_in_block - warp * 32 < 32 ? runs_in_block - warp * 32 : 32;  // runs of this warp
   double mine = 0.0;
   if constexpr (sizeof(T) == 4) {
-    // complex64: |amp|^2 and the run sums as double-float values (error-free
-    // products and sums in FP32, about 44 bits), converted to FP64 once per
-    // run -- FP64 arithmetic per amplitude would bound this read at GB300's
-    // FP64 rate
+    // complex64: each warp stages 512 amplitudes (16 runs) at a time in
+    // shared memory (coalesced 16-byte loads; one pad granule per 8 keeps the
+    // writes and the per-run reads free of bank conflicts), each lane sums
+    // half a run in index order as a double-float value (error-free FP32
+    // products and sums, ~44 bits; FP64 arithmetic per amplitude would bound
+    // this read at GB300's FP64 rate), one shuffle joins the halves
+    __shared__ float4 stage[8][288];
+    float4* sw = stage[warp];
     const float4* s = reinterpret_cast<const float4*>(a.state) + (a0 >> 1);
-#pragma unroll 4
-    for (int k = 0; 2 * k < wruns; ++k) {
-      const float4 q = __ldcs(s + 32 * k + lane);
-      DFv v = dfv_add(dfv_abs2(q.x, q.y), dfv_abs2(q.z, q.w));
+    double got[2] = {0.0, 0.0};
+    for (int it = 0; it < 2 && it * 16 < wruns; ++it) {
+      float4 q[8];
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1)
-        v = dfv_add(v, DFv{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
-      const double w = double(v.hi) + double(v.lo);
-      const double lo = __shfl_sync(0xffffffffu, w, 0), hi = __shfl_sync(0xffffffffu, w, 16);
-      if (lane == 2 * k) mine = lo;
-      if (lane == 2 * k + 1) mine = hi;
+      for (int k = 0; k < 8; ++k) q[k] = __ldcs(s + it * 256 + k * 32 + lane);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int f = k * 32 + lane;
+        sw[f + (f >> 3)] = q[k];
+      }
+      __syncwarp();
+      const int f0 = 8 * lane;  // run lane/2, half lane&1: granules 16 run + 8 half + j
+      DFv v{0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int f = f0 + j;
+        const float4 w = sw[f + (f >> 3)];
+        v = dfv_add(v, dfv_abs2(w.x, w.y));
+        v = dfv_add(v, dfv_abs2(w.z, w.w));
+      }
+      __syncwarp();
+      const DFv o{__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1)};
+      v = (lane & 1) ? dfv_add(o, v) : dfv_add(v, o);  // first half first, in both lanes
+      got[it] = double(v.hi) + double(v.lo);
     }
+    // lane j takes run j of the warp: runs 0..15 from iteration 0 (lane 2j), 16..31 from iteration 1
+    const double r0 = __shfl_sync(0xffffffffu, got[0], (2 * lane) & 31);
+    const double r1 = __shfl_sync(0xffffffffu, got[1], (2 * lane) & 31);
+    mine = lane < 16 ? r0 : r1;
   } else {
     const double2* s = reinterpret_cast<const double2*>(a.state) + a0;
     for (int k = 0; k < wruns; ++k) {
@@ -182,13 +203,20 @@ __global__ void __launch_bounds__(256) k_sample_search(SampleArgs a, uint64_t nb
   uint64_t found = ~0ull;
   for (int r = rl; r >= 0 && found == ~0ull; --r) {
     const uint64_t i0 = (b * uint64_t(runs_in_block) + uint64_t(r)) << RUN_BITS;
-    double c = base + (r > 0 ? rc[r - 1] : 0.0);
+    // the target relative to the run's start; complex64 accumulates the run in
+    // FP32 from there (its relative error, ~1e-7 of one run's mass, only moves
+    // draws that fall within it of an amplitude boundary)
+    const double rel = target - (base + (r > 0 ? rc[r - 1] : 0.0));
+    using Acc = T;
+    const Acc trel = Acc(rel);
+    Acc c = Acc(0);
     uint64_t last_nz = ~0ull;
     for (int j = 0; j < 32; ++j) {
-      const double p = abs2d<T>(st[i0 + j]);
+      const typename CxT<T>::V v = st[i0 + j];
+      const Acc p = fma(v.x, v.x, v.y * v.y);
       c += p;
       if (p > 0) last_nz = i0 + j;
-      if (p > 0 && c > target && r == rl) {
+      if (p > 0 && c > trel && r == rl) {
         found = i0 + j;
         break;
       }
@@ -219,8 +247,9 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------- expectation values
-constexpr int EXP_TERMS = 32;  // terms per launch (launches of one X group share the read pattern)
-constexpr int EXP_CHUNK = 16;  // pairs summed in the state precision before an FP64 add
+constexpr int EXP_TERMS = 16;  // terms per launch (a larger X group takes several launches)
+constexpr int EXP_CHUNK = 16;  // warp blocks summed in the state precision before an FP64 add
+constexpr int EXP_UNROLL = 4;  // warp blocks whose loads are in flight together
 
 // One X group (x) per launch, up to 32 of its terms.  The pair index r runs
 // over the 2^n / 2 pairs (i, i ^ x) with bit h = top bit of x clear in i (for
@@ -233,12 +262,11 @@ constexpr int EXP_CHUNK = 16;  // pairs summed in the state precision before an 
 // a parity and an add per pair.  NT: the smallest power of two >= the term
 // count (that many FP32 chunk sums and FP64 accumulators per lane).
 template <typename T, int NT>
-__global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
+__global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
   __shared__ uint64_t zhs[NT];
-  __shared__ uint32_t zls[NT];
-  __shared__ int ks[NT];
+  __shared__ uint32_t zkw[NT];  // zl | (k << 8) (zl = 0xFF: unused slot)
   __shared__ double red[8][NT];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -255,9 +283,8 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
         zl |= uint32_t((z >> b) & 1) << k;
         ++k;
       }
-    zls[tid] = tid < nt ? zl : 0xFFu;  // unused slots match no lane
+    zkw[tid] = (tid < nt ? zl : 0xFFu) | (uint32_t(tid < nt ? a.phase[tid] : 0) << 8);
     zhs[tid] = z & ~lmask;
-    ks[tid] = tid < nt ? a.phase[tid] : 0;
   }
   __syncthreads();
   double acc[NT];
@@ -272,40 +299,58 @@ __global__ void __launch_bounds__(256) k_expval_group(ExpvalArgs a) {
   const uint64_t lowm = h < 64 ? ((1ull << h) - 1) : ~0ull;
   const uint32_t l16 = uint32_t(lane & 15);
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  constexpr int U = EXP_UNROLL;  // warp blocks of 32 pairs whose loads are in flight together
   int cnt = 0;
   // whole warps iterate together (npairs is a multiple of 32: states have >= 2^10 amplitudes)
-  for (uint64_t wb = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb << 5) < npairs; wb += warps) {
-    const uint64_t r = (wb << 5) | uint64_t(lane);
-    const uint64_t i = x ? (((r >> h) << (h + 1)) | (r & lowm)) : r;
-    const uint64_t r0 = r & ~15ull;  // the half-warp's first pair
-    const uint64_t i0 = x ? (((r0 >> h) << (h + 1)) | (r0 & lowm)) : r0;
-    const V pi_ = st[i];
-    T fr, fi;
-    if (x) {
-      const V pj = st[i ^ x];
-      fr = fma(pi_.x, pj.x, pi_.y * pj.y);   // Re conj(psi_i) psi_j
-      fi = fma(pi_.x, pj.y, -pi_.y * pj.x);  // Im
-    } else {
-      fr = fma(pi_.x, pi_.x, pi_.y * pi_.y);
-      fi = T(0);
+  for (uint64_t wb0 = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb0 << 5) < npairs;
+       wb0 += uint64_t(U) * warps) {
+    V pi_[U], pj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t r = ((wb0 + uint64_t(u) * warps) << 5) | uint64_t(lane);
+      const bool ok = r < npairs;
+      const uint64_t i = x ? (((r >> h) << (h + 1)) | (r & lowm)) : r;
+      pi_[u] = ok ? st[i] : mkc(T(0), T(0));
+      pj[u] = (ok && x) ? st[i ^ x] : pi_[u];
     }
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {  // Walsh-Hadamard over the half-warp
-      const T qr = __shfl_xor_sync(0xffffffffu, fr, o), qi = __shfl_xor_sync(0xffffffffu, fi, o);
-      const bool up = l16 & uint32_t(o);
-      fr = up ? qr - fr : fr + qr;
-      fi = up ? qi - fi : fi + qi;
-    }
+    for (int u = 0; u < U; ++u) {
+      const uint64_t r = ((wb0 + uint64_t(u) * warps) << 5) | uint64_t(lane);
+      const uint64_t r0 = r & ~15ull;  // the half-warp's first pair
+      const uint64_t i0 = x ? (((r0 >> h) << (h + 1)) | (r0 & lowm)) : r0;
+      T fr, fi;
+      if (x) {
+        fr = fma(pi_[u].x, pj[u].x, pi_[u].y * pj[u].y);   // Re conj(psi_i) psi_j
+        fi = fma(pi_[u].x, pj[u].y, -pi_[u].y * pj[u].x);  // Im
+      } else {
+        fr = fma(pi_[u].x, pi_[u].x, pi_[u].y * pi_[u].y);
+        fi = T(0);
+      }
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      if (zls[t] == l16) {
-        const int k = ks[t];
+      for (int o = 1; o < 16; o <<= 1) {  // Walsh-Hadamard over the half-warp
+        const T qr = __shfl_xor_sync(0xffffffffu, fr, o);
+        const bool up = l16 & uint32_t(o);
+        fr = up ? qr - fr : fr + qr;
+        if (x) {
+          const T qi = __shfl_xor_sync(0xffffffffu, fi, o);
+          fi = up ? qi - fi : fi + qi;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        // term data from shared memory every time (kept out of registers)
+        uint32_t w;
+        uint64_t zh;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(uint32_t(__cvta_generic_to_shared(zkw + t))));
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(zh) : "r"(uint32_t(__cvta_generic_to_shared(zhs + t))));
+        const uint32_t k = w >> 8;
         const T c = (k & 1) ? fi : fr;
-        const bool neg = ((__popcll(i0 & zhs[t]) & 1) != 0) != (k >= 2);
-        part[t] += neg ? -c : c;
+        const bool neg = ((__popcll(i0 & zh) & 1) != 0) != (k >= 2);
+        part[t] += ((w & 0xFFu) == l16) ? (neg ? -c : c) : T(0);
       }
     }
-    if (++cnt == EXP_CHUNK) {
+    cnt += U;
+    if (cnt >= EXP_CHUNK) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         acc[t] += double(part[t]);
@@ -351,8 +396,7 @@ static cudaError_t launch_expval_t(const ExpvalArgs& a, int grid, cudaStream_t s
   else if (nt <= 2) k_expval_group<T, 2><<<grid, 256, 0, s>>>(a);
   else if (nt <= 4) k_expval_group<T, 4><<<grid, 256, 0, s>>>(a);
   else if (nt <= 8) k_expval_group<T, 8><<<grid, 256, 0, s>>>(a);
-  else if (nt <= 16) k_expval_group<T, 16><<<grid, 256, 0, s>>>(a);
-  else k_expval_group<T, 32><<<grid, 256, 0, s>>>(a);
+  else k_expval_group<T, 16><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -209,7 +209,7 @@ struct ExpvalArgs {
   uint64_t x_mask;
   const uint64_t* z_masks;  // [nterms]
   const int* phase;         // [nterms] i^phase factor (|x & z| mod 4)
-  int nterms;               // <= 32
+  int nterms;               // <= 16
   double* partials;         // [grid][32]
   double* out;              // [nterms] (written by the last CTA)
   unsigned* ticket;

@@ -959,6 +959,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
     return SV_ERR_ARG;
   }
   P.n = n;
+  P.jit_min_blocks = tune.jit_min_blocks;
   P.n_int = std::max(n, std::max(tune.min_qubits, 10));  // small states are padded with qubits that stay |0>
   P.dtype = dtype;
   int tb = tune.tile_bits > 0 ? tune.tile_bits : 12;

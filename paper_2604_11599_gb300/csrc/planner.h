@@ -16,6 +16,7 @@ struct Tuning {
   int max_pass_gates = 0;  // 0: up to MAX_PASS_GATES
   int min_qubits = 10;     // states are padded to at least this many qubits
   int tile_select = 1;     // 1: each tile's gathered qubits chosen for the gates they unlock; 0: first fit
+  int jit_min_blocks = 0;  // specialised kernels: CTAs per SM they are compiled for (0: 2 complex64, 1 complex128)
 };
 
 struct Plan {
@@ -23,6 +24,7 @@ struct Plan {
   int n_int = 0;    // simulated qubits (>= 4; extra qubits stay |0>)
   int dtype = 0;
   int m = 0, L = 0;
+  int jit_min_blocks = 0;  // Tuning::jit_min_blocks
   std::vector<DPass> passes;
   std::vector<DGate> gates;
   std::vector<DStage> stages;

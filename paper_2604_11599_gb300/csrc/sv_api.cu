@@ -196,7 +196,9 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
   }
   const svj::JitModule* jm = h->use_jit ? p->jit.get() : nullptr;
   if (!P.passes.empty()) {
-    const int grid = pass_grid(h, P.m);
+    int grid = pass_grid(h, P.m);
+    if (jm && P.jit_min_blocks > 0)  // specialised kernels compiled for that many CTAs per SM
+      grid = int(std::min<uint64_t>(1ull << (h->n_int - P.m), uint64_t(h->sms) * uint64_t(P.jit_min_blocks)));
     if (grid < 1) return fail(SV_ERR_CUDA, "pass kernel configuration failed for tile bits " + std::to_string(P.m));
     SV_CUDA(h->partials.reserve(size_t(grid) * 16));
     svk::PassArgs a{};
@@ -389,6 +391,13 @@ sv_status sv_set_tuning(sv_state* h, int tile_bits, int low_bits, int max_pass_g
   h->tune.tile_bits = tile_bits;
   h->tune.low_bits = low_bits ? low_bits : -1;
   h->tune.max_pass_gates = max_pass_gates;
+  return SV_OK;
+}
+
+sv_status sv_set_jit_blocks(sv_state* h, int blocks_per_sm) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (blocks_per_sm < 0 || blocks_per_sm > 4) return fail(SV_ERR_ARG, "blocks_per_sm in 0..4");
+  h->tune.jit_min_blocks = blocks_per_sm;
   return SV_OK;
 }
 
@@ -688,14 +697,14 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
   size_t slot = 0;
   for (uint64_t x : keys) {
     const size_t cnt = groups[x].size();
-    for (size_t c = 0; c < cnt; c += 32) {
+    for (size_t c = 0; c < cnt; c += 16) {  // at most 16 terms per launch
       svk::ExpvalArgs a{};
       a.state = h->state;
       a.n = h->n_int;
       a.x_mask = x;
       a.z_masks = h->exp_z.p + slot + c;
       a.phase = h->exp_k.p + slot + c;
-      a.nterms = int(std::min<size_t>(32, cnt - c));
+      a.nterms = int(std::min<size_t>(16, cnt - c));
       a.partials = h->exp_partials.p;
       a.out = h->exp_out.p + slot + c;
       a.ticket = h->exp_ticket;

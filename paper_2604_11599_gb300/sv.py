@@ -111,6 +111,7 @@ def lib():
         "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
         "sv_selftest_wait": ([vp, C.c_uint32], st),
         "sv_set_tile_select": ([vp, i32], st),
+        "sv_set_jit_blocks": ([vp, i32], st),
         "sv_grad_info": ([vp, C.POINTER(GradStats)], st),
         "sv_batch_profile": ([vp, i32], st),
         "sv_batch_work": ([vp, C.POINTER(WorkCounts)], st),
@@ -256,6 +257,10 @@ class State:
 
     def set_cache(self, enable: bool) -> None:
         _check(lib().sv_set_cache(self._h, 1 if enable else 0))
+
+    def set_jit_blocks(self, blocks_per_sm: int = 0) -> None:
+        """CTAs per SM of the specialised kernels (0: the default for the dtype)."""
+        _check(lib().sv_set_jit_blocks(self._h, int(blocks_per_sm)))
 
     def set_tile_select(self, closure: bool = True) -> None:
         """Tile qubits chosen for the gates they unlock (True) or by first fit."""
