@@ -16,6 +16,15 @@ template <> struct CxT<double> { using V = double2; using V4 = double2; };
 __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
 
+// two complex64 amplitudes in one 16-byte vector (complex128: one amplitude;
+// the pair helpers are used for complex64 only)
+__device__ __forceinline__ float2 pair_lo(float4 q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 pair_hi(float4 q) { return make_float2(q.z, q.w); }
+__device__ __forceinline__ float4 make_pair4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ double2 pair_lo(double2 q) { return q; }
+__device__ __forceinline__ double2 pair_hi(double2 q) { return q; }
+__device__ __forceinline__ double2 make_pair4(double2 a, double2) { return a; }
+
 // m0*x + m1*y (complex)
 template <typename V>
 __device__ __forceinline__ V cmac2(V m0, V x, V m1, V y) {

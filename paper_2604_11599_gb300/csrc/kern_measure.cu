@@ -140,30 +140,39 @@ __global__ void __launch_bounds__(256) k_cdf_runs(SampleArgs a, int runs_in_bloc
 }
 
 // exclusive scan of nb block sums by one CTA (chunk sums per thread, chunk
-// bases in a fixed order).  At chunk boundaries block_prefix[i + 1] may differ
+// bases by a block-wide scan in a fixed order).  At chunk boundaries block_prefix[i + 1] may differ
 // from block_prefix[i] + block_sums[i] by rounding; the shot walk then falls
 // back to the last nonzero amplitude of the block (a draw within an ulp of a
 // boundary).
 __global__ void __launch_bounds__(1024) k_scan_blocks(SampleArgs a, uint64_t nb) {
-  __shared__ double tsum[1024];
-  const int tid = threadIdx.x;
+  __shared__ double wtot[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t per = (nb + 1023) / 1024;
   const uint64_t lo = tid * per, hi = lo + per < nb ? lo + per : nb;
   double s = 0;
+#pragma unroll 8
   for (uint64_t i = lo; i < hi; ++i) s += a.block_sums[i];
-  tsum[tid] = s;
+  // exclusive scan of the 1,024 chunk sums: warp scans, then the warp totals
+  double v = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wtot[warp] = v;
   __syncthreads();
-  if (tid == 0) {
-    double run = 0;
-    for (int t = 0; t < 1024; ++t) {
-      const double v = tsum[t];
-      tsum[t] = run;
-      run += v;
+  if (warp == 0) {
+    double t = wtot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
     }
-    a.block_prefix[nb] = run;
+    wtot[lane] = t;  // inclusive over warps
   }
   __syncthreads();
-  double run = tsum[tid];
+  double run = (warp > 0 ? wtot[warp - 1] : 0.0) + (v - s);
+  if (tid == 1023) a.block_prefix[nb] = wtot[31];
   for (uint64_t i = lo; i < hi; ++i) {
     a.block_prefix[i] = run;
     run += a.block_sums[i];
@@ -248,19 +257,20 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 
 // ---------------------------------------------------------------------- expectation values
 constexpr int EXP_TERMS = 16;  // terms per launch (a larger X group takes several launches)
-constexpr int EXP_CHUNK = 16;  // warp blocks summed in the state precision before an FP64 add
-constexpr int EXP_UNROLL = 4;  // warp blocks whose loads are in flight together
+constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the state precision before an FP64 add
 
-// One X group (x) per launch, up to 32 of its terms.  The pair index r runs
+// One X group (x) per launch, up to 16 of its terms.  The pair index r runs
 // over the 2^n / 2 pairs (i, i ^ x) with bit h = top bit of x clear in i (for
 // x = 0 over the 2^n amplitudes, f = |psi_i|^2); f(r) = conj(psi_i) psi_{i^x}.
-// A half-warp holds 16 consecutive r; four shuffle butterflies give lane l the
-// Walsh-Hadamard coefficient F(l) = sum_l' (-1)^{|l & l'|} f(l'), so a term
-// whose Z mask restricted to the half-warp's index bits is zl takes F(zl) from
-// one lane, with the sign (-1)^{|i0 & zh|} of the rest (i0: the half-warp's
-// first index).  Per term that is one predicated add per 32 pairs instead of
-// a parity and an add per pair.  NT: the smallest power of two >= the term
-// count (that many FP32 chunk sums and FP64 accumulators per lane).
+// A warp block is 128 consecutive r: lane l holds r = 128 w + 32 u + l for
+// u = 0..3 (each of the four loads coalesced).  A 128-point Walsh-Hadamard
+// transform (two butterfly stages over u in registers, five over the lanes by
+// shuffles) leaves in lane l, register u the coefficient
+// F(l + 32 u) = sum_r' (-1)^{|(l + 32u) & r'|} f(r'), so a term whose Z mask
+// restricted to the block's index bits is zl takes F(zl) from one lane, with
+// the sign (-1)^{|i0 & zh|} of the rest (i0: the block's first index).  Per
+// term that is one predicated add per 128 pairs.  NT: the smallest power of
+// two >= the term count (FP32 chunk sums and FP64 accumulators per lane).
 template <typename T, int NT>
 __global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
   using V = typename CxT<T>::V;
@@ -273,12 +283,12 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
   const int nt = a.nterms;
   const uint64_t x = a.x_mask;
   const int h = x ? 63 - __clzll((long long)x) : 64;
-  // index bits of i behind the four low bits of r (bit h skipped)
-  const uint64_t lmask = h < 4 ? (0x1Full & ~(1ull << h)) : 0xFull;
+  // index bits of i behind the seven low bits of r (bit h skipped)
+  const uint64_t lmask = h < 7 ? (0xFFull & ~(1ull << h)) : 0x7Full;
   if (tid < NT) {
     const uint64_t z = tid < nt ? a.z_masks[tid] : 0ull;
     uint32_t zl = 0, k = 0;
-    for (int b = 0; b < 5; ++b)
+    for (int b = 0; b < 8; ++b)
       if ((lmask >> b) & 1) {
         zl |= uint32_t((z >> b) & 1) << k;
         ++k;
@@ -295,62 +305,72 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
     part[t] = 0;
   }
   const uint64_t N = 1ull << a.n;
-  const uint64_t npairs = x ? (N >> 1) : N;
+  const uint64_t npairs = x ? (N >> 1) : N;  // a multiple of 128: states have >= 2^10 amplitudes
   const uint64_t lowm = h < 64 ? ((1ull << h) - 1) : ~0ull;
-  const uint32_t l16 = uint32_t(lane & 15);
+  auto ins = [&](uint64_t r) -> uint64_t { return x ? (((r >> h) << (h + 1)) | (r & lowm)) : r; };
+  // offsets of lane l, register u from the block's first index (the insertion of a zero at bit h
+  // is linear on disjoint bits, so i(r0 + d) = i(r0) + i(d) for d < 128 and r0 a multiple of 128)
+  uint64_t off[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) off[u] = ins(uint64_t(32 * u + lane));
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-  constexpr int U = EXP_UNROLL;  // warp blocks of 32 pairs whose loads are in flight together
   int cnt = 0;
-  // whole warps iterate together (npairs is a multiple of 32: states have >= 2^10 amplitudes)
-  for (uint64_t wb0 = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb0 << 5) < npairs;
-       wb0 += uint64_t(U) * warps) {
-    V pi_[U], pj[U];
+  for (uint64_t wb = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb << 7) < npairs; wb += warps) {
+    const uint64_t i0 = ins(wb << 7);
+    T fr[4], fi[4];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t r = ((wb0 + uint64_t(u) * warps) << 5) | uint64_t(lane);
-      const bool ok = r < npairs;
-      const uint64_t i = x ? (((r >> h) << (h + 1)) | (r & lowm)) : r;
-      pi_[u] = ok ? st[i] : mkc(T(0), T(0));
-      pj[u] = (ok && x) ? st[i ^ x] : pi_[u];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t r = ((wb0 + uint64_t(u) * warps) << 5) | uint64_t(lane);
-      const uint64_t r0 = r & ~15ull;  // the half-warp's first pair
-      const uint64_t i0 = x ? (((r0 >> h) << (h + 1)) | (r0 & lowm)) : r0;
-      T fr, fi;
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t i = i0 + off[u];
+      const V p = st[i];
       if (x) {
-        fr = fma(pi_[u].x, pj[u].x, pi_[u].y * pj[u].y);   // Re conj(psi_i) psi_j
-        fi = fma(pi_[u].x, pj[u].y, -pi_[u].y * pj[u].x);  // Im
+        const V q = st[i ^ x];
+        fr[u] = fma(p.x, q.x, p.y * q.y);   // Re conj(psi_i) psi_j
+        fi[u] = fma(p.x, q.y, -p.y * q.x);  // Im
       } else {
-        fr = fma(pi_[u].x, pi_[u].x, pi_[u].y * pi_[u].y);
-        fi = T(0);
+        fr[u] = fma(p.x, p.x, p.y * p.y);
+        fi[u] = T(0);
       }
+    }
+    // Walsh-Hadamard over u (registers), then over the lanes
 #pragma unroll
-      for (int o = 1; o < 16; o <<= 1) {  // Walsh-Hadamard over the half-warp
-        const T qr = __shfl_xor_sync(0xffffffffu, fr, o);
-        const bool up = l16 & uint32_t(o);
-        fr = up ? qr - fr : fr + qr;
+    for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (!(u & o)) {
+          const T ar = fr[u], br = fr[u | o], ai = fi[u], bi = fi[u | o];
+          fr[u] = ar + br;
+          fr[u | o] = ar - br;
+          fi[u] = ai + bi;
+          fi[u | o] = ai - bi;
+        }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool up = lane & o;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T qr = __shfl_xor_sync(0xffffffffu, fr[u], o);
+        fr[u] = up ? qr - fr[u] : fr[u] + qr;
         if (x) {
-          const T qi = __shfl_xor_sync(0xffffffffu, fi, o);
-          fi = up ? qi - fi : fi + qi;
+          const T qi = __shfl_xor_sync(0xffffffffu, fi[u], o);
+          fi[u] = up ? qi - fi[u] : fi[u] + qi;
         }
       }
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        // term data from shared memory every time (kept out of registers)
-        uint32_t w;
-        uint64_t zh;
-        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(uint32_t(__cvta_generic_to_shared(zkw + t))));
-        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(zh) : "r"(uint32_t(__cvta_generic_to_shared(zhs + t))));
-        const uint32_t k = w >> 8;
-        const T c = (k & 1) ? fi : fr;
-        const bool neg = ((__popcll(i0 & zh) & 1) != 0) != (k >= 2);
-        part[t] += ((w & 0xFFu) == l16) ? (neg ? -c : c) : T(0);
-      }
     }
-    cnt += U;
-    if (cnt >= EXP_CHUNK) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      // term data from shared memory every time (kept out of registers)
+      uint32_t w;
+      uint64_t zh;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(uint32_t(__cvta_generic_to_shared(zkw + t))));
+      asm volatile("ld.shared.u64 %0, [%1];" : "=l"(zh) : "r"(uint32_t(__cvta_generic_to_shared(zhs + t))));
+      const uint32_t zl = w & 0xFFu, k = w >> 8, ur = (zl >> 5) & 3u;
+      const T vr = ur == 0 ? fr[0] : ur == 1 ? fr[1] : ur == 2 ? fr[2] : fr[3];
+      const T vi = ur == 0 ? fi[0] : ur == 1 ? fi[1] : ur == 2 ? fi[2] : fi[3];
+      const T c = (k & 1) ? vi : vr;
+      const bool neg = ((__popcll(i0 & zh) & 1) != 0) != (k >= 2);
+      part[t] += (zl == uint32_t(lane) + 32u * ur && zl != 0xFFu) ? (neg ? -c : c) : T(0);
+    }
+    if (++cnt == EXP_CHUNK) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         acc[t] += double(part[t]);

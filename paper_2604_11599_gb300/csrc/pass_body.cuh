@@ -808,19 +808,37 @@ struct GenericStages {
       const DStage st = A.stages[sp.s0 + si];
       uint32_t off[16];
       reg_offsets(st.R, off);
+      // complex64 with register bit 0 on tile bit 0: amplitude pairs share a
+      // 16-byte granule (the swizzle never touches bit 0), one access per pair
+      const bool pairs = sizeof(T) == 4 && st.R[0] == 1;
       for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
         const uint32_t b = group_base<GB>(st.E, uint32_t(grp));
         V a[16];
+        if (pairs) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
+          for (int j = 0; j < 16; j += 2) {
+            const typename CxT<T>::V4 q = *reinterpret_cast<const typename CxT<T>::V4*>(tb + (b ^ off[j]));
+            a[j] = pair_lo(q);
+            a[j + 1] = pair_hi(q);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) a[j] = tb[b ^ off[j]];
+        }
         for (int g = st.g0; g < st.g0 + st.ng; ++g) {
           const uint32_t w = sgk[g];
           if (!(w & SGK_ON)) continue;
           if ((w & SGK_KEY) == OP_D16 * 16u) d16_apply<T, M, TC>(a, smat + (w >> 16), tb, tc);
           else apply_gate(a, w & SGK_KEY, smat + (w >> 16));
         }
+        if (pairs) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
+          for (int j = 0; j < 16; j += 2)
+            *reinterpret_cast<typename CxT<T>::V4*>(tb + (b ^ off[j])) = make_pair4(a[j], a[j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tb[b ^ off[j]] = a[j];
+        }
       }
       // a direct pass relaxes the barrier after its last stage for kernels that
       // store from registers; this one stores from shared memory

@@ -778,20 +778,89 @@ struct Builder {
       }
       return k;
     };
+    // Gates a tile T runs, for the searches below: the same rule as take(),
+    // over per-gate masks and capacities gathered once per pass.
+    std::vector<uint64_t> cq;
+    std::vector<uint32_t> cml, cnd;
+    auto prep = [&]() {
+      cq.clear();
+      cml.clear();
+      cnd.clear();
+      for (int idx : rem) {
+        const Item& it = items[idx];
+        cq.push_back(it.qmask());
+        cml.push_back(uint32_t(mat_len(it)));
+        cnd.push_back(uint32_t(n_dots(it)));
+      }
+    };
+    auto count = [&](uint64_t T) -> size_t {
+      uint64_t blocked = 0;
+      uint32_t mat = 0, dots = 0, recs = 0;
+      size_t k = 0;
+      const size_t nr = cq.size();
+      for (size_t i = 0; i < nr; ++i) {
+        const uint64_t qm = cq[i];
+        if ((qm & blocked) || (qm & ~T) || recs + 1 + cnd[i] > cap || mat + cml[i] > MAX_PASS_MAT ||
+            dots + cnd[i] > MAX_PASS_DOTS) {
+          blocked |= qm;
+          if (blocked == all) break;  // nothing further can run
+          continue;
+        }
+        mat += cml[i];
+        dots += cnd[i];
+        recs += 1 + cnd[i];
+        ++k;
+      }
+      return k;
+    };
+    // Beam search over the gathered qubits (width kBeam): grow every kept tile
+    // by one qubit, keep the kBeam tiles that run the most gates (ties to the
+    // lower qubit set); returns the best tile seen.
+    auto beam = [&](uint64_t T0) -> uint64_t {
+      constexpr size_t kBeam = 4;
+      std::vector<uint64_t> cur{T0};
+      uint64_t best = T0;
+      size_t bestv = count(best);
+      std::vector<std::pair<size_t, uint64_t>> nx;
+      for (int step = popc(T0); step < m; ++step) {
+        nx.clear();
+        for (uint64_t X : cur)
+          for (int q = 0; q < n; ++q) {
+            if ((X >> q) & 1) continue;
+            const uint64_t X2 = X | (1ull << q);
+            nx.push_back({count(X2), X2});
+          }
+        std::sort(nx.begin(), nx.end(), [](const std::pair<size_t, uint64_t>& a, const std::pair<size_t, uint64_t>& b) {
+          return a.first > b.first || (a.first == b.first && a.second < b.second);
+        });
+        nx.erase(std::unique(nx.begin(), nx.end(),
+                             [](const std::pair<size_t, uint64_t>& a, const std::pair<size_t, uint64_t>& b) {
+                               return a.second == b.second;
+                             }),
+                 nx.end());
+        cur.clear();
+        for (size_t i = 0; i < nx.size() && cur.size() < kBeam; ++i) cur.push_back(nx[i].second);
+        if (!nx.empty() && nx[0].first > bestv) {
+          bestv = nx[0].first;
+          best = nx[0].second;
+        }
+      }
+      return best;
+    };
     while (!rem.empty()) {
       uint64_t T = low;
       if (tile_select && popc(all) > m) {
         // gathered qubits chosen one at a time for the gates they let this
         // pass run (a pair when no single qubit adds any; else the qubits of
         // the first gate that still fits), ties to the lowest qubit
-        size_t have = take(rem, T, false, nullptr, nullptr);
+        prep();
+        size_t have = count(T);
         while (popc(T) < m) {
           int bq = -1;
           size_t bv = 0;
           for (int q = 0; q < n; ++q) {
             if ((T >> q) & 1) continue;
-            uint64_t T2 = T | (1ull << q);
-            const size_t v = take(rem, T2, false, nullptr, nullptr);
+            const size_t v = count(T | (1ull << q));
             if (v > bv) {
               bv = v;
               bq = q;
@@ -808,8 +877,7 @@ struct Builder {
               if ((T >> a) & 1) continue;
               for (int b2 = a + 1; b2 < n; ++b2) {
                 if ((T >> b2) & 1) continue;
-                uint64_t T2 = T | (1ull << a) | (1ull << b2);
-                const size_t v = take(rem, T2, false, nullptr, nullptr);
+                const size_t v = count(T | (1ull << a) | (1ull << b2));
                 if (v > bv) {
                   bv = v;
                   bp = (1ull << a) | (1ull << b2);
@@ -833,8 +901,11 @@ struct Builder {
             }
           }
           if (!grew) break;
-          have = take(rem, T, false, nullptr, nullptr);
+          have = count(T);
         }
+        // the beam's tile when it lets this pass run more gates than the greedy one
+        const uint64_t Tb = beam(low);
+        if (count(Tb) > have) T = Tb;
       }
       std::vector<int> chosen, left;
       take(rem, T, !tile_select || popc(all) <= m, &chosen, &left);
