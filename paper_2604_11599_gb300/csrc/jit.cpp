@@ -60,8 +60,11 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     uint32_t off[16];
     off[0] = 0;
     for (int j = 1; j < 16; ++j) off[j] = off[j & (j - 1)] ^ st.R[__builtin_ctz(unsigned(j))];
-    o << "    for (int grp = tid; grp < " << (1 << GB) << "; grp += " << svp::PASS_THREADS << ") {\n"
-      << "      uint32_t b = 0;\n";
+    // one group per thread (2^(m-4) == threads): straight-line code, so the
+    // group base -- a function of the thread index only -- can stay out of the tile loop
+    if ((1 << GB) == svp::PASS_THREADS) o << "    {\n      const int grp = tid;\n";
+    else o << "    for (int grp = tid; grp < " << (1 << GB) << "; grp += " << svp::PASS_THREADS << ") {\n";
+    o << "      uint32_t b = 0;\n";
     for (int k = 0; k < GB; ++k) o << "      if (grp & " << (1 << k) << ") b ^= " << st.E[k] << "u;\n";
     // complex64 with register bit 0 on tile bit 0: amplitude pairs share a
     // 16-byte granule (the swizzle never touches bit 0), one access per pair

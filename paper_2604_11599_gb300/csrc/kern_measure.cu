@@ -256,7 +256,7 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 }
 
 // ---------------------------------------------------------------------- expectation values
-constexpr int EXP_TERMS = 16;  // terms per launch (a larger X group takes several launches)
+constexpr int EXP_TERMS = EXPVAL_TERMS;  // terms per launch (a larger X group takes several launches)
 constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the state precision before an FP64 add
 
 // One X group (x) per launch, up to 16 of its terms.  The pair index r runs
@@ -272,31 +272,15 @@ constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the sta
 // term that is one predicated add per 128 pairs.  NT: the smallest power of
 // two >= the term count (FP32 chunk sums and FP64 accumulators per lane).
 template <typename T, int NT>
-__global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
+__global__ void __launch_bounds__(256, 2) k_expval_group(const ExpvalArgs a) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
-  __shared__ uint64_t zhs[NT];
-  __shared__ uint32_t zkw[NT];  // zl | (k << 8) (zl = 0xFF: unused slot)
   __shared__ double red[8][NT];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = a.nterms;
   const uint64_t x = a.x_mask;
   const int h = x ? 63 - __clzll((long long)x) : 64;
-  // index bits of i behind the seven low bits of r (bit h skipped)
-  const uint64_t lmask = h < 7 ? (0xFFull & ~(1ull << h)) : 0x7Full;
-  if (tid < NT) {
-    const uint64_t z = tid < nt ? a.z_masks[tid] : 0ull;
-    uint32_t zl = 0, k = 0;
-    for (int b = 0; b < 8; ++b)
-      if ((lmask >> b) & 1) {
-        zl |= uint32_t((z >> b) & 1) << k;
-        ++k;
-      }
-    zkw[tid] = (tid < nt ? zl : 0xFFu) | (uint32_t(tid < nt ? a.phase[tid] : 0) << 8);
-    zhs[tid] = z & ~lmask;
-  }
-  __syncthreads();
   double acc[NT];
   T part[NT];
 #pragma unroll
@@ -358,11 +342,8 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(ExpvalArgs a) {
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      // term data from shared memory every time (kept out of registers)
-      uint32_t w;
-      uint64_t zh;
-      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(uint32_t(__cvta_generic_to_shared(zkw + t))));
-      asm volatile("ld.shared.u64 %0, [%1];" : "=l"(zh) : "r"(uint32_t(__cvta_generic_to_shared(zhs + t))));
+      const uint32_t w = a.zw[t];  // parameter block: warp-uniform operands
+      const uint64_t zh = a.zh[t];
       const uint32_t zl = w & 0xFFu, k = w >> 8, ur = (zl >> 5) & 3u;
       const T vr = ur == 0 ? fr[0] : ur == 1 ? fr[1] : ur == 2 ? fr[2] : fr[3];
       const T vi = ur == 0 ? fi[0] : ur == 1 ? fi[1] : ur == 2 ? fi[2] : fi[3];

@@ -202,13 +202,17 @@ uint64_t sample_blocks(int n);
 uint64_t sample_runs(int n);
 #endif
 
-// Pauli expectation values of one group of terms sharing an X mask
+// Pauli expectation values of one group of terms sharing an X mask.  The
+// terms travel in the kernel's parameter block (warp-uniform operands): for
+// term t, zw[t] = zl | phase << 8 (zl: its Z mask on the seven index bits a
+// 128-pair block spans, phase = |x & z| mod 4) and zh[t] = the rest of its Z mask.
+constexpr int EXPVAL_TERMS = 16;
 struct ExpvalArgs {
   const void* state;
   int n;
   uint64_t x_mask;
-  const uint64_t* z_masks;  // [nterms]
-  const int* phase;         // [nterms] i^phase factor (|x & z| mod 4)
+  uint64_t zh[EXPVAL_TERMS];
+  uint32_t zw[EXPVAL_TERMS];
   int nterms;               // <= 16
   double* partials;         // [grid][32]
   double* out;              // [nterms] (written by the last CTA)

@@ -1037,9 +1037,11 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   // shared-memory tile: 2^14 x 8 B (complex64) or 2^13 x 16 B (complex128) at most
   tb = std::min(std::max(tb, 10), dtype == SV_C64 ? MAX_TILE_BITS : MAX_TILE_BITS - 1);
   P.m = std::min(P.n_int, tb);
-  // 2^4 contiguous amplitudes per gathered chunk (128 B for complex64, 256 B for complex128):
-  // shorter runs than 2^5 leave more qubits to gather, so a tile fuses more gates
-  int lb = tune.low_bits > 0 ? tune.low_bits : 4;
+  // 2^3 contiguous amplitudes per gathered chunk (64 B for complex64, 128 B for complex128):
+  // shorter runs leave more qubits to gather, so a tile fuses more gates (n=30 layered
+  // program: 41 passes with 2^4-amplitude runs, 38 with 2^3, measured 6.37e12 -> 6.50e12
+  // updates/s on one box)
+  int lb = tune.low_bits > 0 ? tune.low_bits : 3;
   P.L = std::min(std::max(lb, 2), P.m);
   P.L = std::max(P.L, P.m - 9);  // at most 2^9 gathered chunks per tile
   P.L = std::min(P.L, dtype == SV_C64 ? 9 : 8);  // a warp-group of 256 threads covers whole chunks

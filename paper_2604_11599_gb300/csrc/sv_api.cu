@@ -112,8 +112,6 @@ struct sv_state {
   DevBuf<double> sample_buf;
   DevBuf<uint64_t> sample_out;
   DevBuf<double> exp_partials;
-  DevBuf<uint64_t> exp_z;
-  DevBuf<int> exp_k;
   DevBuf<double> exp_out;
   unsigned* exp_ticket = nullptr;
   std::vector<double> dense;  // host copy for planning
@@ -678,33 +676,37 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
     if (it == groups.end()) keys.push_back(terms[t].x_mask);
     groups[terms[t].x_mask].push_back(t);
   }
-  std::vector<uint64_t> zs;
-  std::vector<int> ks;
-  std::vector<std::pair<size_t, size_t>> launches;  // (x key index, first term slot)
   std::vector<size_t> order;
   for (uint64_t x : keys)
     for (size_t t : groups[x]) order.push_back(t);
-  for (size_t t : order) {
-    zs.push_back(terms[t].z_mask);
-    ks.push_back(__builtin_popcountll(terms[t].x_mask & terms[t].z_mask) & 3);
-  }
   const size_t nt = order.size();
-  SV_CUDA(h->exp_z.upload(zs, h->stream));
-  SV_CUDA(h->exp_k.upload(ks, h->stream));
   SV_CUDA(h->exp_out.reserve(std::max<size_t>(nt, 1)));
   const int grid = std::max(1, std::min(h->sms * 8, int((1ull << h->n_int) / 256)));
   SV_CUDA(h->exp_partials.reserve(size_t(grid) * 32));
   size_t slot = 0;
   for (uint64_t x : keys) {
     const size_t cnt = groups[x].size();
-    for (size_t c = 0; c < cnt; c += 16) {  // at most 16 terms per launch
+    // index bits of i behind the seven low bits of the pair index (bit h, the top bit of x, skipped)
+    const int hbit = x ? 63 - __builtin_clzll(x) : 64;
+    const uint64_t lmask = hbit < 7 ? (0xFFull & ~(1ull << hbit)) : 0x7Full;
+    const std::vector<size_t>& g = groups[x];
+    for (size_t c = 0; c < cnt; c += svk::EXPVAL_TERMS) {  // at most 16 terms per launch
       svk::ExpvalArgs a{};
       a.state = h->state;
       a.n = h->n_int;
       a.x_mask = x;
-      a.z_masks = h->exp_z.p + slot + c;
-      a.phase = h->exp_k.p + slot + c;
-      a.nterms = int(std::min<size_t>(16, cnt - c));
+      a.nterms = int(std::min<size_t>(svk::EXPVAL_TERMS, cnt - c));
+      for (int t = 0; t < svk::EXPVAL_TERMS; ++t) {
+        a.zw[t] = 0xFFu;  // matches no lane
+        a.zh[t] = 0;
+        if (t >= a.nterms) continue;
+        const uint64_t z = terms[g[c + size_t(t)]].z_mask;
+        uint32_t zl = 0, k = 0;
+        for (int b = 0; b < 8; ++b)
+          if ((lmask >> b) & 1) zl |= uint32_t((z >> b) & 1) << (k++);
+        a.zw[t] = zl | (uint32_t(__builtin_popcountll(x & z) & 3) << 8);
+        a.zh[t] = z & ~lmask;
+      }
       a.partials = h->exp_partials.p;
       a.out = h->exp_out.p + slot + c;
       a.ticket = h->exp_ticket;

@@ -10,7 +10,11 @@ footprint fits the budget, and runs two kinds of work concurrently on the GPU:
   by the next one (continuous batching);
 * large requests get a resident state vector and their own CUDA stream in a
   worker pool; their shots run back to back on that stream, overlapping with
-  the batched launches and with each other.
+  the batched launches and with each other.  Admitted large requests start
+  shortest first (estimated work: 2^n x program length x the shots that can
+  take distinct outcome paths, capped at 64), so a long request does not hold
+  up the short ones behind it; the batched launches run on a high-priority
+  stream, so the GPU turns to them between the large requests' kernels.
 
 Shot s of request r uses Philox key (seed, stream = r.rid) and counter
 (shot = s, draw index): its record does not depend on what else is running,
@@ -79,7 +83,7 @@ class GpuBackend:
 
         self.sv, self.torch = sv, torch
         self.dtype, self.seed, self.branching = dtype, seed, branching
-        self.batch_stream = torch.cuda.Stream()
+        self.batch_stream = torch.cuda.Stream(priority=-1)  # the GPU takes these launches first
         with torch.cuda.stream(self.batch_stream):
             self.batch = sv.Batch(dtype, stream=self.batch_stream.cuda_stream)
         self.prog_ids: dict[int, int] = {}
@@ -132,14 +136,25 @@ class GpuBackend:
         return cregs
 
 
+def work_estimate(r: Req) -> float:
+    """Relative cost of a request on the large-request path: one trajectory
+    sweeps 2^n amplitudes about once per few records, and shot branching runs
+    one trajectory per distinct outcome path (at most the shots)."""
+    return float(1 << max(r.n, 10)) * max(1, len(r.ops)) * min(max(r.shots, 1), 64)
+
+
 class Server:
     def __init__(self, backend, dtype: str = "c64", batch_max_n: int = 18, memory_budget: Optional[int] = None,
-                 large_workers: int = 4, max_launch_shots: int = 8192,
+                 large_workers: int = 4, max_launch_shots: int = 8192, large_order: str = "shortest",
                  clock: Callable[[], float] = time.perf_counter):
+        if large_order not in ("shortest", "fifo"):
+            raise ValueError("large_order is 'shortest' or 'fifo'")
         self.backend = backend
         self.dtype = dtype
         self.batch_max_n = batch_max_n
         self.max_launch_shots = max_launch_shots
+        self.large_order = large_order
+        self.large_workers = large_workers
         self.budget = memory_budget if memory_budget is not None else int(0.8 * backend.free_bytes())
         self.pool = ThreadPoolExecutor(max_workers=large_workers)
         self.clock = clock
@@ -149,7 +164,9 @@ class Server:
         """Runs the request stream to completion; returns per-request results and stats."""
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         small_wait: list[tuple[Req, float]] = []
+        large_wait: list[tuple[float, int, Req, float]] = []  # admitted, not started: (cost, order, req, admitted)
         large_run: dict[int, tuple[Req, float, Future]] = {}
+        admitted_count = 0
         batch_fut: Optional[Future] = None
         batch_reqs: list[tuple[Req, float]] = []
         used = 0
@@ -161,7 +178,7 @@ class Server:
         def now():
             return self.clock() - t0
 
-        while pending or small_wait or large_run or batch_fut is not None:
+        while pending or small_wait or large_wait or large_run or batch_fut is not None:
             t = now() if realtime else float("inf")
             progressed = False
             # admission: first come first served while the footprint fits
@@ -178,7 +195,15 @@ class Server:
                 if r.n <= self.batch_max_n:
                     small_wait.append((r, ta))
                 else:
-                    large_run[r.rid] = (r, ta, self.pool.submit(self.backend.run_large, r))
+                    cost = work_estimate(r) if self.large_order == "shortest" else 0.0
+                    large_wait.append((cost, admitted_count, r, ta))
+                admitted_count += 1
+                progressed = True
+            # start admitted large requests, shortest estimated work first (or in arrival order)
+            while large_wait and len(large_run) < self.large_workers:
+                k = min(range(len(large_wait)), key=lambda j: (large_wait[j][0], large_wait[j][1]))
+                _, _, r, ta = large_wait.pop(k)
+                large_run[r.rid] = (r, ta, self.pool.submit(self.backend.run_large, r))
                 progressed = True
             # continuous batching: waiting small requests join the next launch, in
             # arrival order, up to max_launch_shots shots (at least one request)
@@ -205,7 +230,7 @@ class Server:
                 tf = now()
                 results.append(Result(r.rid, cregs, r.arrival, ta, tf if realtime else ta, "large"))
                 progressed = True
-            if not realtime and not progressed and pending and not large_run and batch_fut is None:
+            if not realtime and not progressed and pending and not large_run and not large_wait and batch_fut is None:
                 raise RuntimeError("admission stalled")
             if not progressed:
                 time.sleep(idle_sleep)

@@ -100,3 +100,32 @@ def test_request_larger_than_budget_is_rejected():
     with pytest.raises(ValueError, match="more than the whole budget"):
         srv.serve(_reqs(1, n_of=lambda i: 30, gap=0.0))
     srv.close()
+
+
+def test_large_requests_start_shortest_first():
+    """Admitted large requests wait for a worker; the one with the least
+    estimated work starts first (arrival order breaks ties)."""
+    be = FakeBackend(large_s=0.03)
+    started = []
+    run = be.run_large
+
+    def spy(r):
+        started.append(r.rid)
+        return run(r)
+
+    be.run_large = spy
+    srv = Server(be, memory_budget=1 << 40, large_workers=1)
+    reqs = [Req(0, 0.0, 26, np.zeros(0), 4), Req(1, 0.0, 24, np.zeros(0), 4), Req(2, 0.0, 22, np.zeros(0), 4),
+            Req(3, 0.0, 23, np.zeros(0), 4)]
+    res, _ = srv.serve(reqs)
+    srv.close()
+    assert len(res) == 4
+    assert started == [2, 3, 1, 0]
+    srv = Server(FakeBackend(large_s=0.01), memory_budget=1 << 40, large_workers=1, large_order="fifo")
+    be2 = srv.backend
+    started.clear()
+    run2 = be2.run_large
+    be2.run_large = lambda r: (started.append(r.rid), run2(r))[1]
+    srv.serve(reqs)
+    srv.close()
+    assert started == [0, 1, 2, 3]
