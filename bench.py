@@ -29,6 +29,7 @@ value the sum of all ranks' updates over that time ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -452,7 +453,7 @@ def measure_forms(sv, torch):
     terms = W.heisenberg_fields(9, n_s, 10 * n_s)
     xs = [int(x) for x in terms["x_mask"]]
     groups = len(set(xs))
-    reads = sum((xs.count(x) + 31) // 32 for x in set(xs))  # one read of the state per launch of <= 32 terms
+    reads = sum((xs.count(x) + 15) // 16 for x in set(xs))  # one read of the state per launch of <= 16 terms
     sbytes = float(1 << n_s) * 8
     shots = 1 << 20
     with sv.State(n_s, "c64") as st:
@@ -698,6 +699,7 @@ def run_reference(args, rank, world):
 
 
 def main():
+    faulthandler.enable()  # a crash in native code prints the Python stack that led to it
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -189,6 +189,9 @@ sv_status sv_set_jit_blocks(sv_state* h, int blocks_per_sm);
  * during the call only.  SV_ERR_ARG for a malformed list (qubit >= n,
  * duplicate qubits, cbit >= 64, lengths out of range, nesting > 64),
  * SV_ERR_UNSUPPORTED if the unrolled program exceeds 2^22 ops or 2^20 predicates.
+ * The program belongs to the caller (sv_program_free).  It launches on this
+ * state only; once the state is destroyed, freeing it is the one valid call
+ * (sv_launch then reports SV_ERR_ARG).
  */
 sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out);
 

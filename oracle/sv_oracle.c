@@ -80,6 +80,11 @@ typedef struct {
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_ZERO = -2 };
 
 #define CHUNK 4096 /* fixed summation chunk (amplitudes) */
+/* states below this size run their loops on one thread: the threads of a
+ * parallel region cost more than the loop itself there (results do not
+ * depend on the thread count: sums are chunked in a fixed order) */
+#define OMP_MIN_AMPS (1ULL << 14)
+#define OMP_MIN_CHUNKS 4
 
 /* ---------------------------------------------------------------- Philox4x64-10 */
 /*
@@ -179,7 +184,7 @@ static int gate_qubits(int gate) {
 static void apply_1q(cplx* psi, int n, int q, int ctrl, const cplx m[4]) {
   const uint64_t N = 1ULL << n, bq = 1ULL << q;
   const uint64_t bc = ctrl >= 0 ? 1ULL << ctrl : 0;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_AMPS)
   for (uint64_t i = 0; i < N; ++i) {
     if (i & bq) continue;
     if (ctrl >= 0 && !(i & bc)) continue;
@@ -193,7 +198,7 @@ static void apply_1q(cplx* psi, int n, int q, int ctrl, const cplx m[4]) {
 /* SWAP(a, b): exchange the amplitudes whose bits a and b differ. */
 static void apply_swap(cplx* psi, int n, int a, int b) {
   const uint64_t N = 1ULL << n, ba = 1ULL << a, bb = 1ULL << b;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_AMPS)
   for (uint64_t i = 0; i < N; ++i) {
     if ((i & ba) && !(i & bb)) {
       uint64_t j = (i ^ ba) | bb;
@@ -209,7 +214,7 @@ static void apply_dense(cplx* psi, int n, int k, const int32_t* qs, const cplx* 
   const uint64_t N = 1ULL << n, K = 1ULL << k;
   uint64_t qmask = 0;
   for (int r = 0; r < k; ++r) qmask |= 1ULL << qs[r];
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_AMPS)
   for (uint64_t base = 0; base < N; ++base) {
     if (base & qmask) continue;
     cplx v[256], w[256];
@@ -236,7 +241,7 @@ static double prob_sum(const cplx* psi, int n, int q, int bit) {
   const uint64_t N = 1ULL << n;
   const uint64_t nchunks = (N + CHUNK - 1) / CHUNK;
   double* part = (double*)malloc(sizeof(double) * nchunks);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (nchunks > OMP_MIN_CHUNKS)
   for (uint64_t c = 0; c < nchunks; ++c) {
     double s = 0;
     uint64_t lo = c * CHUNK, hi = lo + CHUNK < N ? lo + CHUNK : N;
@@ -319,7 +324,7 @@ static int measure(orc_ctx* cx, int q, int is_reset) {
   const double scale = 1.0 / sqrt(p);
   const uint64_t N = 1ULL << cx->n;
   cplx* psi = cx->psi;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_AMPS)
   for (uint64_t i = 0; i < N; ++i) {
     if ((int)((i >> q) & 1) == outcome) psi[i] *= scale;
     else psi[i] = 0;
@@ -441,7 +446,7 @@ int orc_run(int n, const void* ops, size_t n_ops, const double* params, size_t n
   cx.draws = draws; cx.max_draws = draws ? max_draws : 0;
   cx.norms = norms; cx.max_norms = norms ? max_norms : 0;
   const uint64_t N = 1ULL << n;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= OMP_MIN_AMPS)
   for (uint64_t i = 0; i < N; ++i) psi[i] = 0;
   psi[0] = 1;
   exec_range(&cx, 0, n_ops);
@@ -517,7 +522,7 @@ int orc_expval(int n, const cplx* psi, const void* terms_v, size_t n_terms, doub
       else if (z) apply_1q(phi, n, q, -1, PZ);
     }
     if ((terms[t].x_mask | terms[t].z_mask) >> n) { free(phi); free(part); return ORC_ERR_ARG; }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (nchunks > OMP_MIN_CHUNKS)
     for (uint64_t c = 0; c < nchunks; ++c) {
       double s = 0;
       uint64_t lo = c * CHUNK, hi = lo + CHUNK < N ? lo + CHUNK : N;

@@ -141,7 +141,7 @@ constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_WAIT_POLLS = 1u << 20;  // bounded MMA completion wait
 
 // Shared state of the tensor-core path (part of the pass kernel's static shared memory).
-constexpr int TC_SLOTS = 2;  // dense gates per pass (MAX_PASS_MAT holds two 16 x 16 matrices)
+constexpr int TC_SLOTS = 4;  // dense gates per pass (MAX_PASS_MAT holds four 16 x 16 matrices)
 
 struct TcShared {
   __align__(128) float bt[TC_SLOTS][2][1024];  // B high / low parts per dense gate, core-matrix layout

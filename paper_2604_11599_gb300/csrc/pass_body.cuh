@@ -262,7 +262,10 @@ __device__ __forceinline__ void d16_tc(V* a, const V* m, TcCtx& tc) {
   const int tid = threadIdx.x, warp = tid >> 5;
   TcShared& s = *tc.s;
   const uint32_t mo = uint32_t(m - static_cast<const V*>(tc.smat));
-  const int slot = s.slot_mat[0] == mo ? 0 : 1;
+  int slot = 0;
+#pragma unroll
+  for (int k = 1; k < TC_SLOTS; ++k)
+    if (s.slot_mat[k] == mo) slot = k;
   unsigned char* bt0 = reinterpret_cast<unsigned char*>(s.bt[slot][0]);
   unsigned char* bt1 = reinterpret_cast<unsigned char*>(s.bt[slot][1]);
   const uint32_t lane_base = uint32_t(32 * (warp & 3)) << 16;
@@ -973,6 +976,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           if (tid == 0) tc.s->slot_mat[k] = mo;
           ++k;
         }
+      if (tid == 0)
+        for (int j = k; j < TC_SLOTS; ++j) tc.s->slot_mat[j] = ~0u;  // unused slots match no gate
       fence_async_smem();
       __syncthreads();
     }

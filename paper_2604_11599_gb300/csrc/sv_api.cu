@@ -9,6 +9,7 @@
 #include <memory>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/sv.h"
@@ -118,7 +119,7 @@ struct sv_state {
   uint64_t dense_hash = 0;
   svp::Tuning tune;
   std::unordered_map<uint64_t, std::unique_ptr<sv_program>> cache;
-  const sv_program* last = nullptr;
+  std::unordered_set<sv_program*> prepared;  // programs handed out by sv_prepare, not yet freed
   // pass timing
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -236,7 +237,6 @@ sv_status launch_program(sv_state* h, sv_program* p, const double* dev_params, s
       }
     }
   }
-  h->last = p;
   return SV_OK;
 }
 
@@ -355,6 +355,9 @@ sv_status sv_destroy(sv_state* h) {
   if (!h) return SV_OK;
   cudaStreamSynchronize(h->stream);
   h->cache.clear();
+  // programs prepared for this state stay valid for sv_program_free only
+  for (sv_program* p : h->prepared) p->owner = nullptr;
+  h->prepared.clear();
   if (h->owns_state && h->state) cudaFree(h->state);
   if (h->ctrl) cudaFree(h->ctrl);
   if (h->trace) cudaFree(h->trace);
@@ -416,6 +419,7 @@ sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** o
   p->plan = cached->plan;
   st = upload_program(h, p.get());
   if (st != SV_OK) return st;
+  h->prepared.insert(p.get());
   *out = p.release();
   return SV_OK;
 }
@@ -439,7 +443,10 @@ sv_status sv_plan_info(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, co
 sv_status sv_program_free(sv_program* p) {
   if (!p) return SV_OK;
   if (p->cached) return fail(SV_ERR_ARG, "program belongs to a cache");
-  if (p->owner) cudaStreamSynchronize(p->owner->stream);
+  if (p->owner) {  // null once its state was destroyed (which waited for the state's work)
+    cudaStreamSynchronize(p->owner->stream);
+    p->owner->prepared.erase(p);
+  }
   delete p;
   return SV_OK;
 }

@@ -76,7 +76,7 @@ constexpr int PASS_THREADS = 256;
 constexpr int MAX_TILE_BITS = 14;
 constexpr int MAX_GROUP_Q = 4;
 constexpr int MAX_PASS_GATES = 128;
-constexpr int MAX_PASS_MAT = 512;   // complex entries staged in shared memory per pass
+constexpr int MAX_PASS_MAT = 1024;  // complex entries staged in shared memory per pass (four dense 16 x 16)
 constexpr int MAX_TRACE = 4096;     // draw records kept per trajectory
 constexpr int ADJ_REG_BITS = 3;     // gate register bits of a backward stage (bit 3 selects phi / lambda)
 constexpr int MAX_PASS_DOTS = 64;   // derivative accumulators per backward pass

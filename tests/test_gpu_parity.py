@@ -397,3 +397,22 @@ def test_state_tensor_view_is_zero_copy(svmod):
         t = st.tensor()
         assert t.is_cuda and t.dtype == torch.complex64
         assert abs(complex(t[4].item()) - 1) < 1e-7
+
+
+def test_program_outliving_its_state(svmod):
+    """A prepared program freed after its state was closed: the free touches
+    nothing of the state, and a launch of such a program on a new state is an
+    argument error (not a launch of another state's plan)."""
+    c = W.layered(5, 12, layers=2)
+    st = svmod.State(12, "c64")
+    prog = st.prepare(c.ops)
+    st.launch(prog)
+    st.close()
+    st2 = svmod.State(12, "c64")
+    with pytest.raises(svmod.SVError):
+        st2.launch(prog)
+    prog.free()
+    prog2 = st2.prepare(c.ops)
+    st2.launch(prog2)
+    del prog2  # freed while its state is alive
+    st2.close()
