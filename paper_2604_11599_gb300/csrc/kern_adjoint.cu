@@ -20,8 +20,46 @@
 namespace svk {
 using namespace svp;
 
+__device__ __forceinline__ int popc_w(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ int popc_w(uint64_t v) { return __popcll(v); }
+
+// lambda = H psi over this CTA's slot (one gather of psi per X group; the
+// group's coefficient at j from its terms' Z masks, in mask type W), and
+// this thread's part of <psi|lambda>.
+template <typename W, typename T, typename AV>
+__device__ __forceinline__ double lambda_h(const AdjArgs& J, const typename CxT<T>::V* phi,
+                                           typename CxT<T>::V* lam, const AV* hc, const uint64_t* hz,
+                                           uint64_t N) {
+  using V = typename CxT<T>::V;
+  double e = 0;
+  for (uint64_t i = threadIdx.x; i < N; i += PASS_THREADS) {
+    T ar = 0, ai = 0;
+    for (uint32_t g = 0; g < J.ngroups; ++g) {
+      const uint64_t j = i ^ J.hx[g];
+      const V pj = phi[j];
+      const W jw = W(j);
+      T wr = 0, wi = 0;
+      for (uint32_t t = J.hg0[g]; t < J.hg0[g + 1]; ++t) {
+        const bool neg = popc_w(jw & W(hz[t])) & 1;
+        const AV c = hc[t];
+        wr += neg ? -c.x : c.x;
+        wi += neg ? -c.y : c.y;
+      }
+      ar += wr * pj.x - wi * pj.y;
+      ai += wr * pj.y + wi * pj.x;
+    }
+    lam[i] = mkc(ar, ai);
+    const V pi_ = phi[i];
+    e += double(pi_.x) * double(ar) + double(pi_.y) * double(ai);
+  }
+  return e;
+}
+
+// complex64: two CTAs per SM (128 registers, no spills of note), so that the
+// dependent FP32 chains of one CTA's stages overlap the other's; complex128
+// keeps one (its registers would spill at 128)
 template <typename T, int M>
-__global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
+__global__ void __launch_bounds__(PASS_THREADS, sizeof(T) == 4 ? 2 : 1) k_adjoint(const AdjArgs J) {
   using V = typename CxT<T>::V;
   using Acc = T;
   constexpr int GB = M - ADJ_REG_BITS;  // group-index bits of a backward stage
@@ -73,39 +111,23 @@ __global__ void __launch_bounds__(PASS_THREADS, 1) k_adjoint(const AdjArgs J) {
 
     // ---- lambda = H psi and E = <psi|lambda>
     {
-      // Hamiltonian terms staged in the (idle) dynamic shared memory; the
-      // 16-byte coefficients first so that they stay 16-byte aligned
-      double2* hc = reinterpret_cast<double2*>(smem_raw);
+      // Hamiltonian terms staged in the (idle) dynamic shared memory, their
+      // coefficients converted once to the state's precision (complex64:
+      // FP32, whose error stays far below the state's own; converting per
+      // term per amplitude, or summing in FP64, would bound this step at
+      // GB300's FP64 rate); the coefficients first, so that they stay aligned
+      using AV = typename CxT<Acc>::V;
+      AV* hc = reinterpret_cast<AV*>(smem_raw);
       uint64_t* hz = reinterpret_cast<uint64_t*>(hc + J.nterms);
       for (uint32_t t = tid; t < J.nterms; t += PASS_THREADS) {
         hz[t] = J.hz[t];
-        hc[t] = J.hc[t];
+        hc[t] = mkc(Acc(J.hc[t].x), Acc(J.hc[t].y));
       }
       __syncthreads();
-      double e = 0;
-      for (uint64_t i = tid; i < N; i += PASS_THREADS) {
-        Acc ar = 0, ai = 0;
-        for (uint32_t g = 0; g < J.ngroups; ++g) {
-          const uint64_t j = i ^ J.hx[g];
-          const V pj = phi[j];
-          // the group's coefficient at j, sum_t c_t i^k_t (-1)^{|j & z_t|}, in the
-          // state's precision (complex64: FP32, whose error stays far below the
-          // state's own; FP64 per term per amplitude would bound this step at
-          // GB300's FP64 rate)
-          Acc wr = 0, wi = 0;
-          for (uint32_t t = J.hg0[g]; t < J.hg0[g + 1]; ++t) {
-            const bool neg = __popcll(j & hz[t]) & 1;
-            const Acc cr = Acc(hc[t].x), ci = Acc(hc[t].y);
-            wr += neg ? -cr : cr;
-            wi += neg ? -ci : ci;
-          }
-          ar += wr * pj.x - wi * pj.y;
-          ai += wr * pj.y + wi * pj.x;
-        }
-        lam[i] = mkc(ar, ai);
-        const V pi_ = phi[i];
-        e += double(pi_.x) * double(ar) + double(pi_.y) * double(ai);
-      }
+      // the group's coefficient at j, sum_t c_t i^k_t (-1)^{|j & z_t|}; the
+      // masks in 32 bits where the state has at most 32 qubits
+      double e = (J.n_int <= 32) ? lambda_h<uint32_t, T>(J, phi, lam, hc, hz, N)
+                                 : lambda_h<uint64_t, T>(J, phi, lam, hc, hz, N);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
       if (lane == 0) ered[warp] = e;

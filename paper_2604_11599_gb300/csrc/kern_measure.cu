@@ -52,12 +52,6 @@ __device__ __forceinline__ DFv dfv_abs2(float x, float y) {
   return dfv_add(DFv{p, __fmaf_rn(x, x, -p)}, DFv{q, __fmaf_rn(y, y, -q)});
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // One CTA per block, one warp per 32 runs (1,024 amplitudes), loaded
 // coalesced: at step k, complex64 lane l holds amplitudes 64k + 2l, +1 (run
 // 2k + l/16), complex128 lane l holds amplitude 32k + l (run k).  A run's sum
@@ -257,7 +251,23 @@ cudaError_t launch_sample(int dtype, const SampleArgs& a, int sms, cudaStream_t 
 
 // ---------------------------------------------------------------------- expectation values
 constexpr int EXP_TERMS = EXPVAL_TERMS;  // terms per launch (a larger X group takes several launches)
-constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the state precision before an FP64 add
+constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the state precision before the accumulator
+
+// Per-term accumulators of the expectation kernel: complex64 chunk sums go
+// into a double-float (on the FP32 pipes; a conversion and an FP64 add per
+// term per chunk would bind the kernel to GB300's FP64 rate), complex128 into
+// FP64.
+template <typename T> struct ExpAcc;
+template <> struct ExpAcc<float> {
+  DFv v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = dfv_add(v, DFv{x, 0.f}); }
+  __device__ __forceinline__ double get() const { return double(v.hi) + double(v.lo); }
+};
+template <> struct ExpAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double get() const { return v; }
+};
 
 // One X group (x) per launch, up to 16 of its terms.  The pair index r runs
 // over the 2^n / 2 pairs (i, i ^ x) with bit h = top bit of x clear in i (for
@@ -265,29 +275,30 @@ constexpr int EXP_CHUNK = 8;   // warp blocks (128 pairs each) summed in the sta
 // A warp block is 128 consecutive r: lane l holds r = 128 w + 32 u + l for
 // u = 0..3 (each of the four loads coalesced).  A 128-point Walsh-Hadamard
 // transform (two butterfly stages over u in registers, five over the lanes by
-// shuffles) leaves in lane l, register u the coefficient
-// F(l + 32 u) = sum_r' (-1)^{|(l + 32u) & r'|} f(r'), so a term whose Z mask
-// restricted to the block's index bits is zl takes F(zl) from one lane, with
-// the sign (-1)^{|i0 & zh|} of the rest (i0: the block's first index).  Per
-// term that is one predicated add per 128 pairs.  NT: the smallest power of
-// two >= the term count (FP32 chunk sums and FP64 accumulators per lane).
+// shuffles) gives F(p) = sum_r' (-1)^{|p & r'|} f(r') at p = l + 32 u, which
+// the warp writes to its slice of shared memory (Re F at p, Im F at 128 + p);
+// a term whose Z mask restricted to the block's index bits is zl then reads
+// F(zl) (its real or imaginary part, by the phase i^k of the term) with one
+// warp-uniform (broadcast) load and adds it with the sign (-1)^{|i0 & zh|} of
+// the rest (i0: the block's first index; zh has no bits below 7, so the sign
+// is taken on i0 >> 7 and zh >> 7 in 32 bits).  Every lane does the same
+// per-term work, so lane 0's sums are the warp's.  NT: the smallest power of
+// two >= the term count (chunk sums in the state precision, ExpAcc beyond).
 template <typename T, int NT>
 __global__ void __launch_bounds__(256, 2) k_expval_group(const ExpvalArgs a) {
   using V = typename CxT<T>::V;
   const V* st = reinterpret_cast<const V*>(a.state);
   __shared__ double red[8][NT];
+  __shared__ T wf[8][2][128];  // per warp: Re F, Im F of the current block
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = a.nterms;
   const uint64_t x = a.x_mask;
   const int h = x ? 63 - __clzll((long long)x) : 64;
-  double acc[NT];
+  ExpAcc<T> acc[NT];
   T part[NT];
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    acc[t] = 0;
-    part[t] = 0;
-  }
+  for (int t = 0; t < NT; ++t) part[t] = 0;
   const uint64_t N = 1ull << a.n;
   const uint64_t npairs = x ? (N >> 1) : N;  // a multiple of 128: states have >= 2^10 amplitudes
   const uint64_t lowm = h < 64 ? ((1ull << h) - 1) : ~0ull;
@@ -297,6 +308,8 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(const ExpvalArgs a) {
   uint64_t off[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) off[u] = ins(uint64_t(32 * u + lane));
+  T* const fre = wf[warp][0];
+  T* const fim = wf[warp][1];  // = fre + 128
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
   int cnt = 0;
   for (uint64_t wb = uint64_t(blockIdx.x) * (blockDim.x >> 5) + uint64_t(warp); (wb << 7) < npairs; wb += warps) {
@@ -340,21 +353,25 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(const ExpvalArgs a) {
         }
       }
     }
+    __syncwarp();  // the previous block's reads are done
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      fre[32 * u + lane] = fr[u];
+      if (x) fim[32 * u + lane] = fi[u];
+    }
+    __syncwarp();
+    const uint32_t i7 = uint32_t(i0 >> 7);
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const uint32_t w = a.zw[t];  // parameter block: warp-uniform operands
-      const uint64_t zh = a.zh[t];
-      const uint32_t zl = w & 0xFFu, k = w >> 8, ur = (zl >> 5) & 3u;
-      const T vr = ur == 0 ? fr[0] : ur == 1 ? fr[1] : ur == 2 ? fr[2] : fr[3];
-      const T vi = ur == 0 ? fi[0] : ur == 1 ? fi[1] : ur == 2 ? fi[2] : fi[3];
-      const T c = (k & 1) ? vi : vr;
-      const bool neg = ((__popcll(i0 & zh) & 1) != 0) != (k >= 2);
-      part[t] += (zl == uint32_t(lane) + 32u * ur && zl != 0xFFu) ? (neg ? -c : c) : T(0);
+      const T c = fre[w & 0xFFu];
+      const uint32_t sg = (uint32_t(__popc(i7 & a.zh7[t])) ^ (w >> 8)) & 1u;
+      part[t] += sg ? -c : c;
     }
     if (++cnt == EXP_CHUNK) {
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        acc[t] += double(part[t]);
+        acc[t].add(part[t]);
         part[t] = 0;
       }
       cnt = 0;
@@ -362,16 +379,11 @@ __global__ void __launch_bounds__(256, 2) k_expval_group(const ExpvalArgs a) {
   }
   // a pair contributes twice its value (the pair (i^x, i) is not visited)
   const double pw = x == 0 ? 1.0 : 2.0;
+  if (lane == 0)
 #pragma unroll
-  for (int t = 0; t < NT; ++t) acc[t] = pw * (acc[t] + double(part[t]));
-  // block reduction (fixed order)
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const double v = warp_sum_d(acc[t]);
-    if (lane == 0) red[warp][t] = v;
-  }
+    for (int t = 0; t < NT; ++t) red[warp][t] = pw * (acc[t].get() + double(part[t]));
   __syncthreads();
-  if (tid < NT) {
+  if (tid < NT) {  // block reduction (fixed order)
     double sum = 0;
     for (int w = 0; w < 8; ++w) sum += red[w][tid];
     a.partials[blockIdx.x * EXP_TERMS + tid] = sum;

@@ -211,8 +211,8 @@ struct ExpvalArgs {
   const void* state;
   int n;
   uint64_t x_mask;
-  uint64_t zh[EXPVAL_TERMS];
-  uint32_t zw[EXPVAL_TERMS];
+  uint32_t zh7[EXPVAL_TERMS];  // Z mask bits above bit 6 of the pair's first index, shifted down by 7
+  uint32_t zw[EXPVAL_TERMS];   // bits 0..7: index of the term's transform value (Re: zl, Im: 128 + zl); bit 8: sign flip
   int nterms;               // <= 16
   double* partials;         // [grid][32]
   double* out;              // [nterms] (written by the last CTA)

@@ -577,9 +577,11 @@ __device__ __forceinline__ A warp_transpose_reduce16(A (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 // Double-float values: an unevaluated sum hi + lo of two FP32 numbers (about
-// 44 significant bits).  two_sum is Knuth's error-free addition, |x|^2 via the
-// FMA error-free product; used by the complex64 measurement table so that its
-// per-warp partial sums keep FP64-level accuracy before the FP64 accumulation.
+// 44 significant bits).  two_sum is Knuth's error-free addition.  The complex64
+// measurement table forms each |amp|^2 in FP32 (one FMA after a product:
+// relative error <= 2^-23) and sums them in double-float from there on -- the
+// warp tree and the run over tiles -- so the sums carry no error of their own
+// at FP32 scale, on the FP32 pipes (GB300's FP64 rate is 1/64 of FP32's).
 struct DF {
   float hi, lo;
 };
@@ -594,10 +596,6 @@ static __device__ __forceinline__ DF df_add(DF a, DF b) {
   const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
   const float h = __fadd_rn(s.hi, lo);  // renormalise (|s.hi| >= |lo|)
   return DF{h, __fsub_rn(lo, __fsub_rn(h, s.hi))};
-}
-static __device__ __forceinline__ DF df_abs2(float2 x) {
-  const float p = __fmul_rn(x.x, x.x), q = __fmul_rn(x.y, x.y);
-  return df_add(DF{p, __fmaf_rn(x.x, x.x, -p)}, DF{q, __fmaf_rn(x.y, x.y, -q)});
 }
 // warp_transpose_reduce16 on double-float values (same lane -> slot map)
 __device__ __forceinline__ DF warp_transpose_reduce16_df(DF (&v)[16], int lane) {
@@ -1070,6 +1068,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
     }
 
     double tacc = 0.0;  // this lane's measurement-table slot over the tiles (all group qubits in the tile)
+    DF tdf{0.f, 0.f};   // the same for complex64, in double-float
     // tiles this CTA read from / wrote to the state (thread 0 counts; grid passes report them)
     for (uint64_t u = ustart; u < nunits; u += ustep) {
       uint64_t tl[2] = {u, 0};
@@ -1239,17 +1238,34 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           uint32_t off[16];
           reg_offsets(sp.red_R, off);
           double r;
-          if constexpr (sizeof(T) == 4) {  // complex64: double-float partial sums
+          if constexpr (sizeof(T) == 4) {  // complex64: FP32 |amp|^2, double-float sums
             DF acc[16];
+            if constexpr (NGRP == PASS_THREADS) {  // one group per thread
+              const uint32_t b = group_base<GB>(sp.red_E, uint32_t(tid));
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = DF{0.f, 0.f};
-            for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
-              const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+              for (int j = 0; j < 16; ++j) {
+                const V x = tb[b ^ off[j]];
+                acc[j] = DF{__fmaf_rn(x.x, x.x, __fmul_rn(x.y, x.y)), 0.f};
+              }
+            } else {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) acc[j] = df_add(acc[j], df_abs2(tb[b ^ off[j]]));
+              for (int j = 0; j < 16; ++j) acc[j] = DF{0.f, 0.f};
+              for (int grp = tid; grp < NGRP; grp += PASS_THREADS) {
+                const uint32_t b = group_base<GB>(sp.red_E, uint32_t(grp));
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  const V x = tb[b ^ off[j]];
+                  acc[j] = df_add(acc[j], DF{__fmaf_rn(x.x, x.x, __fmul_rn(x.y, x.y)), 0.f});
+                }
+              }
             }
             const DF d = warp_transpose_reduce16_df(acc, lane);
-            r = double(d.hi) + double(d.lo);
+            if (sp.kin == sp.gk) {  // summed over the tiles in double-float, converted once per pass
+              if ((lane & 1) == 0) tdf = df_add(tdf, d);
+              r = 0.0;
+            } else {
+              r = double(d.hi) + double(d.lo);
+            }
           } else {  // complex128: FP64 throughout
             Acc acc[16];
 #pragma unroll
@@ -1266,9 +1282,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
           }
           if (sp.kin == sp.gk) {
             // every measured qubit is a tile qubit, so a lane's table slot is the
-            // same in every tile: lanes accumulate across tiles in FP64 (tile
-            // order) and the warps are combined once, after the tile loop
-            if ((lane & 1) == 0) tacc += r;
+            // same in every tile: lanes accumulate across tiles in FP64
+            // (complex64: double-float), in tile order, and the warps are
+            // combined once, after the tile loop
+            if constexpr (sizeof(T) != 4)
+              if ((lane & 1) == 0) tacc += r;
           } else {
             if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = r;
             __syncthreads();
@@ -1338,6 +1356,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& A, const int pi, PassS
       if (CTA || blockIdx.x == 0) atomicAdd(A.work + 4, 1ull);
     }
     if (needed && sp.kin == sp.gk) {  // the lanes' table slots, combined over warps in a fixed order
+      if constexpr (sizeof(T) == 4) tacc = double(tdf.hi) + double(tdf.lo);
       if ((lane & 1) == 0) sh.wsum[warp][transpose_slot(lane)] = tacc;
       __syncthreads();
       if (tid < 16) {

@@ -704,15 +704,20 @@ sv_status sv_expval(sv_state* h, const sv_pauli* terms, size_t n_terms, double* 
       a.x_mask = x;
       a.nterms = int(std::min<size_t>(svk::EXPVAL_TERMS, cnt - c));
       for (int t = 0; t < svk::EXPVAL_TERMS; ++t) {
-        a.zw[t] = 0xFFu;  // matches no lane
-        a.zh[t] = 0;
+        a.zw[t] = 0;  // unused slot: summed, never written out
+        a.zh7[t] = 0;
         if (t >= a.nterms) continue;
         const uint64_t z = terms[g[c + size_t(t)]].z_mask;
         uint32_t zl = 0, k = 0;
         for (int b = 0; b < 8; ++b)
           if ((lmask >> b) & 1) zl |= uint32_t((z >> b) & 1) << (k++);
-        a.zw[t] = zl | (uint32_t(__builtin_popcountll(x & z) & 3) << 8);
-        a.zh[t] = z & ~lmask;
+        // phase i^q of the term (q = |x & z| mod 4): odd q takes the imaginary
+        // part of the transform, q >= 2 flips the sign
+        const uint32_t q = uint32_t(__builtin_popcountll(x & z) & 3);
+        a.zw[t] = (zl + ((q & 1) ? 128u : 0u)) | ((q >> 1) << 8);
+        // bits of z above the block's index bits (bit hbit < 7 of the first
+        // index is always 0, so it drops out); n <= 34 keeps this in 32 bits
+        a.zh7[t] = uint32_t((z & ~lmask) >> 7);
       }
       a.partials = h->exp_partials.p;
       a.out = h->exp_out.p + slot + c;
