@@ -439,14 +439,25 @@ sv_status sv_grad_create(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, 
 sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_t n_params, double* dev_val,
                       double* dev_grad);
 sv_status sv_grad_destroy(sv_grad* g);
+/* 1 (default): sv_grad_run compiles, at its first call, a kernel specialised
+ * to this program (every gate, register position and shared-memory address a
+ * constant; the per-set matrices stay run-time data) and runs it; 0: the
+ * generic kernel, which reads the gate records at run time.  If the
+ * specialised kernel cannot be built the generic one runs.  SV_ERR_ARG for a
+ * null handle. */
+sv_status sv_grad_set_jit(sv_grad* g, int enable);
 /* Shape of the work of one parameter set (for throughput and roofline
  * accounting): forward and backward state passes, gates, Pauli term groups
  * (one gather of the state each while lambda = H psi is formed), terms, the
- * state's qubits after padding, and the parameter sets resident at once (one
- * per CTA).  SV_ERR_ARG for a null argument. */
+ * state's qubits after padding, the parameter sets resident at once (one per
+ * CTA, for the kernel the next run uses), whether that kernel is the
+ * specialised one, and its compile time in seconds.  SV_ERR_ARG for a null
+ * argument. */
 typedef struct sv_grad_stats {
   uint64_t forward_passes, backward_passes, gates;
   uint32_t term_groups, terms, state_qubits, resident_sets;
+  uint32_t specialised, pad;
+  double compile_seconds;
 } sv_grad_stats;
 sv_status sv_grad_info(const sv_grad* g, sv_grad_stats* out);
 sv_status sv_expval_grad_batch(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* params,

@@ -43,11 +43,15 @@ bool two_qubit(int op) {
          op == svp::OP_U4;
 }
 
-// one straight-line stage program per pass
-void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
+// one straight-line stage program per pass (struct <prefix><pass>).  Without
+// direct_ok the last stage of a direct pass writes the tile back to shared
+// memory like any other, behind a block barrier (kernels whose tile loop
+// stores from shared memory: the CTA-mode forward passes of the adjoint).
+void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi, const char* prefix = "JS",
+                 bool direct_ok = true) {
   const svp::DPass& d = P.passes[pi];
   const int GB = P.m - svp::REG_BITS;
-  o << "struct JS" << pi << " {\n"
+  o << "struct " << prefix << pi << " {\n"
     << "  template <typename T, int M, bool TC>\n"
     << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
@@ -99,7 +103,10 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     for (uint32_t g = st.g0; g < uint32_t(st.g0) + st.ng; ++g) {
       const svp::DGate& gt = P.gates[d.g0 + g];
       const char* fn = op_template(gt.op);
-      if (!fn) continue;
+      if (!fn) {  // a record kind without a template: the module fails to build (generic kernels run)
+        o << "#error gate record kind " << int(gt.op) << " has no template\n";
+        continue;
+      }
       std::ostringstream call;
       call << fn;
       if (gt.op == svp::OP_D16) call << "<T, M, TC>(a, smat + " << gt.mat << ", tb, tc)";
@@ -108,7 +115,8 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
       if (gt.flag >= 0) o << "      if (sgk[" << g << "] & SGK_ON) " << call.str() << ";\n";
       else o << "      " << call.str() << ";\n";
     }
-    if (d.direct && si + 1 == d.ns) {
+    const bool last = si + 1 == d.ns;
+    if (direct_ok && d.direct && last) {
       // direct store: register j of group grp is state index base ^ G(grp) ^ goff[j],
       // G and goff XORs of the qubits behind the group and register bits
       uint64_t goff[16];
@@ -135,7 +143,64 @@ void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi) {
     } else {
       for (int j = 0; j < 16; ++j) o << "      tb[b ^ " << off[j] << "u] = a[" << j << "];\n";
     }
-    o << "    }\n    " << (st.bar ? "__syncthreads();" : "__syncwarp();") << "\n";
+    const bool bar = st.bar || (!direct_ok && d.direct && last);
+    o << "    }\n    " << (bar ? "__syncthreads();" : "__syncwarp();") << "\n";
+  }
+  o << "  }\n};\n\n";
+}
+
+// Backward stage program of one adjoint pass (struct JSB<pass>): groups of 8
+// phi + 8 lambda amplitudes (register bit 3 selects phi / lambda), the gates'
+// templates and register positions, the derivative accumulations and every
+// shared-memory address as constants.
+void emit_bwd_stages(std::ostringstream& o, const svp::Plan& B, size_t bp) {
+  const svp::DPass& d = B.passes[bp];
+  const int GB = B.m - svp::ADJ_REG_BITS;
+  o << "struct JSB" << bp << " {\n"
+    << "  template <typename T, int M>\n"
+    << "  static __device__ __forceinline__ void run(const DPass& sp, const PassShared<T>& sh,\n"
+    << "                                             const uint16_t (&sdslot)[MAX_PASS_GATES],\n"
+    << "                                             typename CxT<T>::V* tphi, typename CxT<T>::V* tlam,\n"
+    << "                                             double (&wdot)[PASS_THREADS / 32][MAX_PASS_DOTS]) {\n"
+    << "    using V = typename CxT<T>::V;\n"
+    << "    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
+    << "    const V* smat = sh.smat;\n";
+  for (uint32_t si = 0; si < d.ns; ++si) {
+    const svp::DStage& st = B.stages[d.s0 + si];
+    uint32_t off[8];
+    off[0] = 0;
+    for (int j = 1; j < 8; ++j) off[j] = off[j & (j - 1)] ^ st.R[__builtin_ctz(unsigned(j))];
+    // the group loop stays rolled and each accumulation is fenced off from the
+    // gates around it: unrolled or interleaved, their registers spill at the
+    // 128 per thread of two CTAs per SM
+    o << "#pragma unroll 1\n    for (int grp = tid; grp < " << (1 << GB) << "; grp += " << svp::PASS_THREADS << ") {\n"
+      << "      uint32_t b = 0;\n";
+    for (int k = 0; k < GB; ++k) o << "      if (grp & " << (1 << k) << ") b ^= " << st.E[k] << "u;\n";
+    o << "      V a[16];\n";
+    for (int j = 0; j < 8; ++j)
+      o << "      a[" << j << "] = tphi[b ^ " << off[j] << "u]; a[" << j + 8 << "] = tlam[b ^ " << off[j] << "u];\n";
+    for (uint32_t g = st.g0; g < uint32_t(st.g0) + st.ng; ++g) {
+      const svp::DGate& gt = B.gates[d.g0 + g];
+      if (gt.op == svp::OP_DOT || gt.op == svp::OP_CDOT) {
+        o << "      asm volatile(\"\" ::: \"memory\");\n      { auto r = ";
+        if (gt.op == svp::OP_DOT) o << "g_dot<" << int(gt.p0) << ">(a, smat + " << gt.mat << ");";
+        else o << "g_cdot<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ");";
+        o << "\n#pragma unroll\n        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);\n"
+          << "        if (lane == 0) wdot[warp][" << gt.dslot << "] += double(r); }\n"
+          << "      asm volatile(\"\" ::: \"memory\");\n";
+        continue;
+      }
+      const char* fn = op_template(gt.op);
+      if (!fn || gt.op == svp::OP_D16) {  // not in backward plans; if it were, the module fails to build
+        o << "#error backward gate record kind " << int(gt.op) << " has no template\n";
+        continue;
+      }
+      if (two_qubit(gt.op)) o << "      " << fn << "<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ");\n";
+      else o << "      " << fn << "<" << int(gt.p0) << ">(a, smat + " << gt.mat << ");\n";
+    }
+    for (int j = 0; j < 8; ++j)
+      o << "      tphi[b ^ " << off[j] << "u] = a[" << j << "]; tlam[b ^ " << off[j] << "u] = a[" << j + 8 << "];\n";
+    o << "    }\n    __syncthreads();\n";
   }
   o << "  }\n};\n\n";
 }
@@ -151,6 +216,7 @@ struct Driver {
   CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
                            void**, void**) = nullptr;
   CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+  CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
   bool ok = false;
 };
 
@@ -171,7 +237,8 @@ const Driver& driver() {
   std::call_once(once, [] {
     d.ok = resolve("cuModuleLoadData", d.moduleLoadData) && resolve("cuModuleUnload", d.moduleUnload) &&
            resolve("cuModuleGetFunction", d.moduleGetFunction) && resolve("cuFuncSetAttribute", d.funcSetAttribute) &&
-           resolve("cuLaunchKernel", d.launchKernel) && resolve("cuGetErrorString", d.getErrorString);
+           resolve("cuLaunchKernel", d.launchKernel) && resolve("cuGetErrorString", d.getErrorString) &&
+           resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", d.occupancy);
   });
   return d;
 }
@@ -249,6 +316,50 @@ size_t chunk_count(const svp::Plan& P) {
 }
 
 std::string generate_source(const svp::Plan& P) { return generate_chunk(P, 0, P.passes.size()); }
+
+std::string generate_adjoint_source(const svp::Plan& F, const svp::Plan& B) {
+  std::ostringstream o;
+  const bool c64 = F.dtype == SV_C64;
+  o << "// specialised adjoint kernel: n = " << F.n_int << ", tile bits " << F.m << ", "
+    << (c64 ? "complex64" : "complex128") << ", " << F.passes.size() << " forward and " << B.passes.size()
+    << " backward passes\n"
+    << "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
+    << "typedef unsigned long long uint64_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+    << "typedef int int32_t;\ntypedef long long int64_t;\n"
+    << "#include \"adjoint_body.cuh\"\n\nnamespace svk {\n\n";
+  for (size_t pi = 0; pi < F.passes.size(); ++pi)
+    if (F.passes[pi].ns) emit_stages(o, F, pi, "JSF", false);
+  o << "struct JitFwd {\n"
+    << "  static constexpr bool kDirect = false;    // the CTA-mode tile loop stores from shared memory\n"
+    << "  static constexpr bool kFoldProj = false;  // adjoint programs measure nothing\n"
+    << "  template <typename T, int M, bool TC>\n"
+    << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
+    << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
+    << "                                             const bool fscale, const ProjFold& pj) {\n"
+    << "    switch (A.pass) {\n";
+  for (size_t pi = 0; pi < F.passes.size(); ++pi)
+    if (F.passes[pi].ns)
+      o << "      case " << pi << ": JSF" << pi << "::run<T, M, TC>(A, sp, sgk, smat, tb, tc, base, fT, fscale, pj); break;\n";
+  o << "      default: break;\n    }\n  }\n};\n\n";
+  for (size_t bp = 0; bp < B.passes.size(); ++bp)
+    if (B.passes[bp].ns) emit_bwd_stages(o, B, bp);
+  o << "struct JitBwd {\n"
+    << "  template <typename T, int M>\n"
+    << "  static __device__ __forceinline__ void run(const DStage*, uint32_t bp, const DPass& sp, const PassShared<T>& sh,\n"
+    << "                                             const uint16_t (&sdslot)[MAX_PASS_GATES],\n"
+    << "                                             typename CxT<T>::V* tphi, typename CxT<T>::V* tlam,\n"
+    << "                                             double (&wdot)[PASS_THREADS / 32][MAX_PASS_DOTS]) {\n"
+    << "    switch (bp) {\n";
+  for (size_t bp = 0; bp < B.passes.size(); ++bp)
+    if (B.passes[bp].ns) o << "      case " << bp << ": JSB" << bp << "::run<T, M>(sp, sh, sdslot, tphi, tlam, wdot); break;\n";
+  o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
+  const char* T = c64 ? "float" : "double";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1)
+    << ") sv_jit_adjoint(const svk::AdjArgs J) {\n"
+    << "  svk::adjoint_body<" << T << ", " << F.m << ", svk::JitFwd, svk::JitBwd>(J);\n}\n";
+  return o.str();
+}
 
 namespace {
 
@@ -392,6 +503,75 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 64) cache.clear();
   cache[key] = out;
+  return SV_OK;
+}
+
+JitAdjoint::~JitAdjoint() {
+  if (module && driver().moduleUnload) driver().moduleUnload(static_cast<CUmodule>(module));
+}
+
+sv_status compile_adjoint(const svp::Plan& F, const svp::Plan& B, size_t smem, std::shared_ptr<JitAdjoint>& out,
+                          std::string& err) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, std::shared_ptr<JitAdjoint>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::string src = generate_adjoint_source(F, B);
+  const auto key = std::make_pair(dev, std::hash<std::string>{}(src + "/" + std::to_string(smem)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      out = it->second;
+      return SV_OK;
+    }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<char> cubin;
+  sv_status st = compile_source(src, cubin, err);
+  if (st != SV_OK) return st;
+  const Driver& D = driver();
+  if (!D.ok) {
+    err = "CUDA driver entry points unavailable";
+    return SV_ERR_CUDA;
+  }
+  std::unique_ptr<JitAdjoint> J(new JitAdjoint());
+  CUmodule mod;
+  CUresult r = D.moduleLoadData(&mod, cubin.data());
+  if (r != CUDA_SUCCESS) {
+    err = "cuModuleLoadData: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  J->module = mod;
+  CUfunction fn;
+  r = D.moduleGetFunction(&fn, mod, "sv_jit_adjoint");
+  if (r == CUDA_SUCCESS) r = D.funcSetAttribute(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(smem));
+  int per_sm = 0;
+  if (r == CUDA_SUCCESS) r = D.occupancy(&per_sm, fn, svp::PASS_THREADS, smem);
+  if (r != CUDA_SUCCESS) {
+    err = "loading the specialised adjoint kernel: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  J->fn = fn;
+  J->smem = smem;
+  J->per_sm = per_sm > 0 ? per_sm : 1;
+  J->compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out = std::shared_ptr<JitAdjoint>(std::move(J));
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() > 64) cache.clear();
+  cache[key] = out;
+  return SV_OK;
+}
+
+sv_status launch_adjoint(const JitAdjoint& J, const svk::AdjArgs& a, int grid, cudaStream_t s, std::string& err) {
+  svk::AdjArgs b = a;
+  void* args[] = {&b};
+  const CUresult r = driver().launchKernel(static_cast<CUfunction>(J.fn), unsigned(grid), 1, 1, svp::PASS_THREADS, 1,
+                                           1, unsigned(J.smem), reinterpret_cast<CUstream>(s), args, nullptr);
+  if (r != CUDA_SUCCESS) {
+    err = "specialised adjoint launch: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
   return SV_OK;
 }
 

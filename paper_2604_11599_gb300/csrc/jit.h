@@ -44,4 +44,22 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
 
 sv_status launch(const JitModule& J, int pass, const svk::PassArgs& a, int grid, cudaStream_t s, std::string& err);
 
+// The batched adjoint kernel specialised to one program: its forward passes'
+// stage programs (CTA mode) and its backward passes' (phi / lambda groups,
+// derivative accumulations) with every gate, register position and address a
+// constant; the per-set matrices stay run-time data.
+struct JitAdjoint {
+  void* module = nullptr;  // CUmodule
+  void* fn = nullptr;      // CUfunction sv_jit_adjoint
+  size_t smem = 0;         // dynamic shared memory per launch
+  int per_sm = 1;          // resident CTAs per SM (occupancy of the compiled kernel)
+  double compile_seconds = 0;
+  ~JitAdjoint();
+};
+std::string generate_adjoint_source(const svp::Plan& F, const svp::Plan& B);
+// compiled and loaded; cached for the process by device, source and shared-memory size
+sv_status compile_adjoint(const svp::Plan& F, const svp::Plan& B, size_t smem, std::shared_ptr<JitAdjoint>& out,
+                          std::string& err);
+sv_status launch_adjoint(const JitAdjoint& J, const svk::AdjArgs& a, int grid, cudaStream_t s, std::string& err);
+
 }  // namespace svj

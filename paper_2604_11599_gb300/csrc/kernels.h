@@ -181,6 +181,7 @@ cudaError_t launch_adjoint(int dtype, const AdjArgs& a, int grid, cudaStream_t s
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t adjoint_occupancy(int dtype, uint32_t nterms, int* blocks_per_sm);
+size_t adjoint_smem_bytes(int dtype, uint32_t nterms);  // dynamic shared memory of an adjoint launch
 #endif
 
 // terminal sampling: run sums and in-block prefixes -> block scan -> per-shot search
@@ -204,8 +205,9 @@ uint64_t sample_runs(int n);
 
 // Pauli expectation values of one group of terms sharing an X mask.  The
 // terms travel in the kernel's parameter block (warp-uniform operands): for
-// term t, zw[t] = zl | phase << 8 (zl: its Z mask on the seven index bits a
-// 128-pair block spans, phase = |x & z| mod 4) and zh[t] = the rest of its Z mask.
+// term t with phase q = |x & z| mod 4 and zl its Z mask on the seven index bits
+// a 128-pair block spans, zw[t] = (zl, or 128 + zl for odd q) | (q >> 1) << 8,
+// and zh7[t] = the rest of its Z mask shifted down by 7.
 constexpr int EXPVAL_TERMS = 16;
 struct ExpvalArgs {
   const void* state;

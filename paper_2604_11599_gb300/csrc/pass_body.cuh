@@ -246,7 +246,7 @@ __device__ __forceinline__ void d16_build_b(const V* m, TcShared& s, int slot) {
   for (int e = threadIdx.x; e < 256; e += PASS_THREADS) {  // entries (2r + i, 2c + j) from U[r][c] = m[16 r + c]
     const int r = e >> 4, c = e & 15;
     const V u = m[e];
-    const float v[4] = {u.x, -u.y, u.y, u.x};
+    const float v[4] = {float(u.x), float(-u.y), float(u.y), float(u.x)};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint32_t off = cm_off(uint32_t(2 * r + (q >> 1)), uint32_t(2 * c + (q & 1)));

@@ -1159,6 +1159,9 @@ struct sv_grad {
   DevBuf<Ctrl> ctrls;
   DevBuf<uint8_t> fslots;
   DevBuf<unsigned> queue;
+  bool use_jit = true;                     // the kernel specialised to this program (sv_grad_set_jit)
+  bool jit_tried = false;
+  std::shared_ptr<svj::JitAdjoint> jit;    // compiled at the first run; null: the generic kernel runs
 };
 
 extern "C" {
@@ -1246,7 +1249,15 @@ sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_
   if (g->fmats.reserve(n_sets * fstride * g->amp_bytes) != cudaSuccess ||
       g->bmats.reserve(n_sets * bstride * g->amp_bytes) != cudaSuccess)
     return fail(SV_ERR_OOM, "per-set gate matrices");
-  const int grid = int(std::min<size_t>(size_t(g->grid), n_sets));
+  if (g->use_jit && !g->jit_tried) {
+    g->jit_tried = true;
+    std::string err;
+    if (svj::compile_adjoint(F, B, svk::adjoint_smem_bytes(g->dtype, g->nterms), g->jit, err) != SV_OK)
+      g->jit.reset();  // the generic kernel remains
+  }
+  const svj::JitAdjoint* jk = g->use_jit ? g->jit.get() : nullptr;
+  const int resident = jk ? g->sms * jk->per_sm : g->grid;
+  const int grid = int(std::min<size_t>(size_t(resident), n_sets));
   const uint64_t slot = 1ull << F.n_int;
   if (g->slots.reserve(size_t(grid) * 2 * slot * g->amp_bytes) != cudaSuccess)
     return fail(SV_ERR_OOM, "phi / lambda work space");
@@ -1300,7 +1311,19 @@ sv_status sv_grad_run(sv_grad* g, const double* dev_params, size_t n_sets, size_
   a.n_int = F.n_int;
   a.val_out = dev_val;
   a.grad_out = dev_grad;
+  if (jk) {
+    std::string err;
+    const sv_status st = svj::launch_adjoint(*jk, a, grid, s, err);
+    if (st != SV_OK) return fail(st, err);
+    return SV_OK;
+  }
   SV_CUDA(svk::launch_adjoint(g->dtype, a, grid, s));
+  return SV_OK;
+}
+
+sv_status sv_grad_set_jit(sv_grad* g, int enable) {
+  if (!g) return fail(SV_ERR_ARG, "null handle");
+  g->use_jit = enable != 0;
   return SV_OK;
 }
 
@@ -1312,7 +1335,11 @@ sv_status sv_grad_info(const sv_grad* g, sv_grad_stats* out) {
   out->term_groups = g->ngroups;
   out->terms = g->nterms;
   out->state_qubits = uint32_t(g->fwd.plan.n_int);
-  out->resident_sets = uint32_t(g->grid);
+  const svj::JitAdjoint* jk = g->use_jit ? g->jit.get() : nullptr;
+  out->resident_sets = uint32_t(jk ? g->sms * jk->per_sm : g->grid);
+  out->specialised = jk ? 1u : 0u;
+  out->pad = 0;
+  out->compile_seconds = jk ? jk->compile_seconds : 0.0;
   return SV_OK;
 }
 

@@ -52,7 +52,8 @@ class WorkCounts(C.Structure):
 class GradStats(C.Structure):
     _fields_ = [("forward_passes", C.c_uint64), ("backward_passes", C.c_uint64), ("gates", C.c_uint64),
                 ("term_groups", C.c_uint32), ("terms", C.c_uint32), ("state_qubits", C.c_uint32),
-                ("resident_sets", C.c_uint32)]
+                ("resident_sets", C.c_uint32), ("specialised", C.c_uint32), ("pad", C.c_uint32),
+                ("compile_seconds", C.c_double)]
 
 
 class BranchStats(C.Structure):
@@ -126,6 +127,7 @@ def lib():
         "sv_grad_create": ([i32, i32, vp, sz, vp, sz, vp, sz, vp, C.POINTER(vp)], st),
         "sv_grad_run": ([vp, vp, sz, sz, vp, vp], st),
         "sv_grad_destroy": ([vp], st),
+        "sv_grad_set_jit": ([vp, i32], st),
         "sv_expval_grad_batch": ([i32, i32, vp, sz, vp, sz, sz, vp, sz, vp, vp, vp], st),
         "sv_last_error": ([], C.c_char_p),
         "sv_version": ([], C.c_char_p),
@@ -554,11 +556,18 @@ class Grad:
         _check(lib().sv_grad_run(self._h, params.data_ptr(), P, n_params, val.data_ptr(), grad.data_ptr()))
         return val, grad
 
+    def set_jit(self, on: bool = True) -> None:
+        """Specialised kernel for this program (default) or the generic one."""
+        _check(lib().sv_grad_set_jit(self._h, 1 if on else 0))
+
     def info(self) -> dict:
-        """Passes, gates, term groups and resident sets of one parameter set's work."""
+        """Passes, gates, term groups and resident sets of one parameter set's
+        work; whether the specialised kernel runs, and its compile seconds."""
         g = GradStats()
         _check(lib().sv_grad_info(self._h, C.byref(g)))
-        return {k: int(getattr(g, k)) for k, _ in GradStats._fields_}
+        out = {k: int(getattr(g, k)) for k, _ in GradStats._fields_ if k not in ("pad", "compile_seconds")}
+        out["compile_seconds"] = float(g.compile_seconds)
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -82,11 +82,19 @@ def test_general_gates_shared_and_scaled_params(svmod, orc, dtype):
 
     val, grad = h.run(torch.tensor(params, device="cuda"))
     val, grad = val.cpu().numpy(), grad.cpu().numpy()
+    assert h.info()["specialised"] == 1  # the kernel specialised to this program ran
+    # the generic kernel (gate records read at run time) on the same sets
+    h.set_jit(False)
+    val_g, grad_g = h.run(torch.tensor(params, device="cuda"))
+    assert h.info()["specialised"] == 0
+    val_g, grad_g = val_g.cpu().numpy(), grad_g.cpu().numpy()
     for s in range(len(params)):
-        assert abs(val[s] - orc.energy(c.ops, n, params[s], terms, c.pool)) <= TOL[dtype] * scale
+        e = orc.energy(c.ops, n, params[s], terms, c.pool)
         g = stencil_grad(orc, c.ops, n, params[s], terms, c.pool)
         tol = max(TOL[dtype], 1e-9) * scale
-        assert np.max(np.abs(grad[s] - g)) <= tol, np.max(np.abs(grad[s] - g))
+        for v, gr in ((val, grad), (val_g, grad_g)):
+            assert abs(v[s] - e) <= TOL[dtype] * scale
+            assert np.max(np.abs(gr[s] - g)) <= tol, np.max(np.abs(gr[s] - g))
 
 
 def test_autograd_backward(svmod):
