@@ -190,8 +190,13 @@ void emit_bwd_stages(std::ostringstream& o, const svp::Plan& B, size_t bp) {
           << "      asm volatile(\"\" ::: \"memory\");\n";
         continue;
       }
+      if (gt.op == svp::OP_D16) {  // a 16 x 16 on all four register bits (three-qubit dense gates: block diagonal)
+        o << "      asm volatile(\"\" ::: \"memory\");\n      g_d16(a, smat + " << gt.mat
+          << ");\n      asm volatile(\"\" ::: \"memory\");\n";
+        continue;
+      }
       const char* fn = op_template(gt.op);
-      if (!fn || gt.op == svp::OP_D16) {  // not in backward plans; if it were, the module fails to build
+      if (!fn) {  // a record kind without a template: the module fails to build (the generic kernel runs)
         o << "#error backward gate record kind " << int(gt.op) << " has no template\n";
         continue;
       }
