@@ -61,6 +61,26 @@ __device__ __forceinline__ double lambda_h(const AdjArgs& J, const typename CxT<
   return e;
 }
 
+// Per-warp derivative accumulators of a backward pass (one per accumulation
+// slot): complex64 in double-float on the FP32 pipes (a conversion and an FP64
+// add per warp per group would bind the backward passes to GB300's FP64
+// rate), complex128 in FP64.
+template <typename T> struct DotAcc;
+template <> struct DotAcc<float> {
+  using type = DF;
+  static __device__ __forceinline__ void add(DF& a, float r) { a = df_add(a, DF{r, 0.f}); }
+  static __device__ __forceinline__ double get(const DF& a) { return double(a.hi) + double(a.lo); }
+  static __device__ __forceinline__ DF zero() { return DF{0.f, 0.f}; }
+};
+template <> struct DotAcc<double> {
+  using type = double;
+  static __device__ __forceinline__ void add(double& a, double r) { a += r; }
+  static __device__ __forceinline__ double get(const double& a) { return a; }
+  static __device__ __forceinline__ double zero() { return 0.0; }
+};
+template <typename T>
+using DotRows = typename DotAcc<T>::type[PASS_THREADS / 32][MAX_PASS_DOTS];
+
 // Backward stage program of the generic kernel: for each stage of backward
 // pass bp, the groups of 8 phi + 8 lambda amplitudes in registers, the gate
 // records (U^dagger on both halves at once: register bit 3 selects phi or
@@ -71,7 +91,7 @@ struct GenericBwd {
   static __device__ __forceinline__ void run(const DStage* stages, uint32_t, const DPass& sp, const PassShared<T>& sh,
                                              const uint16_t (&sdslot)[MAX_PASS_GATES], typename CxT<T>::V* tphi,
                                              typename CxT<T>::V* tlam,
-                                             double (&wdot)[PASS_THREADS / 32][MAX_PASS_DOTS]) {
+                                             DotRows<T>& wdot) {
     using V = typename CxT<T>::V;
     using Acc = T;
     constexpr int GB = M - ADJ_REG_BITS;
@@ -100,7 +120,7 @@ struct GenericBwd {
             Acc r = apply_dot(a, key, mt);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-            if (lane == 0) wdot[warp][sdslot[g]] += double(r);
+            if (lane == 0) DotAcc<T>::add(wdot[warp][sdslot[g]], r);
           } else {
             apply_gate(a, key, mt);
           }
@@ -129,7 +149,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassShared<T> sh;
   __shared__ double gacc[MAX_ADJ_PARAMS];
-  __shared__ double wdot[PASS_THREADS / 32][MAX_PASS_DOTS];
+  __shared__ DotRows<T> wdot;
   __shared__ uint16_t sdslot[MAX_PASS_GATES];
   __shared__ uint32_t sdotg[MAX_PASS_DOTS];
   __shared__ double ered[PASS_THREADS / 32];
@@ -221,7 +241,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs J) {
         if (d.op == OP_DOT || d.op == OP_CDOT) sdotg[d.dslot] = d.gidx;
       }
       for (int i = tid; i < int(sp.nmat); i += PASS_THREADS) sh.smat[i] = bm[sp.mat0 + i];
-      for (int i = tid; i < (PASS_THREADS / 32) * MAX_PASS_DOTS; i += PASS_THREADS) (&wdot[0][0])[i] = 0.0;
+      for (int i = tid; i < (PASS_THREADS / 32) * MAX_PASS_DOTS; i += PASS_THREADS) (&wdot[0][0])[i] = DotAcc<T>::zero();
       const int hb = M - L;
       for (int c = tid; c < (1 << hb); c += PASS_THREADS) {
         uint64_t o = 0;
@@ -278,7 +298,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs J) {
       if (tid == 0)
         for (uint32_t d = 0; d < ndots; ++d) {
           double s = 0;
-          for (int w = 0; w < PASS_THREADS / 32; ++w) s += wdot[w][d];
+          for (int w = 0; w < PASS_THREADS / 32; ++w) s += DotAcc<T>::get(wdot[w][d]);
           gacc[sdotg[d]] += s;
         }
       __syncthreads();

@@ -161,7 +161,7 @@ void emit_bwd_stages(std::ostringstream& o, const svp::Plan& B, size_t bp) {
     << "  static __device__ __forceinline__ void run(const DPass& sp, const PassShared<T>& sh,\n"
     << "                                             const uint16_t (&sdslot)[MAX_PASS_GATES],\n"
     << "                                             typename CxT<T>::V* tphi, typename CxT<T>::V* tlam,\n"
-    << "                                             double (&wdot)[PASS_THREADS / 32][MAX_PASS_DOTS]) {\n"
+    << "                                             DotRows<T>& wdot) {\n"
     << "    using V = typename CxT<T>::V;\n"
     << "    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;\n"
     << "    const V* smat = sh.smat;\n";
@@ -186,7 +186,7 @@ void emit_bwd_stages(std::ostringstream& o, const svp::Plan& B, size_t bp) {
         if (gt.op == svp::OP_DOT) o << "g_dot<" << int(gt.p0) << ">(a, smat + " << gt.mat << ");";
         else o << "g_cdot<" << int(gt.p0) << ", " << int(gt.p1) << ">(a, smat + " << gt.mat << ");";
         o << "\n#pragma unroll\n        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);\n"
-          << "        if (lane == 0) wdot[warp][" << gt.dslot << "] += double(r); }\n"
+          << "        if (lane == 0) DotAcc<T>::add(wdot[warp][" << gt.dslot << "], r); }\n"
           << "      asm volatile(\"\" ::: \"memory\");\n";
         continue;
       }
@@ -354,7 +354,7 @@ std::string generate_adjoint_source(const svp::Plan& F, const svp::Plan& B) {
     << "  static __device__ __forceinline__ void run(const DStage*, uint32_t bp, const DPass& sp, const PassShared<T>& sh,\n"
     << "                                             const uint16_t (&sdslot)[MAX_PASS_GATES],\n"
     << "                                             typename CxT<T>::V* tphi, typename CxT<T>::V* tlam,\n"
-    << "                                             double (&wdot)[PASS_THREADS / 32][MAX_PASS_DOTS]) {\n"
+    << "                                             DotRows<T>& wdot) {\n"
     << "    switch (bp) {\n";
   for (size_t bp = 0; bp < B.passes.size(); ++bp)
     if (B.passes[bp].ns) o << "      case " << bp << ": JSB" << bp << "::run<T, M>(sp, sh, sdslot, tphi, tlam, wdot); break;\n";
