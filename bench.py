@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--form", default=None, choices=["batching", "adjoint", "sample_expval"],
                     help="run only this auxiliary measurement (for profiling) and print its JSON")
     ap.add_argument("--items", type=int, default=65536, help="--form batching: trajectories")
+    ap.add_argument("--jit", action="store_true", help="--form batching: the kernel specialised to the programs")
     ap.add_argument("--sets", type=int, default=1024, help="--form adjoint: parameter sets")
     ap.add_argument("--tile-bits", type=int, default=0, help="qubits per shared-memory tile (0: default 12)")
     ap.add_argument("--low-bits", type=int, default=0, help="contiguous low qubits per tile (0: default 4)")
@@ -635,6 +636,7 @@ def single_form(args):
     if args.form == "batching":
         wl = W.batching(seed=6, n_traj=args.items)
         with sv.Batch("c64") as b:
+            b.set_jit(args.jit)
             pid = {n: b.add_program(c.ops, n + 1) for n, c in wl.circuits.items()}
             ids = np.array([pid[int(n)] for n in wl.traj_n])
             b.set_items(ids, np.arange(len(ids)), np.zeros(len(ids)))
@@ -643,7 +645,9 @@ def single_form(args):
                 b.launch(0)
                 b.results()
                 dt = time.perf_counter() - t0
-        out.update({"trajectories": args.items, "seconds": dt, "trajectories_per_s": args.items / dt})
+            ji = b.jit_info()
+        out.update({"trajectories": args.items, "seconds": dt, "trajectories_per_s": args.items / dt,
+                    "specialised": ji["specialised"], "compile_seconds": ji["compile_seconds"]})
     elif args.form == "adjoint":
         c = W.hea(20, 8)
         terms = W.heisenberg_fields(9, 20, 200)

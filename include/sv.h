@@ -515,6 +515,19 @@ sv_status sv_profile_work(sv_state* h, sv_work_counts* out);
 sv_status sv_batch_profile(sv_batch* b, int enable);
 sv_status sv_batch_work(sv_batch* b, sv_work_counts* out);
 
+/* 1: launches run a kernel specialised to the handle's programs (every gate,
+ * register position and shared-memory address of every pass a constant; the
+ * per-program matrices and flags stay run-time data), compiled at the first
+ * launch after programs were added (seconds for a handful of programs; suited
+ * to a fixed program set run many times, not to a serving loop that adds
+ * programs as requests arrive); if it cannot be built the generic kernel
+ * runs.  0 (default): the generic kernel, which reads the gate records at run
+ * time.  sv_batch_jit_info: whether the next launch runs the specialised
+ * kernel (built and current) and its compile time.  SV_ERR_ARG for a null
+ * handle. */
+sv_status sv_batch_set_jit(sv_batch* b, int enable);
+sv_status sv_batch_jit_info(sv_batch* b, int* specialised, double* compile_seconds);
+
 /*
  * Self test of the failure path of bounded device waits (the tensor-core
  * completion wait of the sweep kernels).  Runs that same wait -- mbarrier

@@ -20,11 +20,12 @@ SOURCES = ["kern_pass.cu", "kern_measure.cu", "kern_batch.cu", "kern_adjoint.cu"
            "expval_static.cu", "jit.cpp", "kern_branch.cu", "kern_clifford.cu"]
 # headers compiled again at run time by the pass specialiser (jit.cpp); embedded as strings
 JIT_HEADERS = [("pass_body.cuh", "csrc/pass_body.cuh"), ("adjoint_body.cuh", "csrc/adjoint_body.cuh"),
+               ("batch_body.cuh", "csrc/batch_body.cuh"),
                ("dev_common.cuh", "csrc/dev_common.cuh"),
                ("dev_tc.cuh", "csrc/dev_tc.cuh"),
                ("kernels.h", "csrc/kernels.h"), ("sv_plan.h", "csrc/sv_plan.h"),
                ("../../include/sv.h", "../include/sv.h")]
-HEADERS = ["sv_plan.h", "kernels.h", "planner.h", "dev_common.cuh", "dev_tc.cuh", "pass_body.cuh", "adjoint_body.cuh",
+HEADERS = ["sv_plan.h", "kernels.h", "planner.h", "dev_common.cuh", "dev_tc.cuh", "pass_body.cuh", "adjoint_body.cuh", "batch_body.cuh",
            "jit.h",
            "branch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

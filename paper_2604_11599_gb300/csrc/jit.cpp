@@ -48,12 +48,13 @@ bool two_qubit(int op) {
 // memory like any other, behind a block barrier (kernels whose tile loop
 // stores from shared memory: the CTA-mode forward passes of the adjoint).
 void emit_stages(std::ostringstream& o, const svp::Plan& P, size_t pi, const char* prefix = "JS",
-                 bool direct_ok = true) {
+                 bool direct_ok = true, bool inline_run = true) {
   const svp::DPass& d = P.passes[pi];
   const int GB = P.m - svp::REG_BITS;
   o << "struct " << prefix << pi << " {\n"
     << "  template <typename T, int M, bool TC>\n"
-    << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
+    << "  static __device__ " << (inline_run ? "__forceinline__" : "__noinline__")
+    << " void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
     << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
     << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
     << "                                             const bool fscale, const ProjFold& pj) {\n"
@@ -322,6 +323,47 @@ size_t chunk_count(const svp::Plan& P) {
 
 std::string generate_source(const svp::Plan& P) { return generate_chunk(P, 0, P.passes.size()); }
 
+std::string generate_batch_source(const std::vector<const svp::Plan*>& plans) {
+  std::ostringstream o;
+  const bool c64 = plans.front()->dtype == SV_C64;
+  const int m = plans.front()->m;
+  o << "// specialised batch kernel: " << plans.size() << " programs, tile bits " << m << ", "
+    << (c64 ? "complex64" : "complex128") << "\n"
+    << "typedef unsigned char uint8_t;\ntypedef unsigned short uint16_t;\ntypedef unsigned int uint32_t;\n"
+    << "typedef unsigned long long uint64_t;\ntypedef signed char int8_t;\ntypedef short int16_t;\n"
+    << "typedef int int32_t;\ntypedef long long int64_t;\n"
+    << "#include \"batch_body.cuh\"\n\nnamespace svk {\n\n";
+  std::vector<std::string> cases;
+  size_t base = 0;
+  for (size_t k = 0; k < plans.size(); ++k) {
+    const svp::Plan& P = *plans[k];
+    const std::string prefix = "JSP" + std::to_string(k) + "_";
+    for (size_t pi = 0; pi < P.passes.size(); ++pi)
+      if (P.passes[pi].ns) {
+        // one function per pass: a module of hundreds of inlined passes takes ptxas minutes
+        emit_stages(o, P, pi, prefix.c_str(), false, false);
+        cases.push_back("      case " + std::to_string(base + pi) + ": " + prefix + std::to_string(pi) +
+                        "::run<T, M, TC>(A, sp, sgk, smat, tb, tc, base, fT, fscale, pj); break;\n");
+      }
+    base += P.passes.size();
+  }
+  o << "struct JitBatch {\n"
+    << "  static constexpr bool kDirect = false;    // the CTA-mode tile loop stores from shared memory\n"
+    << "  static constexpr bool kFoldProj = false;  // the CTA-mode tile loop applies a pending projector\n"
+    << "  template <typename T, int M, bool TC>\n"
+    << "  static __device__ __forceinline__ void run(const PassArgs& A, const DPass& sp, const uint32_t* sgk,\n"
+    << "                                             const typename CxT<T>::V* smat, typename CxT<T>::V* tb,\n"
+    << "                                             TcCtx& tc, const uint64_t base, const typename CxT<T>::V fT,\n"
+    << "                                             const bool fscale, const ProjFold& pj) {\n"
+    << "    switch (A.pass) {\n";
+  for (const std::string& c : cases) o << c;
+  o << "      default: break;\n    }\n  }\n};\n\n}  // namespace svk\n\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << svp::PASS_THREADS << ", " << (c64 ? 2 : 1)
+    << ") sv_jit_batch(const svk::BatchArgs B) {\n"
+    << "  svk::batch_body<" << (c64 ? "float" : "double") << ", " << m << ", svk::JitBatch>(B);\n}\n";
+  return o.str();
+}
+
 std::string generate_adjoint_source(const svp::Plan& F, const svp::Plan& B) {
   std::ostringstream o;
   const bool c64 = F.dtype == SV_C64;
@@ -566,6 +608,86 @@ sv_status compile_adjoint(const svp::Plan& F, const svp::Plan& B, size_t smem, s
   if (cache.size() > 64) cache.clear();
   cache[key] = out;
   return SV_OK;
+}
+
+// one module holding one kernel: compiled, loaded, its dynamic shared memory
+// set and its occupancy read
+sv_status load_single(const std::string& src, const char* name, size_t smem, JitKernel& K, std::string& err) {
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<char> cubin;
+  sv_status st = compile_source(src, cubin, err);
+  if (st != SV_OK) return st;
+  const Driver& D = driver();
+  if (!D.ok) {
+    err = "CUDA driver entry points unavailable";
+    return SV_ERR_CUDA;
+  }
+  CUmodule mod;
+  CUresult r = D.moduleLoadData(&mod, cubin.data());
+  if (r != CUDA_SUCCESS) {
+    err = "cuModuleLoadData: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  K.module = mod;
+  CUfunction fn;
+  r = D.moduleGetFunction(&fn, mod, name);
+  if (r == CUDA_SUCCESS) r = D.funcSetAttribute(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, int(smem));
+  int per_sm = 0;
+  if (r == CUDA_SUCCESS) r = D.occupancy(&per_sm, fn, svp::PASS_THREADS, smem);
+  if (r != CUDA_SUCCESS) {
+    err = std::string("loading ") + name + ": " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  K.fn = fn;
+  K.smem = smem;
+  K.per_sm = per_sm > 0 ? per_sm : 1;
+  K.compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SV_OK;
+}
+
+sv_status compile_batch(const std::vector<const svp::Plan*>& plans, size_t smem, std::shared_ptr<JitKernel>& out,
+                        std::string& err) {
+  if (plans.empty()) {
+    err = "no programs";
+    return SV_ERR_ARG;
+  }
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, std::shared_ptr<JitKernel>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::string src = generate_batch_source(plans);
+  const auto key = std::make_pair(dev, std::hash<std::string>{}(src + "/" + std::to_string(smem)));
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      out = it->second;
+      return SV_OK;
+    }
+  }
+  std::shared_ptr<JitKernel> K(new JitKernel());
+  const sv_status st = load_single(src, "sv_jit_batch", smem, *K, err);
+  if (st != SV_OK) return st;
+  out = K;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() > 16) cache.clear();
+  cache[key] = out;
+  return SV_OK;
+}
+
+sv_status launch_single(const JitKernel& K, void* args, int grid, cudaStream_t s, std::string& err) {
+  void* params[] = {args};
+  const CUresult r = driver().launchKernel(static_cast<CUfunction>(K.fn), unsigned(grid), 1, 1, svp::PASS_THREADS, 1,
+                                           1, unsigned(K.smem), reinterpret_cast<CUstream>(s), params, nullptr);
+  if (r != CUDA_SUCCESS) {
+    err = "specialised kernel launch: " + cu_err(r);
+    return SV_ERR_CUDA;
+  }
+  return SV_OK;
+}
+
+JitKernel::~JitKernel() {
+  if (module && driver().moduleUnload) driver().moduleUnload(static_cast<CUmodule>(module));
 }
 
 sv_status launch_adjoint(const JitAdjoint& J, const svk::AdjArgs& a, int grid, cudaStream_t s, std::string& err) {

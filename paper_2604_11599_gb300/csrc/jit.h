@@ -62,4 +62,23 @@ sv_status compile_adjoint(const svp::Plan& F, const svp::Plan& B, size_t smem, s
                           std::string& err);
 sv_status launch_adjoint(const JitAdjoint& J, const svk::AdjArgs& a, int grid, cudaStream_t s, std::string& err);
 
+// One specialised kernel in its own module.
+struct JitKernel {
+  void* module = nullptr;  // CUmodule
+  void* fn = nullptr;      // CUfunction
+  size_t smem = 0;         // dynamic shared memory per launch
+  int per_sm = 1;          // resident CTAs per SM
+  double compile_seconds = 0;
+  ~JitKernel();
+};
+// The batched kernel specialised to a batch's programs (in the order given):
+// each program's passes get their stage programs, numbered consecutively
+// (BatchProg::jit_base is a program's first number).  Cached for the process by
+// device, source and shared-memory size.
+std::string generate_batch_source(const std::vector<const svp::Plan*>& plans);
+sv_status compile_batch(const std::vector<const svp::Plan*>& plans, size_t smem, std::shared_ptr<JitKernel>& out,
+                        std::string& err);
+// args: the address of the kernel's single parameter (e.g. an svk::BatchArgs)
+sv_status launch_single(const JitKernel& K, void* args, int grid, cudaStream_t s, std::string& err);
+
 }  // namespace svj

@@ -87,6 +87,8 @@ struct BatchProg {
   const void* mats;
   const svp::DScalar* init;
   uint32_t npasses, ninit;
+  uint32_t jit_base;  // specialised batch kernels: the program's first pass in the module's pass numbering
+  uint32_t pad;
 };
 
 struct BatchItem {
@@ -124,6 +126,7 @@ cudaError_t launch_batch(int dtype, const BatchArgs& a, int grid, cudaStream_t s
 #endif
 #ifndef __CUDACC_RTC__
 cudaError_t batch_occupancy(int dtype, int* blocks_per_sm);
+size_t batch_smem_bytes(int dtype);  // dynamic shared memory of a batch launch
 #endif
 
 // the walk over the shots of one or more requests (kern_branch.cu)

@@ -772,6 +772,9 @@ struct sv_batch {
   int tune_low = 0, tune_gates = 0;           // planner tuning of programs added from now on (0: default)
   DevBuf<unsigned long long> work;            // device work counters while profiling (sv_batch_profile)
   bool profiling = false;
+  bool use_jit = false;                       // the kernel specialised to the batch's programs (sv_batch_set_jit)
+  std::shared_ptr<svj::JitKernel> jit;        // built for the first jit_nprogs programs
+  size_t jit_nprogs = 0;
   DevBuf<DTrace> tslots;
   DevBuf<svk::BrDraw> tout;
   DevBuf<uint64_t> mout;
@@ -924,6 +927,46 @@ sv_status batch_items(sv_batch* b, const uint32_t* prog_ids, const uint64_t* str
   b->slot_flags = max_flags;
   return SV_OK;
 }
+
+// The batch kernel of the next launch: with sv_batch_set_jit(1), the one
+// specialised to the handle's programs (built again when programs were added;
+// if it cannot be built, the generic one), else the generic one.
+sv_status batch_kernel(sv_batch* b, const svj::JitKernel** out) {
+  *out = nullptr;
+  if (!b->use_jit || b->progs.empty()) return SV_OK;
+  if (!b->jit || b->jit_nprogs != b->progs.size()) {
+    std::vector<const svp::Plan*> plans;
+    for (const auto& p : b->progs) plans.push_back(&p->plan);
+    std::string err;
+    std::shared_ptr<svj::JitKernel> k;
+    if (svj::compile_batch(plans, svk::batch_smem_bytes(b->dtype), k, err) != SV_OK) {
+      b->jit.reset();
+      b->jit_nprogs = b->progs.size();  // not retried until programs change
+      return SV_OK;
+    }
+    uint32_t base = 0;
+    for (size_t i = 0; i < b->hprogs.size(); ++i) {
+      b->hprogs[i].jit_base = base;
+      base += b->hprogs[i].npasses;
+    }
+    SV_CUDA(b->d_progs.upload(b->hprogs, b->own));
+    b->jit = k;
+    b->jit_nprogs = b->progs.size();
+  }
+  *out = b->jit.get();
+  return SV_OK;
+}
+
+cudaError_t launch_batch_kernel(sv_batch* b, const svj::JitKernel* k, svk::BatchArgs& a) {
+  if (!k) return svk::launch_batch(b->dtype, a, b->grid, b->own);
+  std::string err;
+  const int grid = std::min(b->grid, b->sms * k->per_sm);
+  if (svj::launch_single(*k, &a, grid, b->own, err) != SV_OK) {
+    g_err = err;
+    return cudaErrorLaunchFailure;
+  }
+  return cudaSuccess;
+}
 }  // namespace
 
 extern "C" {
@@ -949,8 +992,12 @@ sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   a.creg_out = b->cregs.p;
   a.status_out = b->status.p;
   a.work = b->profiling ? b->work.p : nullptr;
+  const svj::JitKernel* jk = nullptr;
+  sv_status kst = batch_kernel(b, &jk);
+  if (kst != SV_OK) return kst;
   uint64_t key = fnv1a(&a, sizeof(a));
   key = fnv1a(&b->grid, sizeof(b->grid), key);
+  key = fnv1a(&jk, sizeof(jk), key);
   if (!b->gexec || key != b->gkey) {
     if (b->gexec) {
       cudaGraphExecDestroy(b->gexec);
@@ -960,7 +1007,7 @@ sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
     SV_CUDA(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned), b->own);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status.p, 0, sizeof(int), b->own);
-    if (e == cudaSuccess) e = svk::launch_batch(b->dtype, a, b->grid, b->own);
+    if (e == cudaSuccess) e = launch_batch_kernel(b, jk, a);
     cudaError_t e2 = cudaStreamEndCapture(b->own, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -976,6 +1023,20 @@ sv_status sv_batch_launch(sv_batch* b, uint64_t seed) {
   SV_CUDA(cudaGraphLaunch(b->gexec, b->own));
   SV_CUDA(cudaEventRecord(b->ev_out, b->own));
   SV_CUDA(cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  return SV_OK;
+}
+
+sv_status sv_batch_set_jit(sv_batch* b, int enable) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  b->use_jit = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_batch_jit_info(sv_batch* b, int* specialised, double* compile_seconds) {
+  if (!b) return fail(SV_ERR_ARG, "null handle");
+  const svj::JitKernel* k = (b->use_jit && b->jit && b->jit_nprogs == b->progs.size()) ? b->jit.get() : nullptr;
+  if (specialised) *specialised = k ? 1 : 0;
+  if (compile_seconds) *compile_seconds = k ? k->compile_seconds : 0.0;
   return SV_OK;
 }
 
@@ -1097,7 +1158,12 @@ sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->own, b->ev_in, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->queue.p, 0, sizeof(unsigned), b->own);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status.p, 0, sizeof(int), b->own);
-    if (e == cudaSuccess) e = svk::launch_batch(b->dtype, a, b->grid, b->own);
+    const svj::JitKernel* jk = nullptr;
+    if (batch_kernel(b, &jk) != SV_OK) {
+      err = g_err;
+      return SV_ERR_CUDA;
+    }
+    if (e == cudaSuccess) e = launch_batch_kernel(b, jk, a);
     ic.resize(k);
     im.resize(k);
     itr.resize(k * size_t(cap));

@@ -128,6 +128,8 @@ def lib():
         "sv_grad_run": ([vp, vp, sz, sz, vp, vp], st),
         "sv_grad_destroy": ([vp], st),
         "sv_grad_set_jit": ([vp, i32], st),
+        "sv_batch_set_jit": ([vp, i32], st),
+        "sv_batch_jit_info": ([vp, C.POINTER(i32), C.POINTER(C.c_double)], st),
         "sv_expval_grad_batch": ([i32, i32, vp, sz, vp, sz, sz, vp, sz, vp, vp, vp], st),
         "sv_last_error": ([], C.c_char_p),
         "sv_version": ([], C.c_char_p),
@@ -468,6 +470,16 @@ class Batch:
         w = WorkCounts()
         _check(lib().sv_batch_work(self._h, C.byref(w)))
         return {k: int(getattr(w, k)) for k, _ in WorkCounts._fields_}
+
+    def set_jit(self, on: bool = True) -> None:
+        """Launches run a kernel specialised to the programs added so far (compiled
+        at the next launch) instead of the generic one."""
+        _check(lib().sv_batch_set_jit(self._h, 1 if on else 0))
+
+    def jit_info(self) -> dict:
+        spec, secs = C.c_int(0), C.c_double(0)
+        _check(lib().sv_batch_jit_info(self._h, C.byref(spec), C.byref(secs)))
+        return {"specialised": bool(spec.value), "compile_seconds": float(secs.value)}
 
     def close(self):
         if getattr(self, "_h", None):

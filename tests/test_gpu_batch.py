@@ -50,6 +50,34 @@ def test_batch_matches_plain_path_mixed_n(svmod, orc, dtype):
                 assert int(got[i]) == ref.creg
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_specialised_kernel_matches_generic(svmod, dtype):
+    """The batch kernel specialised to the programs (sv_batch_set_jit) gives the
+    generic kernel's records on a mix of sizes, and is rebuilt when a program is
+    added; records of the plain path cover the new program."""
+    ns = [5, 11, 13]
+    circs = {n: W.sequential_feedforward(700 + n, n, layers=3) for n in ns}
+    rng = np.random.default_rng(3)
+    traj_n = rng.choice(ns, size=48)
+    streams = np.arange(len(traj_n), dtype=np.uint64) + 9
+    shots = rng.integers(0, 1000, size=len(traj_n)).astype(np.uint64)
+    with svmod.Batch(dtype) as b:
+        pid = {n: b.add_program(circs[n].ops, n + 1) for n in ns}
+        ids = [pid[n] for n in traj_n]
+        generic = b.run(ids, streams, shots, seed=3)
+        b.set_jit(True)
+        spec = b.run(ids, streams, shots, seed=3)
+        assert b.jit_info()["specialised"]
+        assert np.array_equal(generic, spec)
+        extra = W.sequential_feedforward(99, 7, layers=3)
+        p7 = b.add_program(extra.ops, 8)  # the next launch builds the kernel again
+        got = b.run([p7] * 8, np.arange(8, dtype=np.uint64), np.arange(8, dtype=np.uint64), seed=3)
+        assert b.jit_info()["specialised"]
+    with svmod.State(8, dtype) as st:
+        for i in range(8):
+            assert int(got[i]) == st.run(extra.ops, seed=3, stream_id=i, shot=i)
+
+
 def test_batch_graph_replay_and_seed(svmod):
     c = W.sequential_feedforward(9, 6, layers=3)
     with svmod.Batch("c64") as b:
