@@ -293,6 +293,15 @@ def measure_forms(sv, torch):
         b.results()
         bw = b.work()
         b.profile(False)
+        # the kernel specialised to these programs (compiled once, then launched like the generic one)
+        b.set_jit(True)
+        b.launch(0)
+        b.results()
+        t0 = time.perf_counter()
+        b.launch(0)
+        b.results()
+        tj = time.perf_counter() - t0
+        bj = b.jit_info()
     sample = wl.traj_n[:256]
     states = {}
     for n in sorted(set(int(v) for v in sample)):
@@ -315,7 +324,11 @@ def measure_forms(sv, torch):
                        "state_bytes_frac_of_hbm": (bw["bytes_read"] + bw["bytes_written"]) / tb / 1e9
                        / measured_peaks()[0]["hbm_gbs"],
                        "state_bytes_note": "tile reads and writes of the per-CTA state slots (2^13..2^21 "
-                                           "amplitudes, largely L2-resident), against the HBM copy peak"}
+                                           "amplitudes, largely L2-resident), against the HBM copy peak",
+                       "specialised": {"trajectories_per_s": len(ids) / tj, "seconds": tj,
+                                       "updates_per_s": bw["updates"] / tj, "kernel": "sv_jit_batch",
+                                       "specialised": bj["specialised"], "compile_seconds": bj["compile_seconds"],
+                                       "note": "sv_batch_set_jit(1): stage programs compiled for the 9 programs"}}
     # plain small program, 1,000 shots, complex128
     c = W.plain_small()
     with sv.State(5, "c128") as st:
