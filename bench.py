@@ -62,6 +62,8 @@ def parse():
                     help="layered: the plain dynamic-circuit workload; dense4: layers of dense 4-qubit unitaries")
     ap.add_argument("--no-dense-tc", action="store_true", help="dense 4-qubit gates on the FP32 pipes")
     ap.add_argument("--first-fit", action="store_true", help="plan tiles by first fit instead of by the gates they unlock")
+    ap.add_argument("--stage-pairs", type=int, default=None, choices=(0, 1, 2),
+                    help="complex64 stage packing: 0 fewest stages, 1/2 weigh 16-byte pair accesses")
     ap.add_argument("--jit-blocks", type=int, default=0, help="CTAs per SM of the specialised kernels (0: default)")
     ap.add_argument("--form", default=None, choices=["batching", "adjoint", "sample_expval"],
                     help="run only this auxiliary measurement (for profiling) and print its JSON")
@@ -752,6 +754,8 @@ def main():
     st.set_jit(not args.no_jit)
     st.set_dense_tc(not args.no_dense_tc)
     st.set_tile_select(not args.first_fit)
+    if args.stage_pairs is not None:
+        st.set_stage_pairs(args.stage_pairs)
     st.set_jit_blocks(args.jit_blocks)
     if args.tile_bits or args.low_bits:
         st.set_tuning(args.tile_bits, args.low_bits, 0)
@@ -814,6 +818,7 @@ def main():
     per_launch = prof["bytes"] / max(1, prof["launches"])
     traffic = (PASS_DRAM_OVER_COUNTED * per_launch
                if (dtype == "c64" and args.circuit == "layered" and not args.first_fit and not args.low_bits
+                   and args.stage_pairs is None
                    and not args.tile_bits) else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

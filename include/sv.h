@@ -177,6 +177,17 @@ sv_status sv_set_dense_pool(sv_state* h, const double* pool, size_t n_complex);
 sv_status sv_set_tile_select(sv_state* h, int closure);
 
 /*
+ * How the planner packs a complex64 pass's gates into register stages.  A
+ * stage whose four register bits include the tile's lowest bit moves its
+ * amplitudes through shared memory as 16-byte pairs, half the access
+ * instructions of one without it.  0: the packing with the fewest stages;
+ * 1 (default) / 2: packings compared at a cost of 3/2 / 2 for a stage without
+ * pair accesses against one with them.  Programs planned from now on use it.
+ * SV_ERR_ARG for a null handle or a mode outside 0..2.
+ */
+sv_status sv_set_stage_pairs(sv_state* h, int mode);
+
+/*
  * CTAs per SM the specialised pass kernels are compiled for (their register
  * budget follows: 65,536 / (256 x blocks) per thread) and launched with; 0
  * (default) keeps 2 for complex64 and 1 for complex128.  Programs planned

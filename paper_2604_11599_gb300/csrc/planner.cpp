@@ -233,6 +233,7 @@ struct Builder {
   int max_pass_gates;
   int tile_select = 1;  // Tuning::tile_select
   int reg_bits = REG_BITS;  // gate register bits per stage (ADJ_REG_BITS for backward plans)
+  int stage_pairs = 1;       // complex64 stage packing weighs 16-byte pair accesses (Tuning::stage_pairs)
   bool adjoint = false;     // backward plan: derivative items, then U^dagger, per gate
 
   Builder(Plan& p, const std::vector<Item>& it, int b, int mpg) : P(p), items(it), B(b), max_pass_gates(mpg) {}
@@ -364,7 +365,9 @@ struct Builder {
         }
         return used;
       };
-      auto pack = [&](bool best, std::vector<uint32_t>& oS, std::vector<std::vector<int>>& oG) {
+      // paired: only register sets that hold local bit 0 (a gate's or the
+      // padding), so that complex64 stages move amplitude pairs as 16 bytes
+      auto pack = [&](bool best, bool paired, std::vector<uint32_t>& oS, std::vector<std::vector<int>>& oG) {
         std::vector<int> rem(chosen.size());
         for (size_t i = 0; i < rem.size(); ++i) rem[i] = int(i);
         while (!rem.empty()) {
@@ -375,12 +378,13 @@ struct Builder {
           } else {
             uint32_t bits = 0;
             for (int i : rem) bits |= lmask[size_t(i)];
+            if (paired) bits |= 1u;
             std::vector<int> bl;
             for (int j = 0; j < 32; ++j)
               if ((bits >> j) & 1) bl.push_back(j);
             const int k = std::min<int>(reg_bits, int(bl.size()));
-            size_t bestn = 0;
-            uint32_t bestS = 0;
+            size_t bestn = 0, bestp = 0;
+            uint32_t bestS = 0, bestSp = 0;
             std::vector<int> pick(static_cast<size_t>(k));
             for (int i = 0; i < k; ++i) pick[size_t(i)] = i;
             while (true) {  // every k-subset of the remaining gates' local bits
@@ -392,13 +396,19 @@ struct Builder {
                 bestn = a.size();
                 bestS = Sc;
               }
+              if ((Sc & 1u) && a.size() > bestp) {
+                bestp = a.size();
+                bestSp = Sc;
+              }
               int i = k - 1;
               while (i >= 0 && pick[size_t(i)] == int(bl.size()) - k + i) --i;
               if (i < 0) break;
               ++pick[size_t(i)];
               for (int j = i + 1; j < k; ++j) pick[size_t(j)] = pick[size_t(j - 1)] + 1;
             }
-            S = take(rem, bestS, sg, left, false);
+            // paired: the best set holding local bit 0, unless none runs a gate
+            // (the next gate needs four other bits, e.g. a dense 4-qubit one)
+            S = take(rem, (paired && bestp > 0) ? bestSp : bestS, sg, left, false);
           }
           for (int& i : sg) i = chosen[size_t(i)];
           rem.swap(left);
@@ -406,13 +416,31 @@ struct Builder {
           oG.push_back(sg);
         }
       };
-      std::vector<uint32_t> s1, s2;
-      std::vector<std::vector<int>> g1, g2;
-      pack(false, s1, g1);
-      if (!adjoint && s1.size() > 1) pack(true, s2, g2);
-      const bool use_best = !s2.empty() && s2.size() < s1.size();
-      stS = use_best ? s2 : s1;
-      stG = use_best ? g2 : g1;
+      std::vector<uint32_t> s1, s2, s3;
+      std::vector<std::vector<int>> g1, g2, g3;
+      pack(false, false, s1, g1);
+      if (!adjoint && s1.size() > 1) pack(true, false, s2, g2);
+      // complex64: a stage whose register set holds local bit 0 moves its
+      // amplitudes as 16-byte pairs (half the shared-memory instructions of a
+      // stage without it), so packings are compared by that cost
+      const bool pair_cost = B == 1 && !adjoint && stage_pairs > 0;
+      if (pair_cost && s1.size() > 1) pack(true, true, s3, g3);
+      auto cost = [&](const std::vector<uint32_t>& ss) {
+        size_t c = 0;
+        for (uint32_t S : ss)
+          c += (!pair_cost || (S & 1u) || popc(S) < reg_bits) ? (stage_pairs == 2 ? 1 : 2) : 3 - (stage_pairs == 2 ? 1 : 0);
+        return c;
+      };
+      stS = s1;
+      stG = g1;
+      if (!s2.empty() && (pair_cost ? cost(s2) < cost(stS) : s2.size() < stS.size())) {
+        stS = s2;
+        stG = g2;
+      }
+      if (!s3.empty() && cost(s3) < cost(stS)) {
+        stS = s3;
+        stG = g3;
+      }
     }
 
     // Warp ownership.  With 2^m >= 16 * PASS_THREADS every thread holds one
@@ -1111,6 +1139,7 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
 
   Builder b(P, U.items, dtype == SV_C64 ? 1 : 0, tune.max_pass_gates);
   b.tile_select = tune.tile_select;
+  b.stage_pairs = tune.stage_pairs;
   for (const Segment& s : segs) {
     if (s.gates.empty() && !s.has_group) continue;
     b.emit_segment(s);

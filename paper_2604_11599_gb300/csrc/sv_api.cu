@@ -408,6 +408,13 @@ sv_status sv_set_tile_select(sv_state* h, int closure) {
   return SV_OK;
 }
 
+sv_status sv_set_stage_pairs(sv_state* h, int mode) {
+  if (!h) return fail(SV_ERR_ARG, "null handle");
+  if (mode < 0 || mode > 2) return fail(SV_ERR_ARG, "stage pair mode is 0, 1 or 2");
+  h->tune.stage_pairs = mode;
+  return SV_OK;
+}
+
 sv_status sv_prepare(sv_state* h, const sv_op* ops, size_t n_ops, sv_program** out) {
   if (!h || !out) return fail(SV_ERR_ARG, "null argument");
   sv_program* cached = nullptr;

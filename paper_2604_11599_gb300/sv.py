@@ -112,6 +112,7 @@ def lib():
         "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
         "sv_selftest_wait": ([vp, C.c_uint32], st),
         "sv_set_tile_select": ([vp, i32], st),
+        "sv_set_stage_pairs": ([vp, i32], st),
         "sv_set_jit_blocks": ([vp, i32], st),
         "sv_grad_info": ([vp, C.POINTER(GradStats)], st),
         "sv_batch_profile": ([vp, i32], st),
@@ -269,6 +270,10 @@ class State:
     def set_tile_select(self, closure: bool = True) -> None:
         """Tile qubits chosen for the gates they unlock (True) or by first fit."""
         _check(lib().sv_set_tile_select(self._h, 1 if closure else 0))
+
+    def set_stage_pairs(self, mode: int = 1) -> None:
+        """Complex64 stage packing: 0 fewest stages, 1/2 weigh 16-byte pair accesses."""
+        _check(lib().sv_set_stage_pairs(self._h, int(mode)))
 
     def set_tuning(self, tile_bits: int = 0, low_bits: int = 0, max_pass_gates: int = 0) -> None:
         _check(lib().sv_set_tuning(self._h, tile_bits, low_bits, max_pass_gates))
