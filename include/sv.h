@@ -180,8 +180,8 @@ sv_status sv_set_tile_select(sv_state* h, int closure);
  * How the planner packs a complex64 pass's gates into register stages.  A
  * stage whose four register bits include the tile's lowest bit moves its
  * amplitudes through shared memory as 16-byte pairs, half the access
- * instructions of one without it.  0: the packing with the fewest stages;
- * 1 (default) / 2: packings compared at a cost of 3/2 / 2 for a stage without
+ * instructions of one without it.  0 (default): the packing with the fewest
+ * stages; 1 / 2: packings compared at a cost of 3/2 / 2 for a stage without
  * pair accesses against one with them.  Programs planned from now on use it.
  * SV_ERR_ARG for a null handle or a mode outside 0..2.
  */

@@ -233,7 +233,7 @@ struct Builder {
   int max_pass_gates;
   int tile_select = 1;  // Tuning::tile_select
   int reg_bits = REG_BITS;  // gate register bits per stage (ADJ_REG_BITS for backward plans)
-  int stage_pairs = 1;       // complex64 stage packing weighs 16-byte pair accesses (Tuning::stage_pairs)
+  int stage_pairs = 0;       // complex64 stage packing weighs 16-byte pair accesses (Tuning::stage_pairs)
   bool adjoint = false;     // backward plan: derivative items, then U^dagger, per gate
 
   Builder(Plan& p, const std::vector<Item>& it, int b, int mpg) : P(p), items(it), B(b), max_pass_gates(mpg) {}

@@ -17,8 +17,9 @@ struct Tuning {
   int min_qubits = 10;     // states are padded to at least this many qubits
   int tile_select = 1;     // 1: each tile's gathered qubits chosen for the gates they unlock; 0: first fit
   int jit_min_blocks = 0;  // specialised kernels: CTAs per SM they are compiled for (0: 2 complex64, 1 complex128)
-  int stage_pairs = 1;     // complex64 stage packing: 0 fewest stages; 1 / 2: a stage without 16-byte pair
-                           // accesses costs 3/2 / 2 times one with them
+  int stage_pairs = 0;     // complex64 stage packing: 0 fewest stages; 1 / 2: a stage without 16-byte pair
+                           // accesses costs 3/2 / 2 times one with them (n=30 layered: 150.1 / 150.4 /
+                           // 155.6 ms per step, so fewest stages is the default)
 };
 
 struct Plan {

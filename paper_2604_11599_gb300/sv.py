@@ -271,7 +271,7 @@ class State:
         """Tile qubits chosen for the gates they unlock (True) or by first fit."""
         _check(lib().sv_set_tile_select(self._h, 1 if closure else 0))
 
-    def set_stage_pairs(self, mode: int = 1) -> None:
+    def set_stage_pairs(self, mode: int = 0) -> None:
         """Complex64 stage packing: 0 fewest stages, 1/2 weigh 16-byte pair accesses."""
         _check(lib().sv_set_stage_pairs(self._h, int(mode)))
 
