@@ -492,10 +492,23 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
   static std::map<std::pair<int, size_t>, std::shared_ptr<JitModule>> cache;
   int dev = 0;
   cudaGetDevice(&dev);
-  std::string all;
-  for (size_t c = 0, k = chunk_count(P), n = P.passes.size(); c < k; ++c)
-    all += generate_chunk(P, n * c / k, n * (c + 1) / k);
-  const auto key = std::make_pair(dev, std::hash<std::string>{}(all));
+  // the generated source is a function of these plan fields (whole records
+  // hashed, so plans that differ anywhere in them get their own module);
+  // hashing them costs far less than generating the text of every chunk
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  const int head[4] = {P.dtype, P.m, P.n_int, P.jit_min_blocks};
+  mix(head, sizeof(head));
+  mix(P.passes.data(), P.passes.size() * sizeof(svp::DPass));
+  mix(P.stages.data(), P.stages.size() * sizeof(svp::DStage));
+  mix(P.gates.data(), P.gates.size() * sizeof(svp::DGate));
+  const auto key = std::make_pair(dev, size_t(h));
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);

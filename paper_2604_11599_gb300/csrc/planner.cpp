@@ -831,7 +831,9 @@ struct Builder {
         if ((qm & blocked) || (qm & ~T) || recs + 1 + cnd[i] > cap || mat + cml[i] > MAX_PASS_MAT ||
             dots + cnd[i] > MAX_PASS_DOTS) {
           blocked |= qm;
-          if (blocked == all) break;  // nothing further can run
+          // nothing further can run once every tile qubit is blocked: a later
+          // gate either leaves the tile or touches a blocked qubit
+          if ((blocked & T) == T) break;
           continue;
         }
         mat += cml[i];
@@ -900,18 +902,30 @@ struct Builder {
             continue;
           }
           uint64_t bp = 0;
-          if (popc(T) + 2 <= m)
-            for (int a = 0; a < n; ++a) {
-              if ((T >> a) & 1) continue;
-              for (int b2 = a + 1; b2 < n; ++b2) {
-                if ((T >> b2) & 1) continue;
-                const size_t v = count(T | (1ull << a) | (1ull << b2));
-                if (v > bv) {
-                  bv = v;
-                  bp = (1ull << a) | (1ull << b2);
-                }
+          if (popc(T) + 2 <= m) {
+            // No single qubit lets another gate run, so a pair can only do so
+            // through a gate with exactly that pair outside the tile (every
+            // other gate that would run is held by a blocker with both qubits
+            // outside): only those pairs are counted, in the (a, b) order of an
+            // exhaustive search, which they would win (count is monotone in T).
+            std::vector<uint32_t> pairs;
+            for (uint64_t qm : cq) {
+              const uint64_t out = qm & ~T;
+              if (popc(out) != 2) continue;
+              const int a = __builtin_ctzll(out), b2 = 63 - __builtin_clzll(out);
+              pairs.push_back(uint32_t(a) << 8 | uint32_t(b2));
+            }
+            std::sort(pairs.begin(), pairs.end());
+            pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+            for (uint32_t pr : pairs) {
+              const uint64_t pm = (1ull << (pr >> 8)) | (1ull << (pr & 0xFF));
+              const size_t v = count(T | pm);
+              if (v > bv) {
+                bv = v;
+                bp = pm;
               }
             }
+          }
           if (bp && bv > have) {
             T |= bp;
             have = bv;
