@@ -593,6 +593,11 @@ sv_status sv_set_dense_tc(sv_state* h, int enable);
  */
 sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
                        size_t n_complex, char* log, size_t log_len);
+/* The same for the adjoint kernel specialised to a program (sv_grad_run's
+ * default): lowers the forward and backward plans and compiles the module.
+ * Errors as sv_grad_create's lowering, or SV_ERR_CUDA with the compiler log. */
+sv_status sv_jit_check_adjoint(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                               size_t n_complex, char* log, size_t log_len);
 
 /* Wait for all work of h.  Resource management of this library; the paper
  * has no counterpart.  SV_ERR_CUDA if earlier asynchronous work failed. */

@@ -566,6 +566,11 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
   return SV_OK;
 }
 
+sv_status compile_adjoint_cubin(const svp::Plan& F, const svp::Plan& B, std::vector<char>& cubin, std::string& err,
+                                std::string* info) {
+  return compile_source(generate_adjoint_source(F, B), cubin, err, info);
+}
+
 JitAdjoint::~JitAdjoint() {
   if (module && driver().moduleUnload) driver().moduleUnload(static_cast<CUmodule>(module));
 }

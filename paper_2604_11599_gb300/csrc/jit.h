@@ -57,6 +57,9 @@ struct JitAdjoint {
   ~JitAdjoint();
 };
 std::string generate_adjoint_source(const svp::Plan& F, const svp::Plan& B);
+// NVRTC only (no device needed), as compile_cubin
+sv_status compile_adjoint_cubin(const svp::Plan& F, const svp::Plan& B, std::vector<char>& cubin, std::string& err,
+                                std::string* info = nullptr);
 // compiled and loaded; cached for the process by device, source and shared-memory size
 sv_status compile_adjoint(const svp::Plan& F, const svp::Plan& B, size_t smem, std::shared_ptr<JitAdjoint>& out,
                           std::string& err);

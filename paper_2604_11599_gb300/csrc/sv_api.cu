@@ -497,6 +497,28 @@ sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, co
   return SV_OK;
 }
 
+sv_status sv_jit_check_adjoint(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
+                               size_t n_complex, char* log, size_t log_len) {
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  svp::Tuning t;
+  t.tile_bits = svk::BATCH_TILE_BITS;
+  t.min_qubits = svk::BATCH_TILE_BITS;
+  svp::Plan F, B;
+  std::string err;
+  sv_status st = svp::build_adjoint_plan(n, dtype, ops, n_ops, dense_pool, dense_pool ? n_complex : 0, t, F, B, err);
+  if (st == SV_OK) {
+    std::vector<char> cubin;
+    st = svj::compile_adjoint_cubin(F, B, cubin, err, &err);
+  }
+  if (log && log_len) {
+    const size_t k = std::min(err.size(), log_len - 1);
+    std::memcpy(log, err.data(), k);
+    log[k] = 0;
+  }
+  if (st != SV_OK) return fail(st, err);
+  return SV_OK;
+}
+
 sv_status sv_launch(sv_state* h, sv_program* p, const double* dev_params, size_t n_params, uint64_t seed,
                     uint64_t stream_id, uint64_t shot) {
   if (!h || !p) return fail(SV_ERR_ARG, "null argument");

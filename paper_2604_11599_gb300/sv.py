@@ -107,6 +107,7 @@ def lib():
         "sv_set_jit": ([vp, i32], st),
         "sv_set_dense_tc": ([vp, i32], st),
         "sv_jit_check": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
+        "sv_jit_check_adjoint": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
         "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
@@ -633,6 +634,18 @@ def jit_check(ops: np.ndarray, n: int, dtype: str = "c64", pool=None) -> str:
     buf = C.create_string_buffer(8192)
     st = lib().sv_jit_check(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(pl),
                             0 if pl is None else pl.size, buf, 8192)
+    if st != 0:
+        raise SVError(st, buf.value.decode(errors="replace"))
+    return buf.value.decode(errors="replace")
+
+
+def jit_check_adjoint(ops: np.ndarray, n: int, dtype: str = "c64", pool=None) -> str:
+    """Compiles a program's specialised adjoint kernel on the host (no GPU); returns the log, raises on failure."""
+    ops = _ops(ops)
+    pl = None if pool is None or len(pool) == 0 else np.ascontiguousarray(pool, dtype=np.complex128)
+    buf = C.create_string_buffer(8192)
+    st = lib().sv_jit_check_adjoint(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(pl),
+                                    0 if pl is None else pl.size, buf, 8192)
     if st != 0:
         raise SVError(st, buf.value.decode(errors="replace"))
     return buf.value.decode(errors="replace")
