@@ -390,14 +390,20 @@ struct Builder {
             while (true) {  // every k-subset of the remaining gates' local bits
               uint32_t Sc = 0;
               for (int i : pick) Sc |= 1u << bl[size_t(i)];
-              std::vector<int> a, b;
-              take(rem, Sc, a, b, false);
-              if (a.size() > bestn) {
-                bestn = a.size();
+              // take(rem, Sc, .., false), counted only
+              size_t na = 0;
+              uint32_t blocked = 0;
+              for (int i : rem) {
+                const uint32_t lm = lmask[size_t(i)];
+                if ((lm & blocked) || (lm & ~Sc)) blocked |= lm;
+                else ++na;
+              }
+              if (na > bestn) {
+                bestn = na;
                 bestS = Sc;
               }
-              if ((Sc & 1u) && a.size() > bestp) {
-                bestp = a.size();
+              if ((Sc & 1u) && na > bestp) {
+                bestp = na;
                 bestSp = Sc;
               }
               int i = k - 1;
@@ -852,14 +858,19 @@ struct Builder {
       uint64_t best = T0;
       size_t bestv = count(best);
       std::vector<std::pair<size_t, uint64_t>> nx;
+      std::vector<uint64_t> cand;
       for (int step = popc(T0); step < m; ++step) {
         nx.clear();
+        cand.clear();
         for (uint64_t X : cur)
           for (int q = 0; q < n; ++q) {
             if ((X >> q) & 1) continue;
-            const uint64_t X2 = X | (1ull << q);
-            nx.push_back({count(X2), X2});
+            cand.push_back(X | (1ull << q));
           }
+        // beams that differ in one qubit reach the same sets: count each once
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        for (uint64_t X2 : cand) nx.push_back({count(X2), X2});
         std::sort(nx.begin(), nx.end(), [](const std::pair<size_t, uint64_t>& a, const std::pair<size_t, uint64_t>& b) {
           return a.first > b.first || (a.first == b.first && a.second < b.second);
         });
