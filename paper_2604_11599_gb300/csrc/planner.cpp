@@ -19,8 +19,10 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 namespace svp {
 namespace {
@@ -764,7 +766,21 @@ struct Builder {
   }
 
   // Greedy fusion of a segment's gates into passes.
+  // The passes of a segment, as (gates, tile qubits, last) in order; reads
+  // the items and the tuning only, so segments can be planned concurrently.
+  struct PassPick {
+    std::vector<int> chosen, tq;
+    bool last = false;
+  };
   void emit_segment(const Segment& seg) {
+    std::vector<PassPick> picks;
+    plan_segment(seg, picks);
+    emit_picks(seg, picks);
+  }
+  void emit_picks(const Segment& seg, const std::vector<PassPick>& picks) {
+    for (const PassPick& pk : picks) emit_pass(pk.chosen, pk.tq, pk.last ? &seg : nullptr, false);
+  }
+  void plan_segment(const Segment& seg, std::vector<PassPick>& picks) const {
     const int n = P.n_int, m = P.m, L = P.L;
     const uint64_t low = (L >= 64) ? ~0ull : ((1ull << L) - 1);
     std::vector<int> rem(seg.gates);
@@ -778,7 +794,7 @@ struct Builder {
       for (int q = 0; q < n && popc(T) < m; ++q) T |= 1ull << q;
       for (int q = 0; q < n; ++q)
         if ((T >> q) & 1) tq.push_back(q);
-      emit_pass({}, tq, &seg, false);
+      picks.push_back(PassPick{{}, tq, true});
       return;
     }
     const size_t cap = max_pass_gates > 0 ? size_t(max_pass_gates) : size_t(MAX_PASS_GATES);
@@ -978,7 +994,7 @@ struct Builder {
       std::vector<int> tq;
       for (int q = 0; q < n; ++q)
         if ((T >> q) & 1) tq.push_back(q);
-      emit_pass(chosen, tq, last ? &seg : nullptr, false);
+      picks.push_back(PassPick{chosen, tq, last});
     }
   }
 };
@@ -1165,9 +1181,30 @@ sv_status build_plan(int n, int dtype, const sv_op* ops, size_t n_ops, const dou
   Builder b(P, U.items, dtype == SV_C64 ? 1 : 0, tune.max_pass_gates);
   b.tile_select = tune.tile_select;
   b.stage_pairs = tune.stage_pairs;
-  for (const Segment& s : segs) {
-    if (s.gates.empty() && !s.has_group) continue;
-    b.emit_segment(s);
+  {
+    // tile selection per segment on worker threads (it dominates the host
+    // time of a plan; segments are independent), passes emitted in order
+    std::vector<const Segment*> todo;
+    for (const Segment& s : segs)
+      if (!(s.gates.empty() && !s.has_group)) todo.push_back(&s);
+    std::vector<std::vector<Builder::PassPick>> picks(todo.size());
+    size_t work = 0;
+    for (const Segment* s : todo) work += s->gates.size();
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>({todo.size(), size_t(hw), 8});
+    if (nt <= 1 || work < 256) {
+      for (size_t i = 0; i < todo.size(); ++i) b.plan_segment(*todo[i], picks[i]);
+    } else {
+      std::atomic<size_t> next{0};
+      auto worker = [&]() {
+        for (size_t i; (i = next.fetch_add(1)) < todo.size();) b.plan_segment(*todo[i], picks[i]);
+      };
+      std::vector<std::thread> th;
+      for (size_t t = 1; t < nt; ++t) th.emplace_back(worker);
+      worker();
+      for (std::thread& t : th) t.join();
+    }
+    for (size_t i = 0; i < todo.size(); ++i) b.emit_picks(*todo[i], picks[i]);
   }
   // A projector can still be pending at the end (a final measurement group,
   // or later passes whose gates were all predicated off): a flush pass
