@@ -529,7 +529,8 @@ sv_status sv_batch_work(sv_batch* b, sv_work_counts* out);
 /* 1: launches run a kernel specialised to the handle's programs (every gate,
  * register position and shared-memory address of every pass a constant; the
  * per-program matrices and flags stay run-time data), compiled at the first
- * launch after programs were added (seconds for a handful of programs; suited
+ * launch after programs were added (about 45 s for nine programs of 13-21
+ * qubits with 228 passes in all, less for fewer or shorter programs; suited
  * to a fixed program set run many times, not to a serving loop that adds
  * programs as requests arrive); if it cannot be built the generic kernel
  * runs.  0 (default): the generic kernel, which reads the gate records at run
