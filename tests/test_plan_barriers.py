@@ -35,3 +35,20 @@ def test_layered_passes_use_warp_barriers(dtype):
     s = sv.plan_info(W.layered(5, n, layers=20).ops, n, dtype)
     total = s["block_barriers"] + s["warp_barriers"]
     assert s["warp_barriers"] >= 0.3 * total
+
+
+def test_plans_are_deterministic_and_keep_their_pass_count():
+    """The planner tiles the segments between measurement groups on worker
+    threads and emits their passes in program order: lowering the same program
+    again gives the same plan.  The n=30 layered program keeps the pass and
+    stage counts its measured throughput was taken with (38 passes)."""
+    n = 30
+    c = W.layered(5, n, layers=20)
+    first = sv.plan_info(c.ops, n, "c64")
+    for _ in range(4):
+        assert sv.plan_info(c.ops, n, "c64") == first
+    assert first["passes"] <= 38, first
+    batch = W.batching(seed=6, n_traj=16)
+    for m, circ in batch.circuits.items():
+        a = sv.plan_info(circ.ops, m + 1, "c64", tile_bits=12)
+        assert sv.plan_info(circ.ops, m + 1, "c64", tile_bits=12) == a
