@@ -298,7 +298,9 @@ sv_status sv_sample_state_device(sv_state* h, uint64_t shots, uint64_t seed, uin
                                  uint64_t* dev_out);
 
 /*
- * <psi| sum_t coeff_t P_t |psi> of the current state (FP64 accumulation): the
+ * <psi| sum_t coeff_t P_t |psi> of the current state (sums of 1,024 pairs in
+ * the state precision, accumulated in double-float for complex64 and in FP64
+ * for complex128, per-term results and the total in FP64): the
  * energy <H> of a Hamiltonian given as a Pauli sum, as in the VQE experiments
  * (Sec. II-D; Sec. IV-A.2, H = Z0 Z1; Sec. IV-D).  terms is a host array read
  * during the call; total (nullable) receives the sum, per_term (nullable,
