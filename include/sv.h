@@ -440,7 +440,9 @@ sv_status sv_batch_sample_branched(sv_batch* b, const uint32_t* prog_ids, const 
  *                  asynchronously on the handle's stream.  One persistent
  *                  launch: each CTA runs whole parameter sets (forward sweep,
  *                  lambda = H psi, backward sweep with the derivative
- *                  accumulations), FP64 accumulation.
+ *                  accumulations); per-warp derivative sums in
+ *                  double-float (complex64) or FP64, gradient entries and
+ *                  energies in FP64.
  * sv_expval_grad_batch  the same with host arrays, waiting for the result.
  * Errors: SV_ERR_ARG (bad sizes or masks, n_params below the largest index
  * referenced, more than 1024 parameters), SV_ERR_UNSUPPORTED (program with
