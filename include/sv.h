@@ -603,6 +603,13 @@ sv_status sv_jit_check(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, co
  * Errors as sv_grad_create's lowering, or SV_ERR_CUDA with the compiler log. */
 sv_status sv_jit_check_adjoint(int n, sv_dtype dtype, const sv_op* ops, size_t n_ops, const double* dense_pool,
                                size_t n_complex, char* log, size_t log_len);
+/* The same for the batched kernel specialised to n_progs programs (as
+ * sv_batch_set_jit builds it): program k has n[k] qubits and ops[k] (n_ops[k]
+ * records, no dense gates), all lowered with the batched engine's 2^12-amplitude
+ * tiles.  Host arrays, read during the call.  SV_ERR_ARG for empty or null
+ * arrays or a malformed program, SV_ERR_CUDA with the compiler log. */
+sv_status sv_jit_check_batch(sv_dtype dtype, size_t n_progs, const int* n, const sv_op* const* ops,
+                             const size_t* n_ops, char* log, size_t log_len);
 
 /* Wait for all work of h.  Resource management of this library; the paper
  * has no counterpart.  SV_ERR_CUDA if earlier asynchronous work failed. */

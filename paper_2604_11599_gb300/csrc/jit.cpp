@@ -566,6 +566,15 @@ sv_status compile(const svp::Plan& P, std::shared_ptr<JitModule>& out, std::stri
   return SV_OK;
 }
 
+sv_status compile_batch_cubin(const std::vector<const svp::Plan*>& plans, std::vector<char>& cubin, std::string& err,
+                              std::string* info) {
+  if (plans.empty()) {
+    err = "no programs";
+    return SV_ERR_ARG;
+  }
+  return compile_source(generate_batch_source(plans), cubin, err, info);
+}
+
 sv_status compile_adjoint_cubin(const svp::Plan& F, const svp::Plan& B, std::vector<char>& cubin, std::string& err,
                                 std::string* info) {
   return compile_source(generate_adjoint_source(F, B), cubin, err, info);

@@ -79,6 +79,9 @@ struct JitKernel {
 // (BatchProg::jit_base is a program's first number).  Cached for the process by
 // device, source and shared-memory size.
 std::string generate_batch_source(const std::vector<const svp::Plan*>& plans);
+// NVRTC only (no device needed), as compile_cubin
+sv_status compile_batch_cubin(const std::vector<const svp::Plan*>& plans, std::vector<char>& cubin, std::string& err,
+                              std::string* info = nullptr);
 sv_status compile_batch(const std::vector<const svp::Plan*>& plans, size_t smem, std::shared_ptr<JitKernel>& out,
                         std::string& err);
 // args: the address of the kernel's single parameter (e.g. an svk::BatchArgs)

@@ -519,6 +519,34 @@ sv_status sv_jit_check_adjoint(int n, sv_dtype dtype, const sv_op* ops, size_t n
   return SV_OK;
 }
 
+sv_status sv_jit_check_batch(sv_dtype dtype, size_t n_progs, const int* n, const sv_op* const* ops,
+                             const size_t* n_ops, char* log, size_t log_len) {
+  if (dtype != SV_C64 && dtype != SV_C128) return fail(SV_ERR_ARG, "unknown dtype");
+  if (!n_progs || !n || !ops || !n_ops) return fail(SV_ERR_ARG, "null or empty program arrays");
+  std::vector<svp::Plan> plans(n_progs);
+  std::vector<const svp::Plan*> pp;
+  std::string err;
+  sv_status st = SV_OK;
+  for (size_t k = 0; k < n_progs && st == SV_OK; ++k) {
+    svp::Tuning t;
+    t.tile_bits = svk::BATCH_TILE_BITS;
+    t.min_qubits = svk::BATCH_TILE_BITS;
+    st = svp::build_plan(n[k], dtype, ops[k], n_ops[k], nullptr, 0, t, plans[k], err);
+    pp.push_back(&plans[k]);
+  }
+  if (st == SV_OK) {
+    std::vector<char> cubin;
+    st = svj::compile_batch_cubin(pp, cubin, err, &err);
+  }
+  if (log && log_len) {
+    const size_t k = std::min(err.size(), log_len - 1);
+    std::memcpy(log, err.data(), k);
+    log[k] = 0;
+  }
+  if (st != SV_OK) return fail(st, err);
+  return SV_OK;
+}
+
 sv_status sv_launch(sv_state* h, sv_program* p, const double* dev_params, size_t n_params, uint64_t seed,
                     uint64_t stream_id, uint64_t shot) {
   if (!h || !p) return fail(SV_ERR_ARG, "null argument");

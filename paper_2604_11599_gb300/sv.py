@@ -108,6 +108,7 @@ def lib():
         "sv_set_dense_tc": ([vp, i32], st),
         "sv_jit_check": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
         "sv_jit_check_adjoint": ([i32, i32, vp, sz, vp, sz, C.c_char_p, sz], st),
+        "sv_jit_check_batch": ([i32, sz, vp, vp, vp, C.c_char_p, sz], st),
         "sv_plan_info": ([i32, i32, vp, sz, vp, sz, i32, i32, i32, C.POINTER(ProgramStats)], st),
         "sv_profile_read": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double)], st),
         "sv_profile_work": ([vp, C.POINTER(WorkCounts)], st),
@@ -646,6 +647,21 @@ def jit_check_adjoint(ops: np.ndarray, n: int, dtype: str = "c64", pool=None) ->
     buf = C.create_string_buffer(8192)
     st = lib().sv_jit_check_adjoint(n, SV_C64 if dtype == "c64" else SV_C128, _ptr(ops), len(ops), _ptr(pl),
                                     0 if pl is None else pl.size, buf, 8192)
+    if st != 0:
+        raise SVError(st, buf.value.decode(errors="replace"))
+    return buf.value.decode(errors="replace")
+
+
+def jit_check_batch(programs, dtype: str = "c64") -> str:
+    """Compiles the batched kernel specialised to [(ops, n), ...] on the host
+    (no GPU); returns the log, raises on failure."""
+    arrs = [_ops(o) for o, _ in programs]
+    k = len(arrs)
+    ns = (C.c_int * k)(*[int(n) for _, n in programs])
+    ptrs = (C.c_void_p * k)(*[a.ctypes.data for a in arrs])
+    lens = (C.c_size_t * k)(*[len(a) for a in arrs])
+    buf = C.create_string_buffer(8192)
+    st = lib().sv_jit_check_batch(SV_C64 if dtype == "c64" else SV_C128, k, ns, ptrs, lens, buf, 8192)
     if st != 0:
         raise SVError(st, buf.value.decode(errors="replace"))
     return buf.value.decode(errors="replace")

@@ -65,3 +65,14 @@ def test_specialised_adjoint_kernel_compiles(svmod, dtype):
     log = svmod.jit_check_adjoint(W.hea(8, 2).ops, 8, dtype)
     spills = [int(v) for v in re.findall(r"(\d+) bytes spill stores", log)]
     assert spills and max(spills) <= 512, log
+
+
+def test_specialised_batch_kernel_compiles(svmod):
+    """The batched kernel specialised to several programs (each program's
+    passes as non-inlined stage functions, numbered consecutively) compiles
+    for sm_103a, for programs with measurement, feed-forward and loops."""
+    progs = [(W.sequential_feedforward(40 + n, n, layers=2).ops, n + 1) for n in (5, 12)]
+    log = svmod.jit_check_batch(progs, "c64")
+    assert "sv_jit_batch" in log
+    with pytest.raises(svmod.SVError, match="SV_ERR_ARG"):
+        svmod.jit_check_batch([], "c64")
